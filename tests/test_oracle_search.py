@@ -1,0 +1,139 @@
+"""Pins of the oracle's greedy search, exhaustive search and top-K (no GPU)."""
+import numpy as np
+import pytest
+
+import indep
+
+
+def _setup(lib, grid, l):
+    import oracle
+    lig = oracle.OLigand.from_library(lib, l)
+    samp = indep.trilinear_sampler(grid.values, grid.origin, grid.spacing)
+    frags = indep.fragments(lig.xyz, lig.bonds, lig.rot_edge)
+    return lig, samp, frags
+
+
+def _indep_score(lig, samp, frags, t, rot, theta, penalty):
+    """Independent score: torsions via scipy, then rotation `rot`, translation t."""
+    pose = np.concatenate([np.zeros(3), [1, 0, 0, 0], theta])
+    y = indep.pose_coords(lig.xyz, lig.bonds, lig.rot_edge, pose, frags=frags)
+    pts = rot.apply(y) + t
+    S, D, _ = indep.score_coords(samp, lig.type, pts, penalty)
+    return S, D
+
+
+def _replay(oracle_lib, w, lib, grid, l, restarts):
+    """Re-derive every greedy decision with the independent scorer."""
+    search = w["search"]
+    og = oracle_lib.OGrid.from_grid(grid)
+    lig, samp, frags = _setup(lib, grid, l)
+    res = oracle_lib.dock_ligand(lig, og, search, l, restarts)
+    step, P, n = search["torsion_step_deg"], search["passes"], lig.n_rot
+    nt = 360 // step
+    pen = search["out_penalty"]
+    for j, r in enumerate(restarts):
+        qr, tr = oracle_lib.restart_init(og, search, l, r)
+        u = [oracle_lib.uniform(search["seed"], l, r, k) for k in range(6)]
+        np.testing.assert_allclose(qr, oracle_lib.shoemake(u[:3]), atol=0)
+        np.testing.assert_allclose(tr, grid.center + (2 * np.array(u[3:]) - 1) * search["jitter"], atol=1e-12)
+        Rr = indep.rot_from_wxyz(qr)
+        rig = [_indep_score(lig, samp, frags, tr, Rr * indep.rot_from_wxyz(oracle_lib.octahedral(k)),
+                            np.zeros(n), pen) for k in range(search["n_rigid"])]
+        s = np.array([v[0] for v in rig])
+        k = int(np.argmax(s))
+        srt = np.sort(s)[::-1]
+        assert res["trace"][j, 0] == k
+        assert abs(res["gap"][j, 0] - (srt[0] - srt[1])) <= 1e-10 * rig[k][1]
+        rot = Rr * indep.rot_from_wxyz(oracle_lib.octahedral(k))
+        counts = np.zeros(n, int)
+        for p in range(P):
+            for b in range(n):
+                cand = []
+                for jj in range(nt):
+                    c = counts.copy()
+                    c[b] += jj
+                    cand.append(_indep_score(lig, samp, frags, tr, rot, np.radians(c * step), pen))
+                s = np.array([v[0] for v in cand])
+                jb = int(np.argmax(s))
+                srt = np.sort(s)[::-1]
+                d = 1 + p * n + b
+                if srt[0] - srt[1] > 1e-9 * cand[jb][1]:
+                    assert res["trace"][j, d] == jb
+                jb = int(res["trace"][j, d])
+                assert abs(res["gap"][j, d] - (srt[0] - srt[1])) <= 1e-10 * cand[jb][1]
+                assert abs(res["dnorm"][j, d] - cand[jb][1]) <= 1e-10 * cand[jb][1]
+                counts[b] = (counts[b] + jb) % nt
+        # final pose: canonical quaternion, wrapped angles, consistent score
+        pose = res["pose"][j]
+        assert pose[3] >= 0 and abs(np.linalg.norm(pose[3:7]) - 1) < 1e-14
+        assert np.all((pose[7:] >= -np.pi) & (pose[7:] < np.pi))
+        S, D = _indep_score(lig, samp, frags, pose[:3], indep.rot_from_wxyz(pose[3:7]), pose[7:], pen)
+        assert abs(res["score"][j] - S) <= 1e-10 * D
+    return res
+
+
+def test_greedy_decisions_are_argmaxes_small32(oracle_lib, small32):
+    w, lib, grid = small32
+    for l in range(0, lib.n_ligands, 4):
+        _replay(oracle_lib, w, lib, grid, l, range(0, 3))
+
+
+def test_greedy_decisions_are_argmaxes_screen(oracle_lib, screen_sample):
+    w, lib, grid = screen_sample
+    small = [l for l in range(lib.n_ligands) if lib.n_rot[l] <= 3 and lib.n_atoms[l] <= 30][:3]
+    assert small
+    for l in small:
+        _replay(oracle_lib, w, lib, grid, l, range(5, 6))
+
+
+def _rigid_copy(lib, l):
+    import gen
+    g = dict(lib.ligand(l))
+    g["rot_edge"] = np.zeros(0, np.int32)
+    return gen.from_ligands([g])
+
+
+def test_rigid_ligand_greedy_equals_brute_force(oracle_lib, small32):
+    w, lib, grid = small32
+    og = oracle_lib.OGrid.from_grid(grid)
+    for l in range(6):
+        rl = _rigid_copy(lib, l)
+        lig, samp, frags = _setup(rl, grid, 0)
+        g = oracle_lib.dock_ligand(lig, og, w["search"], l)
+        e = oracle_lib.dock_exhaustive(lig, og, w["search"], l)
+        np.testing.assert_array_equal(g["score"], e["score"])
+        for r in range(w["search"]["restarts"]):
+            qr, tr = oracle_lib.restart_init(og, w["search"], l, r)
+            Rr = indep.rot_from_wxyz(qr)
+            s = [_indep_score(lig, samp, frags, tr, Rr * indep.rot_from_wxyz(oracle_lib.octahedral(k)),
+                              np.zeros(0), 5.0)[0] for k in range(24)]
+            assert abs(max(s) - g["score"][r]) <= 1e-10 * abs(max(s)) + 1e-12
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 4, 5])
+def test_greedy_never_beats_exhaustive(oracle_lib, small32, l):
+    w, lib, grid = small32
+    og = oracle_lib.OGrid.from_grid(grid)
+    lig, samp, frags = _setup(lib, grid, l)
+    if lig.n_rot > 2:
+        pytest.skip("exhaustive enumeration kept to <= 2 torsions here")
+    rs = range(0, 4)
+    g = oracle_lib.dock_ligand(lig, og, w["search"], l, rs)
+    e = oracle_lib.dock_exhaustive(lig, og, w["search"], l, rs)
+    assert np.all(g["score"] <= e["score"] + 1e-12)
+    # brute force over (k, j) for the first restart, independent scorer
+    if lig.n_rot == 1:
+        qr, tr = oracle_lib.restart_init(og, w["search"], l, 0)
+        Rr = indep.rot_from_wxyz(qr)
+        best = max(_indep_score(lig, samp, frags, tr, Rr * indep.rot_from_wxyz(oracle_lib.octahedral(k)),
+                                np.radians([jj * 30.0]), 5.0)[0] for k in range(24) for jj in range(12))
+        assert abs(best - e["score"][0]) <= 1e-10 * max(1.0, abs(best))
+
+
+def test_top_k_order(oracle_lib):
+    rng = np.random.default_rng(9)
+    for _ in range(50):
+        s = np.round(rng.normal(size=40), 1)            # many exact ties
+        K = int(rng.integers(1, 40))
+        ref = sorted(range(40), key=lambda i: (-s[i], i))[:K]
+        assert oracle_lib.top_k(s, K).tolist() == ref
