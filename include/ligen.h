@@ -1,0 +1,208 @@
+/*
+ * ligen.h — C ABI of the GB300 docking pose search.
+ *
+ * The library docks a library of ligands into one pocket grid. For every
+ * ligand it runs R restarts; each restart tries the 24 rotations of the cube
+ * about the ligand's centroid (rigid stage), then sweeps every rotatable bond
+ * through its torsion increments (one pass after another, bonds in index
+ * order), keeping at every stage the candidate with the highest score; each
+ * ligand keeps its best K restarts. A pose's score is S = -sum_i E_i where E_i
+ * is the trilinear sample of atom i's channel in the grid (a fixed penalty
+ * outside the box). Paper §2 names the docking task; §3 states that its cost
+ * follows the ligand's atoms and its rotamers (rotatable atom subsets), which
+ * is what the per-ligand launch data here is organised around.
+ *
+ * Conventions for every call:
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream) unless an output lives in host memory, in which case
+ *     the call synchronises the stream before returning.
+ *   - Each structure's arrays live in ONE memory space: all device memory
+ *     (cudaMalloc / managed) or all host memory (pageable or pinned). The
+ *     library detects the space per structure; host inputs are copied to the
+ *     device inside the call and host outputs are copied back. The caller
+ *     keeps ownership of every pointer it passes.
+ *   - The library owns one internal device workspace per (device, stream),
+ *     grown on demand and released by ligen_release_workspaces(). Two calls
+ *     in flight on different streams use different workspaces; calls on the
+ *     same stream are ordered by the stream.
+ *   - Argument errors are detected on the host and returned immediately,
+ *     before any device work (message in ligen_last_error()). Errors in a
+ *     single ligand's data (not a tree, index or type out of range) do not
+ *     fail the call: that ligand's status entry is set to
+ *     LIGEN_ERR_BAD_LIGAND, its scores to -INFINITY, its poses to zero
+ *     (identity quaternion); the device never traps.
+ *   - Limits: atoms per ligand 1..256, rotatable bonds per ligand 0..32,
+ *     channels 1..64, grid points per axis >= 2.
+ */
+#ifndef LIGEN_H
+#define LIGEN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LIGEN_ABI_VERSION 1
+#define LIGEN_MAX_ATOMS 256
+#define LIGEN_MAX_ROT 32
+#define LIGEN_MAX_CHANNELS 64
+#define LIGEN_N_RIGID 24
+
+typedef enum {
+  LIGEN_OK = 0,
+  LIGEN_ERR_INVALID_ARG = -1,  /* a host-checkable argument is wrong */
+  LIGEN_ERR_UNSUPPORTED = -2,  /* valid but beyond the documented limits */
+  LIGEN_ERR_OOM = -3,          /* workspace allocation failed */
+  LIGEN_ERR_CUDA = -4,         /* a CUDA runtime call or launch failed */
+  LIGEN_ERR_TIMEOUT = -5,      /* a bounded device wait expired */
+  LIGEN_ERR_BAD_LIGAND = -6    /* per-ligand status value only */
+} ligen_status;
+
+typedef enum { LIGEN_F32 = 0 } ligen_dtype;
+
+/* A ligand library in CSR form.
+ *   h_atom_off, h_rot_off  HOST copies of atom_off and rot_off (always host).
+ *   atom_off [L+1]   ligand l owns atoms atom_off[l] .. atom_off[l+1]-1
+ *   xyz      [sum N][3] input conformation, Angstrom, row per atom
+ *   type     [sum N]    grid channel of each atom (< grid nc)
+ *   bonds    [sum N - L][2] tree edges as LOCAL atom ids (0..N_l-1);
+ *                       ligand l's N_l - 1 rows start at row atom_off[l] - l
+ *   rot_off  [L+1]   ligand l owns rotatable bonds rot_off[l] .. rot_off[l+1]-1
+ *   rot_edge [sum n] each rotatable bond as a LOCAL row id into the ligand's
+ *                    bond rows; rotatable bond b of ligand l is torsion b. */
+typedef struct ligen_ligands {
+  int32_t n_ligands;
+  int32_t reserved;
+  const int32_t* h_atom_off;
+  const int32_t* h_rot_off;
+  const int32_t* atom_off;
+  const float* xyz;
+  const uint8_t* type;
+  const int32_t* bonds;
+  const int32_t* rot_off;
+  const int32_t* rot_edge;
+} ligen_ligands_t;
+
+/* Pocket grid: data[z][y][x][c] (channel innermost), node (i, j, k) at
+ * origin + spacing * (i, j, k). A point is inside the box when
+ * 0 <= (p - origin) / spacing <= n - 1 on every axis. */
+typedef struct ligen_grid {
+  int32_t nx, ny, nz, nc;
+  float origin[3];
+  float spacing;
+  int32_t dtype;   /* ligen_dtype */
+  int32_t reserved;
+  const void* data;
+} ligen_grid_t;
+
+/* Search settings and optional outputs of ligen_dock_batch.
+ *   restarts          R >= 1
+ *   n_rigid           1..24: the rigid stage tries cube rotations 0..n_rigid-1
+ *   torsion_step_deg  2..360 and a divisor of 360; 360/step candidates per bond
+ *   passes            >= 0 sweeps over all rotatable bonds
+ *   top_k             1..R poses kept per ligand
+ *   mode              0 = greedy search (the only mode)
+ *   seed              restart random stream (SplitMix64 counter hash)
+ *   jitter            restart translation = grid centre + U[-jitter, jitter]^3 A
+ *   out_penalty       energy of an atom outside the grid box
+ *   stream            cudaStream_t or NULL
+ * Optional outputs (NULL to skip), same memory space as out_scores:
+ *   status      [L]  0 or LIGEN_ERR_BAD_LIGAND
+ *   trace       per ligand l, per restart r, D_l = 1 + passes * n_l int16:
+ *               the chosen cube rotation, then the chosen increment of every
+ *               (pass, bond); ligand l starts at R * (l + passes * rot_off[l]),
+ *               restart r at + r * D_l
+ *   top_restart [L][K] restart index of each kept pose
+ * Optional host-side timing: stage_ms (HOST, [LIGEN_N_STAGES]) receives the
+ * device time of each stage measured with CUDA events on `stream`; passing it
+ * makes the call synchronise the stream. */
+#define LIGEN_N_STAGES 5 /* h2d, grid prep, pack, dock, top-k + d2h */
+typedef struct ligen_params {
+  int32_t restarts;
+  int32_t n_rigid;
+  int32_t torsion_step_deg;
+  int32_t passes;
+  int32_t top_k;
+  int32_t mode;
+  uint64_t seed;
+  float jitter;
+  float out_penalty;
+  void* stream;
+  int32_t* status;
+  int16_t* trace;
+  int32_t* top_restart;
+  float* stage_ms;
+} ligen_params_t;
+
+/* Dock every ligand (paper §2, the dock task; cost per §3 follows atoms and
+ * rotamers).
+ *   out_scores [L][K]  scores of the kept poses, best first (ties: lower
+ *                      restart index first)
+ *   out_poses  ligand l's K poses start at float K * (7 * l + rot_off[l]);
+ *              each pose is 7 + n_l floats: translation t[3] (Angstrom, the
+ *              image of the input centroid), unit quaternion q = (w, x, y, z)
+ *              with w >= 0, torsion angles theta[n_l] in radians in [-pi, pi).
+ *              Atom positions of a pose: x_i = R(q) (T_theta(X0)_i - c0) + t,
+ *              where c0 is the input centroid and T_theta turns, bond by bond
+ *              in index order, the moving side of rotatable bond b by
+ *              theta_b about the axis from its fixed endpoint to its moving
+ *              endpoint (right-handed). The moving side is the smaller part
+ *              of the tree cut at the bond; on a tie, the part without atom 0.
+ * Returns LIGEN_OK or an error code. */
+int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
+                     const ligen_params_t* params, float* out_poses, float* out_scores);
+
+/* Score given poses (same pose packing as ligen_dock_batch with K =
+ * poses_per_ligand): out_scores[l][p] = S of pose p of ligand l, or
+ * -INFINITY for an invalid ligand. `poses` and `out_scores` share one memory
+ * space. */
+int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
+                      int32_t poses_per_ligand, const float* poses, float out_penalty,
+                      float* out_scores, void* stream);
+
+/* The ligand packer on its own, for inspection (paper §3: ligands are
+ * classified by atom count and rotamer count).
+ *   frag_bits [sum n][8]  bit i of word i/32 set when atom i is on the moving
+ *                         side of the rotatable bond
+ *   axis      [sum n][2]  (fixed endpoint u, moving endpoint v), local ids
+ *   bucket    [L]  atom_class * 11 + rotamer_class, atom classes <=32, <=64,
+ *                  <=128, larger; rotamer classes with upper edges
+ *                  0,1,2,3,4,6,8,12,16,24,32
+ *   status    [L]  0 or LIGEN_ERR_BAD_LIGAND
+ * Any output may be NULL. Outputs share one memory space. */
+int ligen_pack_ligands(const ligen_ligands_t* ligands, int32_t n_channels, uint32_t* frag_bits,
+                       int32_t* axis, int32_t* bucket, int32_t* status, void* stream);
+
+/* Paper Eq. 1: ligands per bucket l = b * SM * t / ws for the docking
+ * kernel instance used for ligands of up to max_atoms atoms, with b from the
+ * CUDA occupancy query, SM the device's multiprocessor count, t the kernel's
+ * threads per block and ws the warp size. Writes the four factors when the
+ * pointers are not NULL. Returns l (> 0) or an error code. */
+int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t, int32_t* ws);
+
+/* Measurement utility (the paper has no counterpart): the achievable rate of
+ * the docking kernel's memory access pattern on this device. Every thread of
+ * a full-device launch makes `loads_per_thread` aligned 32-byte loads from
+ * uniformly random records of `records` (DEVICE, n_records * 8 floats,
+ * 32-byte aligned) and discards the values (`sink`, DEVICE, 1 float, is
+ * written only to keep the loads alive). *loads_done receives the number of
+ * 32-byte loads made and *ms_out their device time (CUDA events on `stream`;
+ * the call synchronises). A buffer that fits in L2 gives the L2 gather
+ * ceiling. Returns LIGEN_OK or an error code. */
+int ligen_probe_gather(const float* records, int64_t n_records, int32_t loads_per_thread, float* sink,
+                       double* loads_done, float* ms_out, void* stream);
+
+/* Release every cached workspace of the calling thread's current device. */
+int ligen_release_workspaces(void);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* ligen_last_error(void);
+
+int ligen_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIGEN_H */

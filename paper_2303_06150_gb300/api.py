@@ -1,0 +1,208 @@
+"""Python binding of the docking library: same calls as include/ligen.h.
+
+Argument marshalling only. PyTorch provides the memory (device tensors, or
+pinned host tensors for the end-to-end path) and the current CUDA stream;
+every step of the search runs in libligen.so's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import GridT, LigandsT, ParamsT, check
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(device: torch.device):
+    if device.type == "cuda":
+        return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    if torch.cuda.is_available():
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return None
+
+
+class Ligands:
+    """A ligand library in CSR form, resident in one memory space.
+
+    Tensors: atom_off int32 [L+1], xyz float32 [sum N, 3], type uint8 [sum N],
+    bonds int32 [sum N - L, 2] (local atom ids), rot_off int32 [L+1],
+    rot_edge int32 [sum n] (local bond rows). Host copies of the offsets are
+    kept for the library's sizing.
+    """
+
+    def __init__(self, atom_off, xyz, type_, bonds, rot_off, rot_edge):
+        self.atom_off, self.xyz, self.type = atom_off, xyz, type_
+        self.bonds, self.rot_off, self.rot_edge = bonds, rot_off, rot_edge
+        self.h_atom_off = np.ascontiguousarray(atom_off.cpu().numpy(), np.int32)
+        self.h_rot_off = np.ascontiguousarray(rot_off.cpu().numpy(), np.int32)
+        self._s = LigandsT(len(self.h_atom_off) - 1, 0, self.h_atom_off.ctypes.data,
+                           self.h_rot_off.ctypes.data, atom_off.data_ptr(), xyz.data_ptr(),
+                           type_.data_ptr(), bonds.data_ptr(), rot_off.data_ptr(), rot_edge.data_ptr())
+
+    @classmethod
+    def from_arrays(cls, lib, device="cuda", pin: bool = False) -> "Ligands":
+        """From any object with numpy atom_off/xyz/type/bonds/rot_off/rot_edge."""
+        def t(a, dtype):
+            x = torch.from_numpy(np.ascontiguousarray(a, dtype))
+            if str(device) == "cpu":
+                return x.pin_memory() if pin else x
+            return x.to(device)
+        return cls(t(lib.atom_off, np.int32), t(lib.xyz, np.float32).reshape(-1, 3), t(lib.type, np.uint8),
+                   t(lib.bonds, np.int32).reshape(-1, 2), t(lib.rot_off, np.int32), t(lib.rot_edge, np.int32))
+
+    @property
+    def n_ligands(self) -> int:
+        return len(self.h_atom_off) - 1
+
+    @property
+    def n_rot(self) -> np.ndarray:
+        return np.diff(self.h_rot_off)
+
+    @property
+    def device(self) -> torch.device:
+        return self.xyz.device
+
+    def tensors(self):
+        return [self.atom_off, self.xyz, self.type, self.bonds, self.rot_off, self.rot_edge]
+
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in self.tensors())
+
+
+class PocketGrid:
+    """values [nz, ny, nx, nc] float32 (channel innermost), origin, spacing."""
+
+    def __init__(self, values: torch.Tensor, origin, spacing: float):
+        assert values.dtype == torch.float32 and values.dim() == 4 and values.is_contiguous()
+        self.values = values
+        self.origin = tuple(float(v) for v in origin)
+        self.spacing = float(spacing)
+        nz, ny, nx, nc = values.shape
+        self._s = GridT(nx, ny, nz, nc, (C.c_float * 3)(*self.origin), self.spacing, 0, 0,
+                        values.data_ptr())
+
+    @classmethod
+    def from_array(cls, values, origin, spacing, device="cuda", pin: bool = False) -> "PocketGrid":
+        x = torch.from_numpy(np.ascontiguousarray(values, np.float32))
+        x = (x.pin_memory() if pin else x) if str(device) == "cpu" else x.to(device)
+        return cls(x, origin, spacing)
+
+
+def _empty(shape, dtype, like: torch.device):
+    if like.type == "cuda":
+        return torch.empty(shape, dtype=dtype, device=like)
+    return torch.empty(shape, dtype=dtype, pin_memory=torch.cuda.is_available())
+
+
+def pose_offsets(rot_off: np.ndarray, K: int) -> np.ndarray:
+    """Start (in floats) of each ligand's K poses: K * (7 l + rot_off[l])."""
+    L = len(rot_off) - 1
+    return K * (7 * np.arange(L + 1, dtype=np.int64) + np.asarray(rot_off, np.int64))
+
+
+@dataclass
+class DockResult:
+    poses: torch.Tensor          # flat float32, see pose_offsets
+    scores: torch.Tensor         # [L, K]
+    status: torch.Tensor | None  # [L]
+    trace: torch.Tensor | None   # flat int16
+    top_restart: torch.Tensor | None
+    stage_ms: np.ndarray | None
+
+    def ligand_poses(self, rot_off, l: int) -> torch.Tensor:
+        K = self.scores.shape[1]
+        off = pose_offsets(rot_off, K)
+        n = int(rot_off[l + 1] - rot_off[l])
+        return self.poses[off[l]:off[l + 1]].reshape(K, 7 + n)
+
+
+def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_step_deg: int, passes: int,
+               top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
+               status: bool = True, trace: bool = False, top_restart: bool = False,
+               stage_ms: bool = False, out: DockResult | None = None) -> DockResult:
+    """ligen_dock_batch: dock every ligand, keep the top_k poses of each."""
+    lib = _abi.load()
+    L, dev = ligands.n_ligands, ligands.device
+    n_sum = int(ligands.h_rot_off[-1])
+    if out is None:
+        out = DockResult(
+            poses=_empty((top_k * (7 * L + n_sum),), torch.float32, dev),
+            scores=_empty((L, top_k), torch.float32, dev),
+            status=_empty((L,), torch.int32, dev) if status else None,
+            trace=_empty((restarts * int(np.sum(1 + passes * np.diff(ligands.h_rot_off))),), torch.int16, dev)
+            if trace else None,
+            top_restart=_empty((L, top_k), torch.int32, dev) if top_restart else None,
+            stage_ms=np.zeros(_abi.LIGEN_N_STAGES, np.float32) if stage_ms else None,
+        )
+    p = ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
+                float(jitter), float(out_penalty), _stream_handle(dev), _ptr(out.status), _ptr(out.trace),
+                _ptr(out.top_restart),
+                out.stage_ms.ctypes.data if out.stage_ms is not None else None)
+    check(lib.ligen_dock_batch(C.byref(ligands._s), C.byref(grid._s), C.byref(p), _ptr(out.poses),
+                               _ptr(out.scores)))
+    return out
+
+
+def score_poses(ligands: Ligands, grid: PocketGrid, poses: torch.Tensor, poses_per_ligand: int,
+                out_penalty: float = 5.0, out: torch.Tensor | None = None) -> torch.Tensor:
+    """ligen_score_poses: scores [L, poses_per_ligand] of packed poses."""
+    lib = _abi.load()
+    L = ligands.n_ligands
+    if out is None:
+        out = _empty((L, poses_per_ligand), torch.float32, poses.device)
+    check(lib.ligen_score_poses(C.byref(ligands._s), C.byref(grid._s), poses_per_ligand, _ptr(poses),
+                                float(out_penalty), _ptr(out), _stream_handle(poses.device)))
+    return out
+
+
+def pack_ligands(ligands: Ligands, n_channels: int):
+    """ligen_pack_ligands: (frag_bits [sum n, 8] uint32 as int32, axis [sum n, 2], bucket [L], status [L])."""
+    lib = _abi.load()
+    L, dev = ligands.n_ligands, ligands.device
+    n_sum = int(ligands.h_rot_off[-1])
+    bits = _empty((max(n_sum, 1), 8), torch.int32, dev)
+    axis = _empty((max(n_sum, 1), 2), torch.int32, dev)
+    bucket = _empty((L,), torch.int32, dev)
+    status = _empty((L,), torch.int32, dev)
+    check(lib.ligen_pack_ligands(C.byref(ligands._s), n_channels, _ptr(bits), _ptr(axis), _ptr(bucket),
+                                 _ptr(status), _stream_handle(dev)))
+    return bits[:n_sum], axis[:n_sum], bucket, status
+
+
+def bucket_size(max_atoms: int) -> dict:
+    """ligen_bucket_size: paper Eq. 1 factors for the docking kernel."""
+    lib = _abi.load()
+    b, sm, t, ws = (C.c_int32() for _ in range(4))
+    l = check(lib.ligen_bucket_size(max_atoms, C.byref(b), C.byref(sm), C.byref(t), C.byref(ws)))
+    return dict(l=int(l), b=b.value, sm=sm.value, t=t.value, ws=ws.value)
+
+
+def probe_gather(records: torch.Tensor, loads_per_thread: int = 256) -> dict:
+    """ligen_probe_gather: random 32-byte-record load rate over `records` (device, [n, 8] float32)."""
+    lib = _abi.load()
+    assert records.is_cuda and records.dtype == torch.float32 and records.shape[-1] == 8
+    sink = torch.zeros(1, dtype=torch.float32, device=records.device)
+    ms = C.c_float()
+    loads = C.c_double()
+    check(lib.ligen_probe_gather(_ptr(records), records.numel() // 8, loads_per_thread, _ptr(sink),
+                                 C.byref(loads), C.byref(ms), _stream_handle(records.device)))
+    return dict(loads=loads.value, ms=ms.value, gbs=loads.value * 32 / (ms.value * 1e-3) / 1e9)
+
+
+def release_workspaces() -> None:
+    check(_abi.load().ligen_release_workspaces())
+
+
+def last_error() -> str:
+    return _abi.load().ligen_last_error().decode()
+
+
+def abi_version() -> int:
+    return int(_abi.load().ligen_abi_version())

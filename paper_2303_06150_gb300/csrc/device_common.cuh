@@ -1,0 +1,164 @@
+// Device building blocks shared by the docking kernels: the restart random
+// stream, quaternion algebra, the cube rotation table and the grid sampler.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ligen {
+
+// ------------------------------------------------------------------ RNG --
+// SplitMix64 (Steele, Lea, Flood 2014): first output of a generator whose
+// state is x.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Uniform k of restart r of ligand l: 24 high bits of
+// SplitMix64(seed ^ ((l * 2^32 + r) * 8 + k)) scaled by 2^-24; exact in FP32.
+__device__ __forceinline__ float restart_uniform(uint64_t seed, uint32_t lig, uint32_t r, uint32_t k) {
+  uint64_t c = ((((uint64_t)lig << 32) + (uint64_t)r) << 3) + k;
+  return (float)(uint32_t)(splitmix64(seed ^ c) >> 40) * (1.0f / 16777216.0f);
+}
+
+// ------------------------------------------------------------ rotations --
+struct Quat {
+  float w, x, y, z;
+};
+
+__device__ __forceinline__ Quat qmul(Quat a, Quat b) {
+  return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z,
+          a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+          a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x,
+          a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+
+__device__ __forceinline__ Quat qnormalize(Quat q) {
+  float s = rsqrtf(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+  return {q.w * s, q.x * s, q.y * s, q.z * s};
+}
+
+// Row-major rotation matrix of a unit quaternion.
+__device__ __forceinline__ void qmat(Quat q, float* m) {
+  float w = q.w, x = q.x, y = q.y, z = q.z;
+  m[0] = 1.f - 2.f * (y * y + z * z); m[1] = 2.f * (x * y - w * z);       m[2] = 2.f * (x * z + w * y);
+  m[3] = 2.f * (x * y + w * z);       m[4] = 1.f - 2.f * (x * x + z * z); m[5] = 2.f * (y * z - w * x);
+  m[6] = 2.f * (x * z - w * y);       m[7] = 2.f * (y * z + w * x);       m[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Shoemake (1992) uniform rotation from three uniforms:
+// (sqrt(u0) cos 2pi u2, sqrt(1-u0) sin 2pi u1, sqrt(1-u0) cos 2pi u1, sqrt(u0) sin 2pi u2).
+__device__ __forceinline__ Quat shoemake(float u0, float u1, float u2) {
+  float r1 = sqrtf(1.0f - u0), r2 = sqrtf(u0);
+  float s1, c1, s2, c2;
+  sincospif(2.0f * u1, &s1, &c1);
+  sincospif(2.0f * u2, &s2, &c2);
+  return {r2 * c2, r1 * s1, r1 * c1, r2 * s2};
+}
+
+// The 24 proper rotations of the cube as unit quaternions (w, x, y, z):
+//  0 identity; 1-3 half turns about x, y, z; 4-9 quarter turns +x, -x, +y,
+//  -y, +z, -z; 10-17 third turns (120 deg) about the body diagonal
+//  (sx, sy, sz) with m = k - 10 and s = -1 where bit 2 (x), 1 (y), 0 (z) of m
+//  is set; 18-23 half turns about the face diagonals (1,1,0), (1,-1,0),
+//  (0,1,1), (0,1,-1), (1,0,1), (1,0,-1).
+#define LIGEN_H_ 0.5f
+#define LIGEN_S_ 0.70710678118654752f
+static __constant__ float kCubeQuat[24][4] = {
+    {1, 0, 0, 0},
+    {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1},
+    {LIGEN_S_, LIGEN_S_, 0, 0}, {LIGEN_S_, -LIGEN_S_, 0, 0},
+    {LIGEN_S_, 0, LIGEN_S_, 0}, {LIGEN_S_, 0, -LIGEN_S_, 0},
+    {LIGEN_S_, 0, 0, LIGEN_S_}, {LIGEN_S_, 0, 0, -LIGEN_S_},
+    {LIGEN_H_, LIGEN_H_, LIGEN_H_, LIGEN_H_}, {LIGEN_H_, LIGEN_H_, LIGEN_H_, -LIGEN_H_},
+    {LIGEN_H_, LIGEN_H_, -LIGEN_H_, LIGEN_H_}, {LIGEN_H_, LIGEN_H_, -LIGEN_H_, -LIGEN_H_},
+    {LIGEN_H_, -LIGEN_H_, LIGEN_H_, LIGEN_H_}, {LIGEN_H_, -LIGEN_H_, LIGEN_H_, -LIGEN_H_},
+    {LIGEN_H_, -LIGEN_H_, -LIGEN_H_, LIGEN_H_}, {LIGEN_H_, -LIGEN_H_, -LIGEN_H_, -LIGEN_H_},
+    {0, LIGEN_S_, LIGEN_S_, 0}, {0, LIGEN_S_, -LIGEN_S_, 0},
+    {0, 0, LIGEN_S_, LIGEN_S_}, {0, 0, LIGEN_S_, -LIGEN_S_},
+    {0, LIGEN_S_, 0, LIGEN_S_}, {0, LIGEN_S_, 0, -LIGEN_S_},
+};
+#undef LIGEN_H_
+#undef LIGEN_S_
+
+__device__ __forceinline__ Quat cube_quat(int k) {
+  return {kCubeQuat[k][0], kCubeQuat[k][1], kCubeQuat[k][2], kCubeQuat[k][3]};
+}
+
+// Matrix of cube rotation k, exact: its entries are 0 or +-1, so the FP32
+// matrix of the (rounded) quaternion is rounded to the nearest integer.
+__device__ __forceinline__ void cube_mat(int k, float* g) {
+  float m[9];
+  qmat(cube_quat(k), m);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) g[i] = rintf(m[i]);
+}
+
+// c = a * b for row-major 3x3 matrices.
+__device__ __forceinline__ void mat3mul(const float* a, const float* b, float* c) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int col = 0; col < 3; ++col)
+      c[3 * r + col] = a[3 * r] * b[col] + a[3 * r + 1] * b[3 + col] + a[3 * r + 2] * b[6 + col];
+}
+
+// Torsion increment j of a step of `step_deg` degrees: (cos, sin) of
+// j * step_deg degrees. Every kernel uses this one definition, so the
+// rotation applied after a decision is the one that was scored.
+__device__ __forceinline__ void torsion_cs(int j, int step_deg, float* c, float* s) {
+  sincospif((float)(j * step_deg) * (1.0f / 180.0f), s, c);
+}
+
+// --------------------------------------------------------------- sampler --
+// The grid is stored per cell and channel as the 8 coefficients of its
+// trilinear polynomial, E(f) = a0 + ax fx + ay fy + az fz + axy fx fy +
+// axz fx fz + ayz fy fz + axyz fx fy fz with f the position inside the cell.
+// One 32-byte record per (cell, channel) makes one sample one aligned 32-byte
+// load (one L2 sector) instead of eight scattered corner loads.
+struct GridView {
+  const float* coef;   // [(cz*cy + iy)*cx + ix][nc][8], 256-byte aligned
+  int cx, cy, cz;      // cells per axis (points - 1)
+  int nc;
+  float mx, my, mz;    // points - 1 per axis, as float: upper box bound in grid units
+  float penalty;
+};
+
+// 256-bit read-only load (sm_100+): one 32-byte record in one instruction.
+// Not volatile: the load has no side effect, so the compiler may batch it.
+__device__ __forceinline__ void ld_global_v8(const float* p, float (&v)[8]) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+                 "=f"(v[7])
+               : "l"(p));
+}
+
+// Energy of channel `c` at grid-unit position u (u = (x - origin) / spacing).
+// Inside iff 0 <= u <= n - 1 on every axis; cell i = min(floor(u), n - 2),
+// f = u - i. Outside: the penalty.
+__device__ __forceinline__ float grid_sample(const GridView& g, float ux, float uy, float uz, int c) {
+  bool inb = (ux >= 0.f) & (ux <= g.mx) & (uy >= 0.f) & (uy <= g.my) & (uz >= 0.f) & (uz <= g.mz);
+  float e = g.penalty;
+  if (inb) {
+    float fx = fminf(floorf(ux), g.mx - 1.f);
+    float fy = fminf(floorf(uy), g.my - 1.f);
+    float fz = fminf(floorf(uz), g.mz - 1.f);
+    int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+    float dx = ux - fx, dy = uy - fy, dz = uz - fz;
+    const float* rec = g.coef + ((size_t)((iz * g.cy + iy) * g.cx + ix) * g.nc + c) * 8;
+    float a[8];
+    ld_global_v8(rec, a);
+    float t1 = fmaf(dz, a[7], a[4]);
+    float t2 = fmaf(dy, t1, a[1]);
+    t2 = fmaf(dz, a[5], t2);
+    float t3 = fmaf(dz, a[6], a[2]);
+    e = fmaf(dz, a[3], a[0]);
+    e = fmaf(dy, t3, e);
+    e = fmaf(dx, t2, e);
+  }
+  return e;
+}
+
+}  // namespace ligen

@@ -1,0 +1,96 @@
+// Internal interface between the C ABI (ligen_api.cu) and the kernel
+// translation units. Not installed; not part of the ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace ligen {
+
+constexpr int kFragStride = 128;   // bytes per rotatable bond in the moving-atom lists
+constexpr int kLanesPerRestart = 4;
+
+// Device-resident ligand library (CSR, see ligen_ligands_t).
+struct LigandsDev {
+  int L;
+  const int32_t* atom_off;
+  const float* xyz;
+  const uint8_t* type;
+  const int32_t* bonds;
+  const int32_t* rot_off;
+  const int32_t* rot_edge;
+};
+
+// Packer outputs.
+struct Packed {
+  float4* xc;        // [sum N] centred input coordinates; w = atom type (int bits)
+  uchar4* binfo;     // [sum n] (fixed u, moving v, moving atoms excluding v, 0)
+  uint8_t* frag;     // [sum n][kFragStride] moving atoms excluding v, ascending
+  int32_t* status;   // [L] 0 or LIGEN_ERR_BAD_LIGAND
+  int32_t* bucket;   // [L] optional
+  uint32_t* fbits;   // [sum n][8] optional: full moving side as a bit mask
+  int32_t* axis;     // [sum n][2] optional: (u, v)
+};
+
+struct DockArgs {
+  LigandsDev lig;
+  Packed pk;
+  GridView grid;
+  float origin[3];
+  float inv_h;
+  float center[3];
+  float jitter;
+  uint64_t seed;
+  int R, n_rigid, step_deg, n_theta, passes;
+  int rpc;            // restarts per CTA
+  int chunks;         // CTAs per ligand
+  int max_atoms, max_rot, max_frag;   // shared-memory carve-up bounds
+  float* res_score;   // [L][R]
+  uint8_t* res_k;     // [L][R]
+  uint8_t* res_cnt;   // [sum n][R] torsion increments (mod n_theta) per restart
+  int16_t* trace;     // optional
+};
+
+struct TopkArgs {
+  int L, R, K, step_deg;
+  const int32_t* rot_off;
+  const int32_t* status;
+  const float* res_score;
+  const uint8_t* res_k;
+  const uint8_t* res_cnt;
+  uint64_t seed;
+  float center[3];
+  float jitter;
+  float* out_poses;
+  float* out_scores;
+  int32_t* top_restart;   // optional
+};
+
+struct ScoreArgs {
+  LigandsDev lig;
+  Packed pk;
+  GridView grid;
+  float origin[3];
+  float inv_h;
+  int P;              // poses per ligand
+  int max_atoms;
+  const float* poses;
+  float* out_scores;
+};
+
+cudaError_t launch_grid_prep(const float* values, int nx, int ny, int nz, int nc, float* coef,
+                             cudaStream_t s);
+cudaError_t launch_pack(const LigandsDev& lig, int nc, const Packed& out, cudaStream_t s);
+size_t dock_smem_bytes(int max_atoms, int max_rot, int max_frag, int rpc);
+cudaError_t launch_dock(const DockArgs& a, cudaStream_t s);
+int dock_threads_per_block(int rpc);
+cudaError_t dock_occupancy(int rpc, size_t smem, int* blocks_per_sm);
+cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s);
+cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s);
+cudaError_t launch_probe(const float* rec, uint32_t n_rec, int iters, uint64_t seed, float* sink, int blocks,
+                         cudaStream_t s);
+int probe_streams();
+int probe_threads();
+
+}  // namespace ligen

@@ -1,0 +1,289 @@
+// Docking kernel: restarts -> rigid stage -> torsion sweeps -> final score.
+//
+// Mapping. A CTA docks one ligand over `rpc` consecutive restarts; each
+// restart is owned by a group of G = 4 adjacent lanes, so one warp runs 8
+// restarts of the same ligand in lockstep (identical atom counts, bonds and
+// fragment sizes: no divergence). Inside a group the lanes split the
+// *candidates* of a stage (cube rotations in the rigid stage, torsion
+// increments in the sweep) and each lane sums its candidates' atom terms on
+// its own, so a stage needs no per-candidate reduction, only a 2-step
+// shuffle argmax across the group.
+//
+// Shared memory per CTA: the ligand (centred coordinates + type, bond axes,
+// moving-atom lists) and the current coordinates of every restart, in grid
+// units, as [atom][restart] planes so that the 8 restarts of a warp read 8
+// consecutive words. The sweep caches nothing: the moving side of a bond is
+// re-sampled for each increment j, the fixed side is a constant of the
+// decision and is not sampled at all (the argmax is over moving-side sums).
+#include "../../include/ligen.h"
+#include "internal.h"
+
+namespace ligen {
+namespace {
+
+constexpr int G = kLanesPerRestart;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct SmemLayout {
+  float4* sx;       // [max_atoms]
+  float* cx;        // [max_atoms][rpc]
+  float* cy;
+  float* cz;
+  uchar4* sb;       // [max_rot]
+  uint16_t* soff;   // [max_rot]
+  uint8_t* scnt;    // [max_rot][rpc]
+  uint8_t* sfrag;   // [max_frag]
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t carve(int max_atoms, int max_rot, int max_frag, int rpc,
+                                        unsigned char* base, SmemLayout* L) {
+  size_t off[8];
+  const size_t bytes[8] = {(size_t)max_atoms * 16, (size_t)max_atoms * rpc * 4, (size_t)max_atoms * rpc * 4,
+                           (size_t)max_atoms * rpc * 4, (size_t)max_rot * 4, (size_t)max_rot * 2,
+                           (size_t)max_rot * rpc, (size_t)max_frag};
+  size_t o = 0;
+  for (int i = 0; i < 8; ++i) { off[i] = o; o = align16(o + bytes[i]); }
+  if (L) {
+    L->sx = (float4*)(base + off[0]); L->cx = (float*)(base + off[1]);
+    L->cy = (float*)(base + off[2]);  L->cz = (float*)(base + off[3]);
+    L->sb = (uchar4*)(base + off[4]); L->soff = (uint16_t*)(base + off[5]);
+    L->scnt = base + off[6];          L->sfrag = base + off[7];
+  }
+  return o;
+}
+
+// Argmax over the G lanes of a group: higher score wins, lower index on ties.
+__device__ __forceinline__ void group_argmax(float& s, int& idx) {
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    float os = __shfl_xor_sync(kFull, s, o);
+    int oi = __shfl_xor_sync(kFull, idx, o);
+    if (os > s || (os == s && oi < idx)) { s = os; idx = oi; }
+  }
+}
+
+template <int SLOTS>
+__global__ void __launch_bounds__(128) dock_kernel(const DockArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int l = blockIdx.x / a.chunks;
+  const int chunk = blockIdx.x - l * a.chunks;
+  if (a.pk.status[l] != 0) return;   // uniform over the CTA
+  SmemLayout S;
+  carve(a.max_atoms, a.max_rot, a.max_frag, a.rpc, smem, &S);
+  const int rpc = a.rpc;
+  const int tid = threadIdx.x;
+  const int a0 = a.lig.atom_off[l];
+  const int N = a.lig.atom_off[l + 1] - a0;
+  const int r0 = a.lig.rot_off[l];
+  const int n = a.lig.rot_off[l + 1] - r0;
+
+  for (int i = tid; i < N; i += blockDim.x) S.sx[i] = a.pk.xc[a0 + i];
+  for (int b = tid; b < n; b += blockDim.x) S.sb[b] = a.pk.binfo[r0 + b];
+  for (int i = tid; i < n * rpc; i += blockDim.x) S.scnt[i] = 0;
+  __syncthreads();
+  if (tid == 0) {
+    int o = 0;
+    for (int b = 0; b < n; ++b) { S.soff[b] = (uint16_t)o; o += S.sb[b].z; }
+  }
+  __syncthreads();
+  for (int b = 0; b < n; ++b) {
+    const int m = S.sb[b].z;
+    for (int i = tid; i < m; i += blockDim.x)
+      S.sfrag[S.soff[b] + i] = a.pk.frag[(size_t)(r0 + b) * kFragStride + i];
+  }
+  __syncthreads();
+
+  const int rr = tid / G, sub = tid % G;
+  const int r_raw = chunk * rpc + rr;
+  const bool active = r_raw < a.R;
+  const int r = active ? r_raw : a.R - 1;   // idle groups shadow a real restart
+  const GridView& grid = a.grid;
+
+  // ---- restart initialisation: q_r (Shoemake), t_r = centre + jitter
+  float u[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) u[k] = restart_uniform(a.seed, (uint32_t)l, (uint32_t)r, (uint32_t)k);
+  const Quat qr = qnormalize(shoemake(u[0], u[1], u[2]));
+  float Rm[9];
+  qmat(qr, Rm);
+  float M[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) M[i] = Rm[i] * a.inv_h;   // body (Angstrom) -> grid units
+  float o[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float t = a.center[k] + (2.0f * u[3 + k] - 1.0f) * a.jitter;
+    o[k] = (t - a.origin[k]) * a.inv_h;
+  }
+
+  // ---- rigid stage: lane `sub` scores cube rotations sub, sub+G, ...
+  float best = -INFINITY;
+  int kb = 0;
+  for (int k = sub; k < a.n_rigid; k += G) {
+    float Gk[9], Mk[9];
+    cube_mat(k, Gk);
+    mat3mul(M, Gk, Mk);
+    float acc = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const float4 X = S.sx[i];
+      const float ux = fmaf(Mk[0], X.x, fmaf(Mk[1], X.y, fmaf(Mk[2], X.z, o[0])));
+      const float uy = fmaf(Mk[3], X.x, fmaf(Mk[4], X.y, fmaf(Mk[5], X.z, o[1])));
+      const float uz = fmaf(Mk[6], X.x, fmaf(Mk[7], X.y, fmaf(Mk[8], X.z, o[2])));
+      acc -= grid_sample(grid, ux, uy, uz, __float_as_int(X.w));
+    }
+    if (acc > best) { best = acc; kb = k; }
+  }
+  group_argmax(best, kb);
+  const int D = 1 + a.passes * n;
+  int16_t* trace = nullptr;
+  if (a.trace && active)
+    trace = a.trace + (size_t)a.R * ((size_t)l + (size_t)a.passes * r0) + (size_t)r * D;
+  if (trace && sub == 0) trace[0] = (int16_t)kb;
+  {
+    float Gk[9], Mk[9];
+    cube_mat(kb, Gk);
+    mat3mul(M, Gk, Mk);
+    for (int i = sub; i < N; i += G) {
+      const float4 X = S.sx[i];
+      S.cx[i * rpc + rr] = fmaf(Mk[0], X.x, fmaf(Mk[1], X.y, fmaf(Mk[2], X.z, o[0])));
+      S.cy[i * rpc + rr] = fmaf(Mk[3], X.x, fmaf(Mk[4], X.y, fmaf(Mk[5], X.z, o[1])));
+      S.cz[i * rpc + rr] = fmaf(Mk[6], X.x, fmaf(Mk[7], X.y, fmaf(Mk[8], X.z, o[2])));
+    }
+  }
+  __syncwarp();
+
+  // ---- torsion sweep: lane `sub` scores increments j = base + sub + G*s
+  const int nt = a.n_theta;
+  const int per_chunk = G * SLOTS;
+  const int nchunks = (nt + per_chunk - 1) / per_chunk;
+  float cs[SLOTS], sn[SLOTS];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) torsion_cs(sub + G * s, a.step_deg, &cs[s], &sn[s]);
+
+  for (int p = 0; p < a.passes; ++p) {
+    for (int b = 0; b < n; ++b) {
+      const uchar4 bi = S.sb[b];
+      const int vi = bi.y, m = bi.z, off = S.soff[b];
+      const float vx = S.cx[vi * rpc + rr], vy = S.cy[vi * rpc + rr], vz = S.cz[vi * rpc + rr];
+      float kx = vx - S.cx[bi.x * rpc + rr];
+      float ky = vy - S.cy[bi.x * rpc + rr];
+      float kz = vz - S.cz[bi.x * rpc + rr];
+      const float kn = rsqrtf(kx * kx + ky * ky + kz * kz);
+      kx *= kn; ky *= kn; kz *= kn;
+      float bs = -INFINITY;
+      int jb = 0;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        const int jbase = ch * per_chunk;
+        if (ch > 0) {
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) torsion_cs(jbase + sub + G * s, a.step_deg, &cs[s], &sn[s]);
+        }
+        float acc[SLOTS];
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) acc[s] = 0.f;
+        for (int t = 0; t < m; ++t) {
+          const int i = S.sfrag[off + t];
+          const int c = __float_as_int(S.sx[i].w);
+          const float dx = S.cx[i * rpc + rr] - vx;
+          const float dy = S.cy[i * rpc + rr] - vy;
+          const float dz = S.cz[i * rpc + rr] - vz;
+          const float kd = kx * dx + ky * dy + kz * dz;
+          const float px = fmaf(kx, kd, vx), py = fmaf(ky, kd, vy), pz = fmaf(kz, kd, vz);
+          const float ex = fmaf(-kx, kd, dx), ey = fmaf(-ky, kd, dy), ez = fmaf(-kz, kd, dz);
+          const float qx = ky * dz - kz * dy, qy = kz * dx - kx * dz, qz = kx * dy - ky * dx;
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) {
+            const float ux = fmaf(ex, cs[s], fmaf(qx, sn[s], px));
+            const float uy = fmaf(ey, cs[s], fmaf(qy, sn[s], py));
+            const float uz = fmaf(ez, cs[s], fmaf(qz, sn[s], pz));
+            acc[s] -= grid_sample(grid, ux, uy, uz, c);
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          const int j = jbase + sub + G * s;
+          if (j < nt && acc[s] > bs) { bs = acc[s]; jb = j; }
+        }
+      }
+      if (nchunks > 1) {
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) torsion_cs(sub + G * s, a.step_deg, &cs[s], &sn[s]);
+      }
+      group_argmax(bs, jb);
+      if (jb != 0) {
+        float c, s;
+        torsion_cs(jb, a.step_deg, &c, &s);
+        for (int t = sub; t < m; t += G) {
+          const int i = S.sfrag[off + t];
+          const float dx = S.cx[i * rpc + rr] - vx;
+          const float dy = S.cy[i * rpc + rr] - vy;
+          const float dz = S.cz[i * rpc + rr] - vz;
+          const float kd = kx * dx + ky * dy + kz * dz;
+          const float px = fmaf(kx, kd, vx), py = fmaf(ky, kd, vy), pz = fmaf(kz, kd, vz);
+          const float ex = fmaf(-kx, kd, dx), ey = fmaf(-ky, kd, dy), ez = fmaf(-kz, kd, dz);
+          const float qx = ky * dz - kz * dy, qy = kz * dx - kx * dz, qz = kx * dy - ky * dx;
+          S.cx[i * rpc + rr] = fmaf(ex, c, fmaf(qx, s, px));
+          S.cy[i * rpc + rr] = fmaf(ey, c, fmaf(qy, s, py));
+          S.cz[i * rpc + rr] = fmaf(ez, c, fmaf(qz, s, pz));
+        }
+      }
+      __syncwarp();
+      if (sub == 0) {
+        S.scnt[b * rpc + rr] = (uint8_t)((S.scnt[b * rpc + rr] + jb) % nt);
+        if (trace) trace[1 + p * n + b] = (int16_t)jb;
+      }
+    }
+  }
+
+  // ---- final score of the restart's pose (all atoms)
+  float acc = 0.f;
+  for (int i = sub; i < N; i += G)
+    acc -= grid_sample(grid, S.cx[i * rpc + rr], S.cy[i * rpc + rr], S.cz[i * rpc + rr],
+                       __float_as_int(S.sx[i].w));
+#pragma unroll
+  for (int off = 1; off < G; off <<= 1) acc += __shfl_xor_sync(kFull, acc, off);
+  if (active && sub == 0) {
+    const size_t lr = (size_t)l * a.R + r;
+    a.res_score[lr] = acc;
+    a.res_k[lr] = (uint8_t)kb;
+    uint8_t* cnt = a.res_cnt + (size_t)r0 * a.R + (size_t)r * n;
+    for (int b = 0; b < n; ++b) cnt[b] = S.scnt[b * rpc + rr];
+  }
+}
+
+}  // namespace
+
+size_t dock_smem_bytes(int max_atoms, int max_rot, int max_frag, int rpc) {
+  return carve(max_atoms, max_rot, max_frag, rpc, nullptr, nullptr);
+}
+
+int dock_threads_per_block(int rpc) { return rpc * G; }
+
+template <int SLOTS>
+static cudaError_t launch_slots(const DockArgs& a, size_t smem, cudaStream_t s) {
+  auto* k = dock_kernel<SLOTS>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const size_t blocks = (size_t)a.lig.L * a.chunks;
+  k<<<(unsigned)blocks, a.rpc * G, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dock(const DockArgs& a, cudaStream_t s) {
+  if (a.lig.L == 0) return cudaSuccess;
+  const size_t smem = dock_smem_bytes(a.max_atoms, a.max_rot, a.max_frag, a.rpc);
+  if (a.n_theta <= 3 * G) return launch_slots<3>(a, smem, s);
+  return launch_slots<9>(a, smem, s);
+}
+
+cudaError_t dock_occupancy(int rpc, size_t smem, int* blocks_per_sm) {
+  auto* k = dock_kernel<9>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, rpc * G, smem);
+}
+
+}  // namespace ligen

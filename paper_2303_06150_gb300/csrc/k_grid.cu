@@ -1,0 +1,56 @@
+// Grid preparation: node values [z][y][x][c] -> per-(cell, channel) records
+// of the 8 coefficients of the cell's trilinear polynomial (see GridView).
+// One thread per (cell, channel); consecutive threads read consecutive
+// channels of the same corners and write consecutive 32-byte records.
+#include "internal.h"
+
+namespace ligen {
+namespace {
+
+__global__ void grid_prep_kernel(const float* __restrict__ v, int nx, int ny, int nz, int nc,
+                                 float* __restrict__ coef) {
+  const int cx = nx - 1, cy = ny - 1, cz = nz - 1;
+  const size_t total = (size_t)cx * cy * cz * nc;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t % nc);
+    size_t cell = t / nc;
+    const int ix = (int)(cell % cx);
+    cell /= cx;
+    const int iy = (int)(cell % cy);
+    const int iz = (int)(cell / cy);
+    auto at = [&](int dx, int dy, int dz) -> double {
+      return (double)v[(((size_t)(iz + dz) * ny + (iy + dy)) * nx + (ix + dx)) * nc + c];
+    };
+    const double c000 = at(0, 0, 0), c100 = at(1, 0, 0), c010 = at(0, 1, 0), c110 = at(1, 1, 0);
+    const double c001 = at(0, 0, 1), c101 = at(1, 0, 1), c011 = at(0, 1, 1), c111 = at(1, 1, 1);
+    float4 lo, hi;
+    lo.x = (float)c000;                                   // a0
+    lo.y = (float)(c100 - c000);                          // ax
+    lo.z = (float)(c010 - c000);                          // ay
+    lo.w = (float)(c001 - c000);                          // az
+    hi.x = (float)(c110 - c100 - c010 + c000);            // axy
+    hi.y = (float)(c101 - c100 - c001 + c000);            // axz
+    hi.z = (float)(c011 - c010 - c001 + c000);            // ayz
+    hi.w = (float)(c111 - c110 - c101 - c011 + c100 + c010 + c001 - c000);  // axyz
+    float4* rec = reinterpret_cast<float4*>(coef + t * 8);
+    rec[0] = lo;
+    rec[1] = hi;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_grid_prep(const float* values, int nx, int ny, int nz, int nc, float* coef,
+                             cudaStream_t s) {
+  const size_t total = (size_t)(nx - 1) * (ny - 1) * (nz - 1) * nc;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t want = (total + 255) / 256;
+  const int blocks = (int)(want < (size_t)sms * 16 ? want : (size_t)sms * 16);
+  grid_prep_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(values, nx, ny, nz, nc, coef);
+  return cudaGetLastError();
+}
+
+}  // namespace ligen

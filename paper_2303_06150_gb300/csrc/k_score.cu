@@ -1,0 +1,89 @@
+// Pose scoring: one warp per pose.
+//
+// The pose (t, q, theta) is turned into atom positions exactly as the docking
+// output defines them: torsions bond by bond in index order on the centred
+// input coordinates (each about the current axis from its fixed endpoint to
+// its moving endpoint), then the rotation R(q / |q|) and the translation t.
+// Each lane then samples its atoms and the warp sums S = -sum_i E_i.
+#include <cmath>
+
+#include "../../include/ligen.h"
+#include "internal.h"
+
+namespace ligen {
+namespace {
+
+constexpr int kScoreWarps = 4;
+
+__global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(const ScoreArgs a) {
+  __shared__ float4 ys[kScoreWarps][LIGEN_MAX_ATOMS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t gp = (size_t)blockIdx.x * kScoreWarps + w;
+  if (gp >= (size_t)a.lig.L * a.P) return;
+  const int l = (int)(gp / a.P), p = (int)(gp % a.P);
+  const unsigned full = 0xffffffffu;
+  if (a.pk.status[l] != 0) {
+    if (lane == 0) a.out_scores[gp] = -INFINITY;
+    return;
+  }
+  const int a0 = a.lig.atom_off[l];
+  const int N = a.lig.atom_off[l + 1] - a0;
+  const int r0 = a.lig.rot_off[l];
+  const int n = a.lig.rot_off[l + 1] - r0;
+  const float* pose = a.poses + (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
+  float4* y = ys[w];
+  for (int i = lane; i < N; i += 32) y[i] = a.pk.xc[a0 + i];
+  __syncwarp();
+  for (int b = 0; b < n; ++b) {
+    const uchar4 bi = a.pk.binfo[r0 + b];
+    const float4 pv = y[bi.y], pu = y[bi.x];
+    float kx = pv.x - pu.x, ky = pv.y - pu.y, kz = pv.z - pu.z;
+    const float kn = rsqrtf(kx * kx + ky * ky + kz * kz);
+    kx *= kn; ky *= kn; kz *= kn;
+    float s, c;
+    sincosf(pose[7 + b], &s, &c);
+    const uint8_t* fr = a.pk.frag + (size_t)(r0 + b) * kFragStride;
+    for (int t = lane; t < bi.z; t += 32) {
+      const int i = fr[t];
+      float4 v = y[i];
+      const float dx = v.x - pv.x, dy = v.y - pv.y, dz = v.z - pv.z;
+      const float kd = kx * dx + ky * dy + kz * dz;
+      const float ex = dx - kx * kd, ey = dy - ky * kd, ez = dz - kz * kd;
+      const float qx = ky * dz - kz * dy, qy = kz * dx - kx * dz, qz = kx * dy - ky * dx;
+      v.x = pv.x + kx * kd + ex * c + qx * s;
+      v.y = pv.y + ky * kd + ey * c + qy * s;
+      v.z = pv.z + kz * kd + ez * c + qz * s;
+      y[i] = v;
+    }
+    __syncwarp();
+  }
+  const Quat q = qnormalize({pose[3], pose[4], pose[5], pose[6]});
+  float R[9];
+  qmat(q, R);
+  float acc = 0.f;
+  for (int i = lane; i < N; i += 32) {
+    const float4 v = y[i];
+    float u[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float x = fmaf(R[3 * r], v.x, fmaf(R[3 * r + 1], v.y, fmaf(R[3 * r + 2], v.z, pose[r])));
+      u[r] = (x - a.origin[r]) * a.inv_h;
+    }
+    acc -= grid_sample(a.grid, u[0], u[1], u[2], __float_as_int(v.w));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(full, acc, o);
+  if (lane == 0) a.out_scores[gp] = acc;
+}
+
+}  // namespace
+
+cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s) {
+  const size_t total = (size_t)a.lig.L * a.P;
+  if (total == 0) return cudaSuccess;
+  const size_t blocks = (total + kScoreWarps - 1) / kScoreWarps;
+  score_kernel<<<(unsigned)blocks, 32 * kScoreWarps, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ligen

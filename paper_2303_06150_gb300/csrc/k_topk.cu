@@ -1,0 +1,97 @@
+// Top-K selection and pose compaction: one warp per ligand.
+//
+// Round k extracts the best restart that ranks after the one extracted in
+// round k-1 in the order (score descending, restart index ascending), so no
+// "taken" marks are needed: every restart ranked before the previous winner
+// compares as already taken. The winner's pose is rebuilt from its restart
+// index (random stream), its cube rotation and its torsion counts and
+// written as t[3], q[4] (w >= 0), theta[n] in [-pi, pi). A NaN score (only
+// possible from a NaN grid) ranks as -infinity, so the order stays total and
+// K <= R rounds always find a restart.
+#include <cmath>
+
+#include "../../include/ligen.h"
+#include "internal.h"
+
+namespace ligen {
+namespace {
+
+constexpr int kTopkWarps = 4;
+
+__global__ void __launch_bounds__(32 * kTopkWarps) topk_kernel(const TopkArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.x * kTopkWarps + (threadIdx.x >> 5);
+  if (l >= a.L) return;
+  const unsigned full = 0xffffffffu;
+  const int r0 = a.rot_off[l];
+  const int n = a.rot_off[l + 1] - r0;
+  const int plen = 7 + n;
+  float* poses = a.out_poses + (size_t)a.K * (7 * (size_t)l + r0);
+  float* scores = a.out_scores + (size_t)l * a.K;
+  if (a.status[l] != 0) {
+    for (int k = 0; k < a.K; ++k) {
+      if (lane == 0) scores[k] = -INFINITY;
+      if (a.top_restart && lane == 0) a.top_restart[(size_t)l * a.K + k] = -1;
+      for (int e = lane; e < plen; e += 32) poses[(size_t)k * plen + e] = (e == 3) ? 1.f : 0.f;
+    }
+    return;
+  }
+  const float* rs = a.res_score + (size_t)l * a.R;
+  float last_s = INFINITY;
+  int last_r = -1;
+  for (int k = 0; k < a.K; ++k) {
+    float bs = -INFINITY;
+    int br = 0x7fffffff;
+    for (int r = lane; r < a.R; r += 32) {
+      const float s = isnan(rs[r]) ? -INFINITY : rs[r];   // total order: always R candidates
+      const bool after = (s < last_s) || (s == last_s && r > last_r);
+      if (after && (s > bs || (s == bs && r < br))) { bs = s; br = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(full, bs, o);
+      const int orr = __shfl_xor_sync(full, br, o);
+      if (os > bs || (os == bs && orr < br)) { bs = os; br = orr; }
+    }
+    if (br >= a.R) br = a.R - 1;   // unreachable while K <= R; keeps every index in range
+    last_s = bs;
+    last_r = br;
+    // rebuild the winner's pose
+    float u[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) u[q] = restart_uniform(a.seed, (uint32_t)l, (uint32_t)br, (uint32_t)q);
+    const Quat qr = qnormalize(shoemake(u[0], u[1], u[2]));
+    Quat q = qnormalize(qmul(qr, cube_quat(a.res_k[(size_t)l * a.R + br])));
+    if (q.w < 0.f) q = {-q.w, -q.x, -q.y, -q.z};
+    float* out = poses + (size_t)k * plen;
+    const uint8_t* cnt = a.res_cnt + (size_t)r0 * a.R + (size_t)br * n;
+    for (int e = lane; e < plen; e += 32) {
+      float v;
+      if (e < 3) {
+        v = a.center[e] + (2.0f * u[3 + e] - 1.0f) * a.jitter;
+      } else if (e < 7) {
+        v = (e == 3) ? q.w : (e == 4) ? q.x : (e == 5) ? q.y : q.z;
+      } else {
+        int deg = ((int)cnt[e - 7] * a.step_deg) % 360;
+        if (deg >= 180) deg -= 360;
+        v = (float)deg * 0.017453292519943295f;
+      }
+      out[e] = v;
+    }
+    if (lane == 0) {
+      scores[k] = bs;
+      if (a.top_restart) a.top_restart[(size_t)l * a.K + k] = br;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s) {
+  if (a.L == 0) return cudaSuccess;
+  const int blocks = (a.L + kTopkWarps - 1) / kTopkWarps;
+  topk_kernel<<<blocks, 32 * kTopkWarps, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ligen

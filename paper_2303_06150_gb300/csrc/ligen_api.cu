@@ -1,0 +1,591 @@
+// C ABI of the docking library: argument checks, memory-space detection,
+// workspace management, host staging and the launch sequence
+//   [H2D] -> grid preparation -> ligand packer -> docking -> top-K -> [D2H].
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ligen.h"
+#include "internal.h"
+
+using namespace ligen;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(LIGEN_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LG_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// 1 = host memory (pageable or pinned), 0 = device or managed memory.
+int is_host(const void* p) {
+  if (!p) return -1;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 0 : 1;
+}
+
+// Memory space shared by a set of pointers (NULL entries ignored); -1 if mixed.
+int space_of(std::initializer_list<const void*> ptrs) {
+  int s = -2;
+  for (const void* p : ptrs) {
+    if (!p) continue;
+    int h = is_host(p);
+    if (s == -2) s = h;
+    else if (s != h) return -1;
+  }
+  return s == -2 ? 0 : s;
+}
+
+// ------------------------------------------------------------ workspace --
+struct Workspace {
+  char* base = nullptr;
+  size_t cap = 0;
+};
+
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+// Bump allocator over one workspace; every region is 256-byte aligned.
+struct Arena {
+  size_t used = 0;
+  char* base = nullptr;
+  size_t take(size_t bytes) {
+    size_t at = used;
+    used = (used + bytes + 255) & ~(size_t)255;
+    return at;
+  }
+  template <class T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
+};
+
+int get_workspace(cudaStream_t s, size_t bytes, char** out) {
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  Workspace& w = g_ws[{dev, s}];
+  if (w.cap < bytes) {
+    if (w.base) {
+      LG_CUDA(cudaStreamSynchronize(s));
+      cudaFree(w.base);
+      w.base = nullptr;
+      w.cap = 0;
+    }
+    size_t want = bytes + bytes / 8 + (1 << 20);
+    cudaError_t e = cudaMalloc(&w.base, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      w.base = nullptr;
+      return fail(LIGEN_ERR_OOM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+    }
+    w.cap = want;
+  }
+  *out = w.base;
+  return LIGEN_OK;
+}
+
+// ------------------------------------------------------------ checking --
+struct LibShape {
+  int64_t atoms = 0, rot = 0;
+  int max_atoms = 0, max_rot = 0;
+  int64_t max_frag = 0;
+  int64_t trace_len = 0;   // sum over ligands of 1 + passes * n_l (times R later)
+};
+
+int check_ligands(const ligen_ligands_t* g, int passes, LibShape* sh) {
+  if (!g) return fail(LIGEN_ERR_INVALID_ARG, "ligands is NULL");
+  if (g->n_ligands < 0) return fail(LIGEN_ERR_INVALID_ARG, "n_ligands < 0");
+  if (g->n_ligands == 0) return LIGEN_OK;
+  if (!g->h_atom_off || !g->h_rot_off)
+    return fail(LIGEN_ERR_INVALID_ARG, "h_atom_off and h_rot_off (host copies) are required");
+  if (!g->atom_off || !g->rot_off || !g->xyz || !g->type)
+    return fail(LIGEN_ERR_INVALID_ARG, "atom_off, rot_off, xyz and type are required");
+  if (g->h_atom_off[0] != 0 || g->h_rot_off[0] != 0)
+    return fail(LIGEN_ERR_INVALID_ARG, "offsets must start at 0");
+  for (int l = 0; l < g->n_ligands; ++l) {
+    int N = g->h_atom_off[l + 1] - g->h_atom_off[l];
+    int n = g->h_rot_off[l + 1] - g->h_rot_off[l];
+    if (N < 1) return fail(LIGEN_ERR_INVALID_ARG, "ligand %d has %d atoms", l, N);
+    if (n < 0) return fail(LIGEN_ERR_INVALID_ARG, "rot_off decreases at ligand %d", l);
+    if (N > LIGEN_MAX_ATOMS) return fail(LIGEN_ERR_UNSUPPORTED, "ligand %d has %d atoms (max %d)", l, N, LIGEN_MAX_ATOMS);
+    if (n > LIGEN_MAX_ROT) return fail(LIGEN_ERR_UNSUPPORTED, "ligand %d has %d rotatable bonds (max %d)", l, n, LIGEN_MAX_ROT);
+    sh->max_atoms = N > sh->max_atoms ? N : sh->max_atoms;
+    sh->max_rot = n > sh->max_rot ? n : sh->max_rot;
+    int64_t frag = (int64_t)n * (N / 2);
+    sh->max_frag = frag > sh->max_frag ? frag : sh->max_frag;
+    sh->trace_len += 1 + (int64_t)passes * n;
+  }
+  sh->atoms = g->h_atom_off[g->n_ligands];
+  sh->rot = g->h_rot_off[g->n_ligands];
+  if (sh->atoms - g->n_ligands > 0 && !g->bonds) return fail(LIGEN_ERR_INVALID_ARG, "bonds is NULL");
+  if (sh->rot > 0 && !g->rot_edge) return fail(LIGEN_ERR_INVALID_ARG, "rot_edge is NULL");
+  if (sh->atoms > INT32_MAX / 4) return fail(LIGEN_ERR_UNSUPPORTED, "library too large");
+  return LIGEN_OK;
+}
+
+int check_grid(const ligen_grid_t* g) {
+  if (!g) return fail(LIGEN_ERR_INVALID_ARG, "grid is NULL");
+  if (!g->data) return fail(LIGEN_ERR_INVALID_ARG, "grid data is NULL");
+  if (g->nx < 2 || g->ny < 2 || g->nz < 2) return fail(LIGEN_ERR_INVALID_ARG, "grid needs >= 2 points per axis");
+  if (g->nc < 1 || g->nc > LIGEN_MAX_CHANNELS)
+    return fail(LIGEN_ERR_UNSUPPORTED, "grid channels %d outside 1..%d", g->nc, LIGEN_MAX_CHANNELS);
+  if (g->dtype != LIGEN_F32) return fail(LIGEN_ERR_UNSUPPORTED, "grid dtype %d not supported", g->dtype);
+  if (!(g->spacing > 0.f) || !std::isfinite(g->spacing)) return fail(LIGEN_ERR_INVALID_ARG, "grid spacing must be > 0");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(g->origin[k])) return fail(LIGEN_ERR_INVALID_ARG, "grid origin not finite");
+  double cells = (double)(g->nx - 1) * (g->ny - 1) * (g->nz - 1);
+  if (cells * g->nc > 2.0e9) return fail(LIGEN_ERR_UNSUPPORTED, "grid too large");
+  return LIGEN_OK;
+}
+
+int check_params(const ligen_params_t* p) {
+  if (!p) return fail(LIGEN_ERR_INVALID_ARG, "params is NULL");
+  if (p->restarts < 1 || p->restarts > 65536) return fail(LIGEN_ERR_INVALID_ARG, "restarts must be 1..65536");
+  if (p->n_rigid < 1 || p->n_rigid > LIGEN_N_RIGID) return fail(LIGEN_ERR_INVALID_ARG, "n_rigid must be 1..24");
+  if (p->torsion_step_deg < 2 || p->torsion_step_deg > 360 || 360 % p->torsion_step_deg != 0)
+    return fail(LIGEN_ERR_INVALID_ARG, "torsion_step_deg must divide 360 and be >= 2");
+  if (p->passes < 0 || p->passes > 1000) return fail(LIGEN_ERR_INVALID_ARG, "passes must be 0..1000");
+  if (p->top_k < 1 || p->top_k > p->restarts) return fail(LIGEN_ERR_INVALID_ARG, "top_k must be 1..restarts");
+  if (p->mode != 0) return fail(LIGEN_ERR_UNSUPPORTED, "mode %d not supported", p->mode);
+  if (!std::isfinite(p->jitter) || p->jitter < 0.f) return fail(LIGEN_ERR_INVALID_ARG, "jitter must be >= 0");
+  if (!std::isfinite(p->out_penalty)) return fail(LIGEN_ERR_INVALID_ARG, "out_penalty not finite");
+  return LIGEN_OK;
+}
+
+// ------------------------------------------------------ staged library --
+// Ligand arrays on the device: the caller's pointers, or workspace copies.
+struct LigandPlan {
+  size_t off_atom_off, off_xyz, off_type, off_bonds, off_rot_off, off_rot_edge;
+  bool host;
+};
+
+void plan_ligands(Arena& ar, const ligen_ligands_t* g, const LibShape& sh, bool host, LigandPlan* p) {
+  p->host = host;
+  if (!host) return;
+  p->off_atom_off = ar.take(4 * (size_t)(g->n_ligands + 1));
+  p->off_xyz = ar.take(12 * (size_t)sh.atoms);
+  p->off_type = ar.take((size_t)sh.atoms);
+  p->off_bonds = ar.take(8 * (size_t)(sh.atoms - g->n_ligands));
+  p->off_rot_off = ar.take(4 * (size_t)(g->n_ligands + 1));
+  p->off_rot_edge = ar.take(4 * (size_t)sh.rot);
+}
+
+int stage_ligands(const Arena& ar, const ligen_ligands_t* g, const LibShape& sh, const LigandPlan& p,
+                  cudaStream_t s, LigandsDev* d) {
+  d->L = g->n_ligands;
+  if (!p.host) {
+    d->atom_off = g->atom_off; d->xyz = g->xyz; d->type = g->type; d->bonds = g->bonds;
+    d->rot_off = g->rot_off; d->rot_edge = g->rot_edge;
+    return LIGEN_OK;
+  }
+  auto cp = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(ar.base + off, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  LG_CUDA(cp(p.off_atom_off, g->atom_off, 4 * (size_t)(g->n_ligands + 1)));
+  LG_CUDA(cp(p.off_xyz, g->xyz, 12 * (size_t)sh.atoms));
+  LG_CUDA(cp(p.off_type, g->type, (size_t)sh.atoms));
+  LG_CUDA(cp(p.off_bonds, g->bonds, 8 * (size_t)(sh.atoms - g->n_ligands)));
+  LG_CUDA(cp(p.off_rot_off, g->rot_off, 4 * (size_t)(g->n_ligands + 1)));
+  LG_CUDA(cp(p.off_rot_edge, g->rot_edge, 4 * (size_t)sh.rot));
+  d->atom_off = ar.at<int32_t>(p.off_atom_off);
+  d->xyz = ar.at<float>(p.off_xyz);
+  d->type = ar.at<uint8_t>(p.off_type);
+  d->bonds = ar.at<int32_t>(p.off_bonds);
+  d->rot_off = ar.at<int32_t>(p.off_rot_off);
+  d->rot_edge = ar.at<int32_t>(p.off_rot_edge);
+  return LIGEN_OK;
+}
+
+size_t grid_values_bytes(const ligen_grid_t* g) {
+  return (size_t)g->nx * g->ny * g->nz * g->nc * sizeof(float);
+}
+size_t grid_coef_bytes(const ligen_grid_t* g) {
+  return (size_t)(g->nx - 1) * (g->ny - 1) * (g->nz - 1) * g->nc * 32;
+}
+
+GridView make_view(const ligen_grid_t* g, const float* coef, float penalty) {
+  GridView v;
+  v.coef = coef;
+  v.cx = g->nx - 1; v.cy = g->ny - 1; v.cz = g->nz - 1;
+  v.nc = g->nc;
+  v.mx = (float)(g->nx - 1); v.my = (float)(g->ny - 1); v.mz = (float)(g->nz - 1);
+  v.penalty = penalty;
+  return v;
+}
+
+struct Timer {
+  float* out;
+  cudaStream_t s;
+  cudaEvent_t ev[LIGEN_N_STAGES + 1] = {};
+  int n = 0;
+  Timer(float* o, cudaStream_t st) : out(o), s(st) {
+    if (!out) return;
+    for (auto& e : ev) cudaEventCreate(&e);
+  }
+  void mark() {
+    if (out && n <= LIGEN_N_STAGES) cudaEventRecord(ev[n++], s);
+  }
+  void finish() {
+    if (!out) return;
+    while (n <= LIGEN_N_STAGES) mark();
+    cudaEventSynchronize(ev[LIGEN_N_STAGES]);
+    for (int i = 0; i < LIGEN_N_STAGES; ++i) cudaEventElapsedTime(&out[i], ev[i], ev[i + 1]);
+  }
+  ~Timer() {
+    if (!out) return;
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+int dock_restarts_per_cta(int R) {
+  int rpc = ((R + 7) / 8) * 8;
+  return rpc < 32 ? rpc : 32;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ligen_abi_version(void) { return LIGEN_ABI_VERSION; }
+
+const char* ligen_last_error(void) { return g_err.c_str(); }
+
+int ligen_release_workspaces(void) {
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  for (auto it = g_ws.begin(); it != g_ws.end();) {
+    if (it->first.first == dev) {
+      cudaStreamSynchronize(it->first.second);
+      cudaFree(it->second.base);
+      it = g_ws.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return LIGEN_OK;
+}
+
+int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, const ligen_params_t* params,
+                     float* out_poses, float* out_scores) {
+  g_err.clear();
+  int rc;
+  if ((rc = check_params(params)) != LIGEN_OK) return rc;
+  LibShape sh;
+  if ((rc = check_ligands(ligands, params->passes, &sh)) != LIGEN_OK) return rc;
+  if ((rc = check_grid(grid)) != LIGEN_OK) return rc;
+  if (!out_poses || !out_scores) return fail(LIGEN_ERR_INVALID_ARG, "out_poses and out_scores are required");
+  const int L = ligands->n_ligands;
+  if (L == 0) return LIGEN_OK;
+  cudaStream_t s = (cudaStream_t)params->stream;
+  const int R = params->restarts, K = params->top_k, P = params->passes;
+
+  const int lhost = space_of({ligands->atom_off, ligands->xyz, ligands->type, ligands->bonds,
+                              ligands->rot_off, ligands->rot_edge});
+  const int ghost = space_of({grid->data});
+  const int ohost = space_of({out_poses, out_scores, params->status, params->trace, params->top_restart});
+  if (lhost < 0) return fail(LIGEN_ERR_INVALID_ARG, "ligand arrays mix host and device memory");
+  if (ohost < 0) return fail(LIGEN_ERR_INVALID_ARG, "output arrays mix host and device memory");
+
+  const size_t pose_floats = (size_t)K * (7 * (size_t)L + sh.rot);
+  const size_t trace_elems = (size_t)R * sh.trace_len;
+  Arena ar;
+  LigandPlan lp;
+  plan_ligands(ar, ligands, sh, lhost == 1, &lp);
+  const size_t o_gval = ghost ? ar.take(grid_values_bytes(grid)) : 0;
+  const size_t o_coef = ar.take(grid_coef_bytes(grid));
+  const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
+  const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
+  const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
+  const size_t o_status = ar.take(4 * (size_t)L);
+  const size_t o_rs = ar.take(4 * (size_t)L * R);
+  const size_t o_rk = ar.take((size_t)L * R);
+  const size_t o_rc = ar.take((size_t)sh.rot * R);
+  size_t o_poses = 0, o_scores = 0, o_trace = 0, o_top = 0;
+  if (ohost == 1) {
+    o_poses = ar.take(4 * pose_floats);
+    o_scores = ar.take(4 * (size_t)L * K);
+    if (params->trace) o_trace = ar.take(2 * trace_elems);
+    if (params->top_restart) o_top = ar.take(4 * (size_t)L * K);
+  }
+  if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+
+  Timer tm(params->stage_ms, s);
+  tm.mark();
+  LigandsDev lig;
+  if ((rc = stage_ligands(ar, ligands, sh, lp, s, &lig)) != LIGEN_OK) return rc;
+  const float* gvals = (const float*)grid->data;
+  if (ghost) {
+    LG_CUDA(cudaMemcpyAsync(ar.base + o_gval, grid->data, grid_values_bytes(grid), cudaMemcpyHostToDevice, s));
+    gvals = ar.at<float>(o_gval);
+  }
+  tm.mark();
+  float* coef = ar.at<float>(o_coef);
+  LG_CUDA(launch_grid_prep(gvals, grid->nx, grid->ny, grid->nz, grid->nc, coef, s));
+  tm.mark();
+  Packed pk{};
+  pk.xc = ar.at<float4>(o_xc);
+  pk.binfo = ar.at<uchar4>(o_binfo);
+  pk.frag = ar.at<uint8_t>(o_frag);
+  pk.status = ar.at<int32_t>(o_status);
+  LG_CUDA(launch_pack(lig, grid->nc, pk, s));
+  tm.mark();
+
+  float* d_poses = ohost ? ar.at<float>(o_poses) : out_poses;
+  float* d_scores = ohost ? ar.at<float>(o_scores) : out_scores;
+  int16_t* d_trace = params->trace ? (ohost ? ar.at<int16_t>(o_trace) : params->trace) : nullptr;
+  int32_t* d_top = params->top_restart ? (ohost ? ar.at<int32_t>(o_top) : params->top_restart) : nullptr;
+
+  DockArgs da{};
+  da.lig = lig;
+  da.pk = pk;
+  da.grid = make_view(grid, coef, params->out_penalty);
+  const float h = grid->spacing;
+  const int np[3] = {grid->nx, grid->ny, grid->nz};
+  for (int k = 0; k < 3; ++k) {
+    da.origin[k] = grid->origin[k];
+    da.center[k] = (float)((double)grid->origin[k] + (double)h * (np[k] - 1) / 2.0);
+  }
+  da.inv_h = (float)(1.0 / (double)h);
+  da.jitter = params->jitter;
+  da.seed = params->seed;
+  da.R = R;
+  da.n_rigid = params->n_rigid;
+  da.step_deg = params->torsion_step_deg;
+  da.n_theta = 360 / params->torsion_step_deg;
+  da.passes = P;
+  da.rpc = dock_restarts_per_cta(R);
+  da.chunks = (R + da.rpc - 1) / da.rpc;
+  da.max_atoms = sh.max_atoms;
+  da.max_rot = sh.max_rot;
+  da.max_frag = (int)sh.max_frag;
+  da.res_score = ar.at<float>(o_rs);
+  da.res_k = ar.at<uint8_t>(o_rk);
+  da.res_cnt = ar.at<uint8_t>(o_rc);
+  da.trace = d_trace;
+  LG_CUDA(launch_dock(da, s));
+  tm.mark();
+
+  TopkArgs ta{};
+  ta.L = L; ta.R = R; ta.K = K; ta.step_deg = params->torsion_step_deg;
+  ta.rot_off = lig.rot_off;
+  ta.status = pk.status;
+  ta.res_score = da.res_score; ta.res_k = da.res_k; ta.res_cnt = da.res_cnt;
+  ta.seed = params->seed;
+  for (int k = 0; k < 3; ++k) ta.center[k] = da.center[k];
+  ta.jitter = params->jitter;
+  ta.out_poses = d_poses;
+  ta.out_scores = d_scores;
+  ta.top_restart = d_top;
+  LG_CUDA(launch_topk(ta, s));
+
+  const cudaMemcpyKind back = ohost ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (params->status) LG_CUDA(cudaMemcpyAsync(params->status, pk.status, 4 * (size_t)L, back, s));
+  if (ohost) {
+    LG_CUDA(cudaMemcpyAsync(out_poses, d_poses, 4 * pose_floats, back, s));
+    LG_CUDA(cudaMemcpyAsync(out_scores, d_scores, 4 * (size_t)L * K, back, s));
+    if (d_trace) LG_CUDA(cudaMemcpyAsync(params->trace, d_trace, 2 * trace_elems, back, s));
+    if (d_top) LG_CUDA(cudaMemcpyAsync(params->top_restart, d_top, 4 * (size_t)L * K, back, s));
+  }
+  tm.mark();
+  tm.finish();
+  if (ohost) LG_CUDA(cudaStreamSynchronize(s));
+  return LIGEN_OK;
+}
+
+int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, int32_t poses_per_ligand,
+                      const float* poses, float out_penalty, float* out_scores, void* stream) {
+  g_err.clear();
+  int rc;
+  LibShape sh;
+  if ((rc = check_ligands(ligands, 0, &sh)) != LIGEN_OK) return rc;
+  if ((rc = check_grid(grid)) != LIGEN_OK) return rc;
+  if (poses_per_ligand < 0) return fail(LIGEN_ERR_INVALID_ARG, "poses_per_ligand < 0");
+  if (!std::isfinite(out_penalty)) return fail(LIGEN_ERR_INVALID_ARG, "out_penalty not finite");
+  const int L = ligands->n_ligands;
+  if (L == 0 || poses_per_ligand == 0) return LIGEN_OK;
+  if (!poses || !out_scores) return fail(LIGEN_ERR_INVALID_ARG, "poses and out_scores are required");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int lhost = space_of({ligands->atom_off, ligands->xyz, ligands->type, ligands->bonds,
+                              ligands->rot_off, ligands->rot_edge});
+  const int ghost = space_of({grid->data});
+  const int ohost = space_of({poses, out_scores});
+  if (lhost < 0 || ohost < 0) return fail(LIGEN_ERR_INVALID_ARG, "arrays mix host and device memory");
+  const size_t pose_floats = (size_t)poses_per_ligand * (7 * (size_t)L + sh.rot);
+  const size_t nscores = (size_t)poses_per_ligand * L;
+  Arena ar;
+  LigandPlan lp;
+  plan_ligands(ar, ligands, sh, lhost == 1, &lp);
+  const size_t o_gval = ghost ? ar.take(grid_values_bytes(grid)) : 0;
+  const size_t o_coef = ar.take(grid_coef_bytes(grid));
+  const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
+  const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
+  const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
+  const size_t o_status = ar.take(4 * (size_t)L);
+  size_t o_poses = 0, o_scores = 0;
+  if (ohost) {
+    o_poses = ar.take(4 * pose_floats);
+    o_scores = ar.take(4 * nscores);
+  }
+  if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+  LigandsDev lig;
+  if ((rc = stage_ligands(ar, ligands, sh, lp, s, &lig)) != LIGEN_OK) return rc;
+  const float* gvals = (const float*)grid->data;
+  if (ghost) {
+    LG_CUDA(cudaMemcpyAsync(ar.base + o_gval, grid->data, grid_values_bytes(grid), cudaMemcpyHostToDevice, s));
+    gvals = ar.at<float>(o_gval);
+  }
+  const float* d_poses = poses;
+  if (ohost) {
+    LG_CUDA(cudaMemcpyAsync(ar.base + o_poses, poses, 4 * pose_floats, cudaMemcpyHostToDevice, s));
+    d_poses = ar.at<float>(o_poses);
+  }
+  float* coef = ar.at<float>(o_coef);
+  LG_CUDA(launch_grid_prep(gvals, grid->nx, grid->ny, grid->nz, grid->nc, coef, s));
+  Packed pk{};
+  pk.xc = ar.at<float4>(o_xc);
+  pk.binfo = ar.at<uchar4>(o_binfo);
+  pk.frag = ar.at<uint8_t>(o_frag);
+  pk.status = ar.at<int32_t>(o_status);
+  LG_CUDA(launch_pack(lig, grid->nc, pk, s));
+  ScoreArgs sa{};
+  sa.lig = lig;
+  sa.pk = pk;
+  sa.grid = make_view(grid, coef, out_penalty);
+  for (int k = 0; k < 3; ++k) sa.origin[k] = grid->origin[k];
+  sa.inv_h = (float)(1.0 / (double)grid->spacing);
+  sa.P = poses_per_ligand;
+  sa.max_atoms = sh.max_atoms;
+  sa.poses = d_poses;
+  sa.out_scores = ohost ? ar.at<float>(o_scores) : out_scores;
+  LG_CUDA(launch_score(sa, s));
+  if (ohost) {
+    LG_CUDA(cudaMemcpyAsync(out_scores, sa.out_scores, 4 * nscores, cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaStreamSynchronize(s));
+  }
+  return LIGEN_OK;
+}
+
+int ligen_pack_ligands(const ligen_ligands_t* ligands, int32_t n_channels, uint32_t* frag_bits, int32_t* axis,
+                       int32_t* bucket, int32_t* status, void* stream) {
+  g_err.clear();
+  int rc;
+  LibShape sh;
+  if ((rc = check_ligands(ligands, 0, &sh)) != LIGEN_OK) return rc;
+  if (n_channels < 1 || n_channels > LIGEN_MAX_CHANNELS)
+    return fail(LIGEN_ERR_INVALID_ARG, "n_channels must be 1..%d", LIGEN_MAX_CHANNELS);
+  const int L = ligands->n_ligands;
+  if (L == 0) return LIGEN_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int lhost = space_of({ligands->atom_off, ligands->xyz, ligands->type, ligands->bonds,
+                              ligands->rot_off, ligands->rot_edge});
+  const int ohost = space_of({frag_bits, axis, bucket, status});
+  if (lhost < 0 || ohost < 0) return fail(LIGEN_ERR_INVALID_ARG, "arrays mix host and device memory");
+  Arena ar;
+  LigandPlan lp;
+  plan_ligands(ar, ligands, sh, lhost == 1, &lp);
+  const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
+  const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
+  const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
+  const size_t o_status = ar.take(4 * (size_t)L);
+  const size_t o_bucket = ar.take(4 * (size_t)L);
+  const size_t o_bits = ar.take(32 * (size_t)sh.rot);
+  const size_t o_axis = ar.take(8 * (size_t)sh.rot);
+  if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+  LigandsDev lig;
+  if ((rc = stage_ligands(ar, ligands, sh, lp, s, &lig)) != LIGEN_OK) return rc;
+  Packed pk{};
+  pk.xc = ar.at<float4>(o_xc);
+  pk.binfo = ar.at<uchar4>(o_binfo);
+  pk.frag = ar.at<uint8_t>(o_frag);
+  pk.status = ar.at<int32_t>(o_status);
+  pk.bucket = ar.at<int32_t>(o_bucket);
+  pk.fbits = ar.at<uint32_t>(o_bits);
+  pk.axis = ar.at<int32_t>(o_axis);
+  LG_CUDA(launch_pack(lig, n_channels, pk, s));
+  const cudaMemcpyKind k = ohost ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (frag_bits && sh.rot) LG_CUDA(cudaMemcpyAsync(frag_bits, pk.fbits, 32 * (size_t)sh.rot, k, s));
+  if (axis && sh.rot) LG_CUDA(cudaMemcpyAsync(axis, pk.axis, 8 * (size_t)sh.rot, k, s));
+  if (bucket) LG_CUDA(cudaMemcpyAsync(bucket, pk.bucket, 4 * (size_t)L, k, s));
+  if (status) LG_CUDA(cudaMemcpyAsync(status, pk.status, 4 * (size_t)L, k, s));
+  if (ohost) LG_CUDA(cudaStreamSynchronize(s));
+  return LIGEN_OK;
+}
+
+int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t, int32_t* ws) {
+  g_err.clear();
+  if (max_atoms < 1 || max_atoms > LIGEN_MAX_ATOMS)
+    return fail(LIGEN_ERR_INVALID_ARG, "max_atoms must be 1..%d", LIGEN_MAX_ATOMS);
+  int dev = 0, nsm = 0, warp = 0, blocks = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  LG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  LG_CUDA(cudaDeviceGetAttribute(&warp, cudaDevAttrWarpSize, dev));
+  const int rpc = 32;
+  const size_t smem = dock_smem_bytes(max_atoms, LIGEN_MAX_ROT, LIGEN_MAX_ROT * (max_atoms / 2), rpc);
+  LG_CUDA(dock_occupancy(rpc, smem, &blocks));
+  const int threads = dock_threads_per_block(rpc);
+  if (b) *b = blocks;
+  if (sm) *sm = nsm;
+  if (t) *t = threads;
+  if (ws) *ws = warp;
+  return (int64_t)blocks * nsm * threads / warp;
+}
+
+int ligen_probe_gather(const float* records, int64_t n_records, int32_t loads_per_thread, float* sink,
+                       double* loads_done, float* ms_out, void* stream) {
+  g_err.clear();
+  if (!records || !sink || !ms_out || !loads_done) return fail(LIGEN_ERR_INVALID_ARG, "NULL argument");
+  if (n_records < 1 || n_records > (int64_t)UINT32_MAX) return fail(LIGEN_ERR_INVALID_ARG, "n_records out of range");
+  if ((uintptr_t)records % 32 != 0) return fail(LIGEN_ERR_INVALID_ARG, "records must be 32-byte aligned");
+  const int iters = loads_per_thread / probe_streams();
+  if (iters < 1) return fail(LIGEN_ERR_INVALID_ARG, "loads_per_thread must be >= %d", probe_streams());
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, nsm = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  LG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = nsm * (2048 / probe_threads());
+  cudaEvent_t e0, e1;
+  LG_CUDA(cudaEventCreate(&e0));
+  LG_CUDA(cudaEventCreate(&e1));
+  LG_CUDA(launch_probe(records, (uint32_t)n_records, 1, 7, sink, blocks, s));   // warm the cache
+  LG_CUDA(cudaEventRecord(e0, s));
+  LG_CUDA(launch_probe(records, (uint32_t)n_records, iters, 11, sink, blocks, s));
+  LG_CUDA(cudaEventRecord(e1, s));
+  LG_CUDA(cudaEventSynchronize(e1));
+  LG_CUDA(cudaEventElapsedTime(ms_out, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *loads_done = (double)blocks * probe_threads() * iters * probe_streams();
+  return LIGEN_OK;
+}
+
+}  // extern "C"

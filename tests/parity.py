@@ -1,0 +1,55 @@
+"""Helpers that compare the CUDA path with the oracle (test infrastructure).
+
+Tolerances:
+  * scores: |S_gpu - S_ref| <= 1e-5 * D with D = max(|S_ref|, sum_i |E_i|);
+  * decisions (chosen cube rotation, chosen torsion increment): equal at every
+    decision whose oracle top-2 gap exceeds 1e-4 * D; the first decision at or
+    under that gap and everything after it in the restart are not compared;
+  * fragment masks, axes, buckets, statuses: bit-exact.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SCORE_RTOL = 1e-5
+GAP_RTOL = 1e-4
+
+
+def ligand_trace(trace: np.ndarray, rot_off: np.ndarray, R: int, passes: int, l: int) -> np.ndarray:
+    n = np.diff(rot_off)
+    start = R * (l + passes * int(rot_off[l]))
+    D = 1 + passes * int(n[l])
+    return trace[start:start + R * D].reshape(R, D)
+
+
+def compare_restart(gpu_trace_row, ref: dict, j: int) -> tuple[int, bool]:
+    """Compare one restart's decisions; returns (decisions compared, all clean)."""
+    gap, dn, tr = ref["gap"][j], ref["dnorm"][j], ref["trace"][j]
+    for d in range(len(tr)):
+        if gap[d] <= GAP_RTOL * dn[d]:
+            return d, False
+        assert gpu_trace_row[d] == tr[d], f"decision {d}: gpu {gpu_trace_row[d]} oracle {tr[d]}"
+    return len(tr), True
+
+
+def check_dock_ligand(l: int, ref: dict, gpu_trace: np.ndarray, gpu_final: dict | None) -> dict:
+    """Per-restart parity of one ligand. gpu_final maps restart -> final score."""
+    stats = dict(decisions=0, restarts=0, clean=0, scores=0)
+    for j, r in enumerate(ref["restarts"]):
+        nd, clean = compare_restart(gpu_trace[r], ref, j)
+        stats["decisions"] += nd
+        stats["restarts"] += 1
+        if clean:
+            stats["clean"] += 1
+            if gpu_final is not None:
+                D = ref["dnorm"][j, -1]
+                g = gpu_final[int(r)]
+                assert abs(g - ref["score"][j]) <= SCORE_RTOL * D, (l, r, g, ref["score"][j], D)
+                stats["scores"] += 1
+    return stats
+
+
+def unpack_bits(words: np.ndarray, N: int) -> np.ndarray:
+    w = words.astype(np.uint32)
+    bits = (w[:, :, None] >> np.arange(32, dtype=np.uint32)[None, None, :]) & 1
+    return bits.reshape(len(words), -1)[:, :N].astype(bool)

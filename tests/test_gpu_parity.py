@@ -1,0 +1,290 @@
+"""CUDA path vs the oracle on the same seeded inputs (needs a GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lg():
+    import paper_2303_06150_gb300 as lg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return lg
+
+
+def _dev(lg, lib, grid, device="cuda"):
+    return (lg.Ligands.from_arrays(lib, device),
+            lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, device))
+
+
+def _bad_ligands():
+    xyz = np.array([[0, 0, 0], [1.5, 0, 0], [2, 1.4, 0], [3.5, 1.4, 0]], float)
+    good = dict(xyz=xyz, type=np.array([0, 1, 2, 3], np.uint8), bonds=np.array([[0, 1], [1, 2], [2, 3]]),
+                rot_edge=np.array([1], np.int32))
+    cycle = dict(good, bonds=np.array([[0, 1], [1, 2], [2, 0]]))
+    rng_id = dict(good, bonds=np.array([[0, 1], [1, 2], [2, 7]]))
+    rot_rng = dict(good, rot_edge=np.array([5], np.int32))
+    typ = dict(good, type=np.array([0, 1, 2, 9], np.uint8))
+    dup = dict(good, bonds=np.array([[0, 1], [0, 1], [2, 3]]))
+    return [good, cycle, rng_id, rot_rng, typ, dup], [0, 1, 1, 1, 1, 1]
+
+
+# ------------------------------------------------------------- packer ---
+@pytest.mark.parametrize("which", ["small32", "screen64", "screen64_shuffled", "bad"])
+def test_packer_bit_exact(lg, oracle_lib, small32, screen_sample, which):
+    if which == "small32":
+        _, lib, grid = small32
+        nc = 4
+    elif which == "bad":
+        ligs, _ = _bad_ligands()
+        lib = gen.from_ligands(ligs)
+        nc = 4
+    else:
+        _, lib, grid = screen_sample
+        nc = 8
+        if which.endswith("shuffled"):
+            lib = gen.shuffle_bonds(lib, 3)
+    L = lg.Ligands.from_arrays(lib, "cuda")
+    bits, axis, bucket, status = (t.cpu().numpy() for t in lg.pack_ligands(L, nc))
+    for l in range(lib.n_ligands):
+        g = lib.ligand(l)
+        lig = oracle_lib.OLigand(g["xyz"], g["type"], g["bonds"], g["rot_edge"])
+        bad = oracle_lib.validate(lig, nc)
+        assert status[l] == (-6 if bad else 0), l
+        assert bucket[l] == oracle_lib.bucket_id(lig.n_atoms, lig.n_rot)
+        if bad:
+            continue
+        _, mask, ax = oracle_lib.fragments(lig)
+        r0, r1 = lib.rot_off[l], lib.rot_off[l + 1]
+        assert np.array_equal(parity.unpack_bits(bits[r0:r1], lig.n_atoms), mask), l
+        assert np.array_equal(axis[r0:r1], ax), l
+
+
+# ------------------------------------------------------------ scoring ---
+def _random_poses(rng, lib, grid, K):
+    out = []
+    for l in range(lib.n_ligands):
+        n = lib.n_rot[l]
+        for _ in range(K):
+            q = rng.normal(size=4)
+            out.append(np.concatenate([grid.center + rng.uniform(-4, 4, 3), q, rng.uniform(-np.pi, np.pi, n)]))
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("which", ["small32", "screen64"])
+def test_score_poses_within_1e5(lg, oracle_lib, small32, screen_sample, which):
+    w, lib, grid = small32 if which == "small32" else screen_sample
+    K = 8
+    rng = np.random.default_rng(11)
+    poses = _random_poses(rng, lib, grid, K)
+    Ld, Gd = _dev(lg, lib, grid)
+    out = lg.score_poses(Ld, Gd, torch.tensor(poses, dtype=torch.float32, device="cuda"), K).cpu().numpy()
+    og = oracle_lib.OGrid.from_grid(grid)
+    off = lg.pose_offsets(lib.rot_off, K)
+    worst = 0.0
+    for l in range(lib.n_ligands):
+        lig = oracle_lib.OLigand.from_library(lib, l)
+        P = poses[off[l]:off[l + 1]].astype(np.float32).astype(np.float64).reshape(K, -1)
+        for p in range(K):
+            S, D, _ = oracle_lib.score_pose(lig, og, P[p], 5.0)
+            err = abs(out[l, p] - S) / D
+            worst = max(worst, err)
+            assert err <= parity.SCORE_RTOL, (l, p, out[l, p], S, D)
+    print(f"worst relative score error {worst:.2e}")
+
+
+# ------------------------------------------------------------ docking ---
+def _dock_and_compare(lg, oracle_lib, w, lib, grid, restarts=None, ligands=None, device="cuda"):
+    s = dict(w["search"])
+    R = s["restarts"]
+    Ld, Gd = _dev(lg, lib, grid, device)
+    res = lg.dock_batch(Ld, Gd, restarts=R, torsion_step_deg=s["torsion_step_deg"], passes=s["passes"],
+                        top_k=R, seed=s["seed"], n_rigid=s.get("n_rigid", 24), trace=True, top_restart=True)
+    if device == "cuda":
+        torch.cuda.synchronize()
+    trace = res.trace.cpu().numpy()
+    scores = res.scores.cpu().numpy()
+    top = res.top_restart.cpu().numpy()
+    status = res.status.cpu().numpy()
+    ref = oracle_lib.dock_library(lib, grid, s, ligands=ligands, restarts=restarts)
+    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    for r_ in ref:
+        l = r_["ligand"]
+        assert status[l] == 0
+        gt = parity.ligand_trace(trace, lib.rot_off, R, s["passes"], l)
+        final = {int(top[l, k]): float(scores[l, k]) for k in range(R)}
+        st = parity.check_dock_ligand(l, r_, gt, final)
+        for k in tot:
+            tot[k] += st[k]
+        # ranking: scores sorted, ties by restart index, every restart once
+        assert np.all(np.diff(scores[l]) <= 0)
+        assert sorted(top[l].tolist()) == list(range(R))
+    return res, ref, tot
+
+
+def test_dock_small32_matches_oracle(lg, oracle_lib, small32):
+    w, lib, grid = small32
+    _, _, tot = _dock_and_compare(lg, oracle_lib, w, lib, grid)
+    print(tot)
+    assert tot["clean"] >= 0.9 * tot["restarts"] and tot["scores"] > 0
+
+
+def test_dock_screen_sample_matches_oracle(lg, oracle_lib, screen_sample):
+    w, lib, grid = screen_sample
+    _, _, tot = _dock_and_compare(lg, oracle_lib, w, lib, grid, restarts=range(0, 24),
+                                  ligands=range(0, 64, 2))
+    print(tot)
+    assert tot["clean"] >= 0.8 * tot["restarts"] and tot["scores"] > 0
+
+
+def test_dock_top_k_and_poses(lg, oracle_lib, small32):
+    w, lib, grid = small32
+    s = w["search"]
+    Ld, Gd = _dev(lg, lib, grid)
+    full = lg.dock_batch(Ld, Gd, restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"],
+                         passes=s["passes"], top_k=s["restarts"], seed=s["seed"], top_restart=True)
+    kept = lg.dock_batch(Ld, Gd, restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"],
+                         passes=s["passes"], top_k=s["top_k"], seed=s["seed"], top_restart=True)
+    K = s["top_k"]
+    assert torch.equal(full.scores[:, :K], kept.scores)
+    assert torch.equal(full.top_restart[:, :K], kept.top_restart)
+    # kept poses re-score to the reported scores (same FP32 path, different route)
+    rescored = lg.score_poses(Ld, Gd, kept.poses, K).cpu().numpy()
+    sc = kept.scores.cpu().numpy()
+    og = oracle_lib.OGrid.from_grid(grid)
+    poses = kept.poses.cpu().numpy()
+    off = lg.pose_offsets(lib.rot_off, K)
+    ref = oracle_lib.dock_library(lib, grid, s)
+    for l in range(lib.n_ligands):
+        lig = oracle_lib.OLigand.from_library(lib, l)
+        P = poses[off[l]:off[l + 1]].reshape(K, -1)
+        for k in range(K):
+            S, D, _ = oracle_lib.score_pose(lig, og, P[k].astype(np.float64), 5.0)
+            assert abs(rescored[l, k] - sc[l, k]) <= 1e-5 * D
+            assert abs(S - sc[l, k]) <= 1e-5 * D
+            assert P[k, 3] >= 0 and abs(np.linalg.norm(P[k, 3:7]) - 1) < 1e-6
+            assert np.all(np.abs(P[k, 7:]) <= np.pi + 1e-6)
+        # where the oracle's top-K is separated by more than the gap tolerance,
+        # the kept restarts and their poses agree
+        r_ = ref[l]
+        if np.all(r_["gap"] > parity.GAP_RTOL * r_["dnorm"]):
+            os_ = np.sort(r_["score"])[::-1]
+            D = r_["dnorm"][:, -1].max()
+            for k in range(K):
+                sep = (k == 0 or os_[k - 1] - os_[k] > 1e-4 * D) and (os_[k] - os_[k + 1] > 1e-4 * D
+                                                                       if k + 1 < len(os_) else True)
+                if sep:
+                    assert kept.top_restart[l, k].item() == r_["top_restart"][k]
+                    np.testing.assert_allclose(P[k], r_["top_pose"][k], atol=2e-5)
+
+
+@pytest.mark.parametrize("variant", ["ragged_R13", "step5_chunked", "passes0", "rigid7", "step45"])
+def test_dock_search_variants(lg, oracle_lib, small32, variant):
+    w, lib, grid = small32
+    w = dict(w, search=dict(w["search"]))
+    s = w["search"]
+    if variant == "ragged_R13":
+        s["restarts"] = 13
+    elif variant == "step5_chunked":
+        s["torsion_step_deg"] = 5
+        s["passes"] = 1
+    elif variant == "passes0":
+        s["passes"] = 0
+    elif variant == "rigid7":
+        s["n_rigid"] = 7
+    elif variant == "step45":
+        s["torsion_step_deg"] = 45
+    sub = lib.subset(range(0, 32, 4))
+    _, _, tot = _dock_and_compare(lg, oracle_lib, w, sub, grid)
+    assert tot["restarts"] > 0 and tot["clean"] >= 0.8 * tot["restarts"]
+
+
+def test_dock_edge_ligands(lg, oracle_lib, small32):
+    """Single atom, rigid (no rotatable bond), terminal-bond torsion, 256 atoms / 32 bonds."""
+    w, lib, grid = small32
+    one = dict(xyz=np.zeros((1, 3)), type=np.zeros(1, np.uint8), bonds=np.zeros((0, 2), np.int32),
+               rot_edge=np.zeros(0, np.int32))
+    rigid = dict(lib.ligand(0), rot_edge=np.zeros(0, np.int32))
+    term = dict(lib.ligand(1))
+    term["rot_edge"] = np.array([len(term["bonds"]) - 1], np.int32)   # last atom is a leaf
+    big_lib = gen.make_library(dict(kind="uniform", n_ligands=1, n_atoms=(256, 256), n_rot=(32, 32),
+                                    n_types=4, seed=5))
+    big = big_lib.ligand(0)
+    ligs = [one, rigid, term, big]
+    sub = gen.from_ligands(ligs)
+    assert sub.n_atoms.max() == 256 and sub.n_rot.max() >= 24
+    w2 = dict(w, search=dict(w["search"], passes=1))
+    _, _, tot = _dock_and_compare(lg, oracle_lib, w2, sub, grid)
+    assert tot["restarts"] == 4 * w["search"]["restarts"]
+
+
+def test_bad_ligands_do_not_fail_the_batch(lg, small32):
+    w, lib, grid = small32
+    ligs, bad = _bad_ligands()
+    mixed = gen.from_ligands([lib.ligand(0)] + ligs + [lib.ligand(1)])
+    s = w["search"]
+    Ld, Gd = _dev(lg, mixed, grid)
+    res = lg.dock_batch(Ld, Gd, restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"],
+                        passes=s["passes"], top_k=s["top_k"], seed=s["seed"])
+    st = res.status.cpu().numpy()
+    assert st.tolist() == [0] + [-6 * b for b in bad] + [0]
+    sc = res.scores.cpu().numpy()
+    for i, b in enumerate([0] + bad + [0]):
+        assert np.all(np.isneginf(sc[i])) == bool(b)
+    # a good ligand docks the same alone and inside the mixed batch
+    alone = lg.dock_batch(*_dev(lg, lib.subset([0]), grid), restarts=s["restarts"],
+                          torsion_step_deg=s["torsion_step_deg"], passes=s["passes"], top_k=s["top_k"],
+                          seed=s["seed"])
+    assert torch.equal(alone.scores[0], res.scores[0])
+
+
+def test_empty_library(lg, small32):
+    w, lib, grid = small32
+    empty = gen.from_ligands([])
+    Ld, Gd = _dev(lg, empty, grid)
+    s = w["search"]
+    res = lg.dock_batch(Ld, Gd, restarts=8, torsion_step_deg=30, passes=2, top_k=4, seed=0)
+    assert res.scores.numel() == 0
+
+
+def test_host_memory_path_equals_device_path(lg, small32):
+    w, lib, grid = small32
+    s = w["search"]
+    kw = dict(restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"], passes=s["passes"],
+              top_k=s["top_k"], seed=s["seed"], trace=True)
+    dev = lg.dock_batch(*_dev(lg, lib, grid, "cuda"), **kw)
+    host = lg.dock_batch(lg.Ligands.from_arrays(lib, "cpu", pin=True),
+                         lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, "cpu", pin=True), **kw)
+    assert host.scores.device.type == "cpu"
+    assert torch.equal(dev.scores.cpu(), host.scores)
+    assert torch.equal(dev.poses.cpu(), host.poses)
+    assert torch.equal(dev.trace.cpu(), host.trace)
+
+
+def test_side_stream_and_determinism(lg, small32):
+    w, lib, grid = small32
+    s = w["search"]
+    Ld, Gd = _dev(lg, lib, grid)
+    kw = dict(restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"], passes=s["passes"],
+              top_k=s["top_k"], seed=s["seed"])
+    a = lg.dock_batch(Ld, Gd, **kw)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        b = lg.dock_batch(Ld, Gd, **kw)
+    st.synchronize()
+    assert torch.equal(a.scores, b.scores) and torch.equal(a.poses, b.poses)
+    c = lg.dock_batch(Ld, Gd, **dict(kw, seed=s["seed"] + 1))
+    assert not torch.equal(a.scores, c.scores)
+
+
+def test_bucket_size_eq1(lg):
+    for max_atoms in (32, 64, 128, 256):
+        f = lg.bucket_size(max_atoms)
+        assert f["b"] >= 1 and f["sm"] > 0 and f["ws"] == 32
+        assert f["l"] == f["b"] * f["sm"] * f["t"] // f["ws"]
+    assert lg.bucket_size(32)["b"] >= lg.bucket_size(256)["b"]
