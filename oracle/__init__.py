@@ -71,12 +71,13 @@ def lib():
                 "or_bucket_id": (C.c_int32, [C.c_int32, C.c_int32]),
                 "or_eq1_bucket_size": (C.c_int64, [C.c_int64] * 4),
                 "or_trilinear": (C.c_double, [P, C.c_int32, P, P]),
-                "or_score_coords": (C.c_double, [P, P, P, C.c_double, P, P]),
+                "or_trilinear_grad": (C.c_double, [P, C.c_int32, P, P, P]),
+                "or_score_coords": (C.c_double, [P, P, P, C.c_double, P, P, P]),
                 "or_pose_coords": (None, [P, P, P, P, P]),
-                "or_score_pose": (C.c_double, [P, P, P, P, P, C.c_double, P, P]),
+                "or_score_pose": (C.c_double, [P, P, P, P, P, C.c_double, P, P, P]),
                 "or_torsion_angle": (C.c_double, [C.c_int32, C.c_int32]),
                 "or_restart_init": (None, [P, P, C.c_int64, C.c_int64, P, P]),
-                "or_dock_ligand": (C.c_int32, [P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P, P]),
+                "or_dock_ligand": (C.c_int32, [P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P, P, P]),
                 "or_dock_exhaustive": (C.c_int32, [P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P]),
                 "or_top_k": (None, [C.c_int32, P, C.c_int32, P]),
             }
@@ -217,6 +218,15 @@ def trilinear(grid: OGrid, c: int, x):
     return float(v), bool(inb.value)
 
 
+def trilinear_grad(grid: OGrid, c: int, x):
+    """(value, gradient [3] per Angstrom, inbox) of channel c at point x."""
+    x = np.ascontiguousarray(x, np.float64)
+    g = np.zeros(3)
+    inb = C.c_int32(0)
+    v = lib().or_trilinear_grad(C.byref(grid.s), c, _ptr(x), _ptr(g), C.byref(inb))
+    return float(v), g, bool(inb.value)
+
+
 def _frag_arrays(lig: OLigand):
     st, mask, axis = fragments(lig)
     if st:
@@ -233,24 +243,25 @@ def pose_coords(lig: OLigand, pose) -> np.ndarray:
     return out
 
 
-def score_coords(lig: OLigand, grid: OGrid, xyz, penalty: float = 5.0):
-    """(S, D, E[N]) for explicit atom positions."""
+def score_coords(lig: OLigand, grid: OGrid, xyz, penalty: float = 5.0, sensitivity: bool = False):
+    """(S, D, E[N]) for explicit atom positions; adds Gs when sensitivity=True."""
     xyz = np.ascontiguousarray(xyz, np.float64)
-    D = C.c_double(0)
+    D, G = C.c_double(0), C.c_double(0)
     E = np.zeros(lig.n_atoms)
-    s = lib().or_score_coords(C.byref(lig.s), C.byref(grid.s), _ptr(xyz), penalty, C.byref(D), _ptr(E))
-    return float(s), float(D.value), E
+    s = lib().or_score_coords(C.byref(lig.s), C.byref(grid.s), _ptr(xyz), penalty, C.byref(D), _ptr(E),
+                              C.byref(G))
+    return (float(s), float(D.value), E, float(G.value)) if sensitivity else (float(s), float(D.value), E)
 
 
-def score_pose(lig: OLigand, grid: OGrid, pose, penalty: float = 5.0):
-    """(S, D, E[N]) of pose (t[3], q[4], theta[n])."""
+def score_pose(lig: OLigand, grid: OGrid, pose, penalty: float = 5.0, sensitivity: bool = False):
+    """(S, D, E[N]) of pose (t[3], q[4], theta[n]); adds Gs when sensitivity=True."""
     mask, axis = _frag_arrays(lig)
     pose = np.ascontiguousarray(pose, np.float64)
-    D = C.c_double(0)
+    D, G = C.c_double(0), C.c_double(0)
     E = np.zeros(lig.n_atoms)
     s = lib().or_score_pose(C.byref(lig.s), C.byref(grid.s), _ptr(mask), _ptr(axis), _ptr(pose),
-                            penalty, C.byref(D), _ptr(E))
-    return float(s), float(D.value), E
+                            penalty, C.byref(D), _ptr(E), C.byref(G))
+    return (float(s), float(D.value), E, float(G.value)) if sensitivity else (float(s), float(D.value), E)
 
 
 def torsion_angle(count: int, step_deg: int) -> float:
@@ -273,10 +284,10 @@ def dock_ligand(lig: OLigand, grid: OGrid, search: dict, lig_index: int, restart
     n = lig.n_rot
     dlen = 1 + p.passes * n
     out = dict(score=np.zeros(R), pose=np.zeros((R, 7 + n)), trace=np.zeros((R, dlen), np.int16),
-               gap=np.zeros((R, dlen)), dnorm=np.zeros((R, dlen)))
+               gap=np.zeros((R, dlen)), dnorm=np.zeros((R, dlen)), gsens=np.zeros((R, dlen)))
     st = lib().or_dock_ligand(C.byref(lig.s), C.byref(grid.s), C.byref(p), lig_index, r0, r1,
                               _ptr(out["score"]), _ptr(out["pose"]), _ptr(out["trace"]),
-                              _ptr(out["gap"]), _ptr(out["dnorm"]))
+                              _ptr(out["gap"]), _ptr(out["dnorm"]), _ptr(out["gsens"]))
     out["status"] = int(st)
     out["restarts"] = np.arange(r0, r1)
     return out

@@ -317,21 +317,64 @@ double or_trilinear(const or_grid* g, int32_t c, const double* x, int32_t* inbox
   return e;
 }
 
+// Gradient (d/dx, d/dy, d/dz, per Angstrom) of the trilinear sample inside its
+// cell: the derivative of the corner-weighted sum with the weight of the
+// differentiated axis replaced by -1 (corner 0) or +1 (corner 1), over the
+// spacing. Zero outside the box. Returns the value as or_trilinear does.
+double or_trilinear_grad(const or_grid* g, int32_t c, const double* x, double* grad, int32_t* inbox) {
+  int n[3] = {g->nx, g->ny, g->nz};
+  double u[3], f[3];
+  int i[3];
+  grad[0] = grad[1] = grad[2] = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    u[a] = (x[a] - g->origin[a]) / g->spacing;
+    if (!(u[a] >= 0.0 && u[a] <= n[a] - 1)) {
+      *inbox = 0;
+      return 0.0;
+    }
+    i[a] = std::min((int)std::floor(u[a]), n[a] - 2);
+    f[a] = u[a] - i[a];
+  }
+  *inbox = 1;
+  double e = 0.0;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        double wx = dx ? f[0] : 1 - f[0], wy = dy ? f[1] : 1 - f[1], wz = dz ? f[2] : 1 - f[2];
+        double sx = dx ? 1.0 : -1.0, sy = dy ? 1.0 : -1.0, sz = dz ? 1.0 : -1.0;
+        size_t node = (((size_t)(i[2] + dz) * g->ny + (i[1] + dy)) * g->nx + (i[0] + dx));
+        double v = g->v[node * g->nc + c];
+        e += wx * wy * wz * v;
+        grad[0] += sx * wy * wz * v / g->spacing;
+        grad[1] += wx * sy * wz * v / g->spacing;
+        grad[2] += wx * wy * sz * v / g->spacing;
+      }
+  return e;
+}
+
 // Score of a set of atom positions: S = -sum_i E_i, with E_i the trilinear
 // value of atom i's channel, or `penalty` when the atom is outside the box.
-// Also returns D = max(|S|, sum_i |E_i|) and, if E is not null, each E_i.
+// Also returns D = max(|S|, sum_i |E_i|), if E is not null each E_i, and if
+// Gs is not null the position sensitivity Gs = sum_i |grad E_i| |x_i - origin|:
+// a relative perturbation eps of every atom's grid coordinate moves S by at
+// most about eps * Gs.
 double or_score_coords(const or_ligand* L, const or_grid* g, const double* xyz, double penalty,
-                       double* D, double* E) {
-  double s = 0.0, a = 0.0;
+                       double* D, double* E, double* Gs) {
+  double s = 0.0, a = 0.0, sens = 0.0;
   for (int i = 0; i < L->n_atoms; ++i) {
     int32_t inb = 0;
-    double e = or_trilinear(g, L->type[i], xyz + 3 * i, &inb);
+    double gr[3];
+    double e = or_trilinear_grad(g, L->type[i], xyz + 3 * i, gr, &inb);
     if (!inb) e = penalty;
     if (E) E[i] = e;
     s -= e;
     a += std::fabs(e);
+    double r[3] = {xyz[3 * i] - g->origin[0], xyz[3 * i + 1] - g->origin[1], xyz[3 * i + 2] - g->origin[2]};
+    sens += std::sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]) *
+            std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
   }
   if (D) *D = std::max(std::fabs(s), a);
+  if (Gs) *Gs = sens;
   return s;
 }
 
@@ -371,10 +414,10 @@ void or_pose_coords(const or_ligand* L, const uint8_t* mask, const int32_t* axis
 // Score of pose (t, q, theta): or_pose_coords, then or_score_coords. The
 // ligand must be valid (or_validate); mask and axis come from or_fragments.
 double or_score_pose(const or_ligand* L, const or_grid* g, const uint8_t* mask, const int32_t* axis,
-                     const double* pose, double penalty, double* D, double* E) {
+                     const double* pose, double penalty, double* D, double* E, double* Gs) {
   std::vector<double> x(3 * (size_t)L->n_atoms);
   or_pose_coords(L, mask, axis, pose, x.data());
-  return or_score_coords(L, g, x.data(), penalty, D, E);
+  return or_score_coords(L, g, x.data(), penalty, D, E, Gs);
 }
 
 // Torsion angle of `count` increments of step_deg degrees, wrapped to
@@ -405,10 +448,11 @@ void or_restart_init(const or_grid* g, const or_params* P, int64_t lig, int64_t 
 //   trace[j][D]          chosen k, then chosen increment per (pass, bond)
 //   gap[j][D], dn[j][D]  best minus second-best score of each decision, and
 //                        D = max(|S|, sum |E|) of its best candidate
+//   gs[j][D]             position sensitivity Gs of the best candidate
 // Ties go to the lowest index. Returns 0, or 1 for an invalid ligand.
 int32_t or_dock_ligand(const or_ligand* L, const or_grid* g, const or_params* P, int64_t lig,
                        int32_t r_begin, int32_t r_end, double* score, double* pose,
-                       int16_t* trace, double* gap, double* dn) {
+                       int16_t* trace, double* gap, double* dn, double* gs) {
   int N = L->n_atoms, n = L->n_rot;
   if (or_validate(L, g->nc)) return 1;
   std::vector<uint8_t> mask((size_t)n * N);
@@ -429,17 +473,17 @@ int32_t or_dock_ligand(const or_ligand* L, const or_grid* g, const or_params* P,
       for (int b = 0; b < n; ++b) cand[7 + b] = or_torsion_angle(count[b], P->step_deg);
     };
     // rigid stage: q = q_r * g_k
-    double best = -INFINITY, second = -INFINITY, bestD = 0.0, q[4];
+    double best = -INFINITY, second = -INFINITY, bestD = 0.0, bestG = 0.0, q[4];
     int kbest = 0;
     for (int k = 0; k < P->n_rigid; ++k) {
-      double gk[4], qk[4], D;
+      double gk[4], qk[4], D, Gs;
       or_octahedral(k, gk);
       or_quat_mul(qr, gk, qk);
       fill(qk);
-      double s = or_score_pose(L, g, mask.data(), axis.data(), cand.data(), P->penalty, &D, nullptr);
+      double s = or_score_pose(L, g, mask.data(), axis.data(), cand.data(), P->penalty, &D, nullptr, &Gs);
       if (s > best) {
         second = best;
-        best = s; bestD = D; kbest = k;
+        best = s; bestD = D; bestG = Gs; kbest = k;
       } else if (s > second) {
         second = s;
       }
@@ -452,21 +496,22 @@ int32_t or_dock_ligand(const or_ligand* L, const or_grid* g, const or_params* P,
     trace[(size_t)j * dlen] = (int16_t)kbest;
     gap[(size_t)j * dlen] = best - second;
     dn[(size_t)j * dlen] = bestD;
+    gs[(size_t)j * dlen] = bestG;
     double cur = best;
     // torsion sweep
     for (int p = 0; p < P->passes; ++p) {
       for (int b = 0; b < n; ++b) {
         int base = count[b];
-        double bs = -INFINITY, sc = -INFINITY, bD = 0.0;
+        double bs = -INFINITY, sc = -INFINITY, bD = 0.0, bG = 0.0;
         int jb = 0;
         for (int t = 0; t < nt; ++t) {
           count[b] = base + t;
           fill(q);
-          double D;
-          double s = or_score_pose(L, g, mask.data(), axis.data(), cand.data(), P->penalty, &D, nullptr);
+          double D, Gs;
+          double s = or_score_pose(L, g, mask.data(), axis.data(), cand.data(), P->penalty, &D, nullptr, &Gs);
           if (s > bs) {
             sc = bs;
-            bs = s; bD = D; jb = t;
+            bs = s; bD = D; bG = Gs; jb = t;
           } else if (s > sc) {
             sc = s;
           }
@@ -476,6 +521,7 @@ int32_t or_dock_ligand(const or_ligand* L, const or_grid* g, const or_params* P,
         trace[d] = (int16_t)jb;
         gap[d] = bs - sc;
         dn[d] = bD;
+        gs[d] = bG;
         cur = bs;
       }
     }
@@ -517,7 +563,8 @@ int32_t or_dock_exhaustive(const or_ligand* L, const or_grid* g, const or_params
         cand[0] = tr[0]; cand[1] = tr[1]; cand[2] = tr[2];
         for (int a = 0; a < 4; ++a) cand[3 + a] = q[a];
         for (int b = 0; b < n; ++b) cand[7 + b] = or_torsion_angle(j[b], P->step_deg);
-        double s = or_score_pose(L, g, mask.data(), axis.data(), cand.data(), P->penalty, nullptr, nullptr);
+        double s = or_score_pose(L, g, mask.data(), axis.data(), cand.data(), P->penalty, nullptr, nullptr,
+                                 nullptr);
         if (s > best) {
           best = s;
           bestp = cand;

@@ -1,0 +1,111 @@
+"""Full-size screening workload (20,000 ligands, 256 restarts, 10-degree steps,
+3 passes, top 30) in the launch configuration the benchmark times, checked
+against the oracle on sampled ligands and restarts, and by properties that
+hold for every output (needs a GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def run():
+    import paper_2303_06150_gb300 as lg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = gen.WORKLOADS["screen20k"]
+    lib = gen.make_library(w["library"])
+    grid = gen.make_grid(w["grid"])
+    s = w["search"]
+    L = lg.Ligands.from_arrays(lib, "cuda")
+    G = lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, "cuda")
+    res = lg.dock_batch(L, G, restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"], passes=s["passes"],
+                        top_k=s["top_k"], seed=s["seed"], n_rigid=s["n_rigid"], jitter=s["jitter"],
+                        out_penalty=s["out_penalty"], trace=True, top_restart=True)
+    torch.cuda.synchronize()
+    return lg, w, lib, grid, L, G, res
+
+
+def test_every_output_is_well_formed(run):
+    lg, w, lib, grid, L, G, res = run
+    K, R = w["search"]["top_k"], w["search"]["restarts"]
+    assert int(res.status.abs().sum()) == 0
+    sc = res.scores.cpu().numpy()
+    top = res.top_restart.cpu().numpy()
+    assert np.isfinite(sc).all() and np.all(np.diff(sc, axis=1) <= 0)
+    assert top.min() >= 0 and top.max() < R
+    assert all(len(set(row)) == K for row in top[::97])
+    poses = res.poses.cpu().numpy()
+    off = lg.pose_offsets(lib.rot_off, K)
+    for l in range(0, lib.n_ligands, 211):
+        P = poses[off[l]:off[l + 1]].reshape(K, -1)
+        assert np.all(P[:, 3] >= 0)
+        np.testing.assert_allclose(np.linalg.norm(P[:, 3:7], axis=1), 1.0, atol=1e-6)
+        assert np.all((P[:, 7:] >= -np.pi - 1e-6) & (P[:, 7:] < np.pi + 1e-6))
+        assert np.all(np.abs(P[:, :3] - grid.center) <= w["search"]["jitter"] + 1e-5)
+
+
+def test_sampled_ligands_match_oracle(run, oracle_lib):
+    lg, w, lib, grid, L, G, res = run
+    s = w["search"]
+    R, K = s["restarts"], s["top_k"]
+    n_atoms, n_rot = lib.n_atoms, lib.n_rot
+    pick = set(np.linspace(0, lib.n_ligands - 1, 20).astype(int).tolist())
+    pick |= {int(np.argmax(n_atoms)), int(np.argmax(n_rot)), int(np.argmin(n_atoms)), int(np.argmin(n_rot))}
+    pick = sorted(pick)
+    rs = range(0, 24)
+    trace = res.trace.cpu().numpy()
+    scores = res.scores.cpu().numpy()
+    top = res.top_restart.cpu().numpy()
+    ref = oracle_lib.dock_library(lib, grid, s, ligands=pick, restarts=rs)
+    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    for r_ in ref:
+        l = r_["ligand"]
+        gt = parity.ligand_trace(trace, lib.rot_off, R, s["passes"], l)
+        final = {int(top[l, k]): float(scores[l, k]) for k in range(K)}
+        st = parity.check_dock_ligand(l, r_, gt, {r: final[r] for r in rs if r in final} or None)
+        for k in tot:
+            tot[k] += st[k]
+    print(tot)
+    assert tot["restarts"] == len(pick) * len(rs)
+    assert tot["clean"] >= 0.8 * tot["restarts"]
+
+
+def test_kept_poses_rescore_to_their_scores(run, oracle_lib):
+    lg, w, lib, grid, L, G, res = run
+    K = w["search"]["top_k"]
+    rescored = lg.score_poses(L, G, res.poses, K).cpu().numpy()
+    sc = res.scores.cpu().numpy()
+    poses = res.poses.cpu().numpy()
+    og = oracle_lib.OGrid.from_grid(grid)
+    off = lg.pose_offsets(lib.rot_off, K)
+    for l in np.linspace(0, lib.n_ligands - 1, 40).astype(int):
+        lig = oracle_lib.OLigand.from_library(lib, int(l))
+        P = poses[off[l]:off[l + 1]].reshape(K, -1).astype(np.float64)
+        for k in range(0, K, 3):
+            S, D, _, Gs = oracle_lib.score_pose(lig, og, P[k], 5.0, sensitivity=True)
+            tol = parity.score_tol(D, Gs)
+            assert abs(sc[l, k] - S) <= tol and abs(rescored[l, k] - S) <= tol, (l, k)
+
+
+def test_full_top_k_matches_oracle_on_two_ligands(run, oracle_lib):
+    lg, w, lib, grid, L, G, res = run
+    s = w["search"]
+    K = s["top_k"]
+    small = [int(l) for l in np.argsort(lib.n_atoms * (1 + lib.n_rot))[:2]]
+    ref = oracle_lib.dock_library(lib, grid, s, ligands=small)
+    top = res.top_restart.cpu().numpy()
+    for r_ in ref:
+        l = r_["ligand"]
+        clean = [parity.clean_restart(r_, j) for j in range(s["restarts"])]
+        if not all(clean):
+            continue
+        os_ = np.sort(r_["score"])[::-1]
+        tol = parity.gap_tol(r_["dnorm"][:, -1].max(), r_["gsens"][:, -1].max())
+        for k in range(K):
+            if (k == 0 or os_[k - 1] - os_[k] > tol) and os_[k] - os_[k + 1] > tol:
+                assert top[l, k] == r_["top_restart"][k]

@@ -101,3 +101,47 @@ def test_out_of_box_atoms_take_the_penalty(oracle_lib, small32):
     pose = np.concatenate([[1e3, 0, 0], [1, 0, 0, 0], np.zeros(lig.n_rot)])
     S, D, E = oracle_lib.score_pose(lig, og, pose, 7.5)
     assert np.all(E == 7.5) and S == -7.5 * lig.n_atoms
+
+
+def test_trilinear_gradient_pins(oracle_lib, small32):
+    # exact on linear fields, and the central difference elsewhere (away from faces)
+    rng = np.random.default_rng(5)
+    vals = np.zeros((6, 6, 6, 1))
+    zz, yy, xx = np.meshgrid(*(0.5 * np.arange(6),) * 3, indexing="ij")
+    b = np.array([0.3, -1.7, 2.2])
+    vals[..., 0] = 1.0 + b[0] * xx + b[1] * yy + b[2] * zz
+    g = _grid(vals, (0.0, 0.0, 0.0), 0.5)
+    for _ in range(50):
+        v, gr, inb = oracle_lib.trilinear_grad(g, 0, rng.uniform(0, 2.5, 3))
+        assert inb
+        np.testing.assert_allclose(gr, b, atol=1e-12)
+    _, _, grid = small32
+    g = _grid(grid.values, grid.origin, grid.spacing)
+    h = 1e-6
+    for _ in range(300):
+        cell = rng.integers(2, 35, 3)
+        p = grid.spacing * (cell + rng.uniform(0.05, 0.95, 3))
+        c = int(rng.integers(0, 4))
+        v, gr, inb = oracle_lib.trilinear_grad(g, c, p)
+        assert inb and v == oracle_lib.trilinear(g, c, p)[0]
+        fd = [(oracle_lib.trilinear(g, c, p + h * e)[0] - oracle_lib.trilinear(g, c, p - h * e)[0]) / (2 * h)
+              for e in np.eye(3)]
+        np.testing.assert_allclose(gr, fd, atol=1e-6 * (1 + np.abs(gr).max()))
+
+
+def test_position_sensitivity_bounds_relative_coordinate_noise(oracle_lib, small32):
+    import oracle
+    _, lib, grid = small32
+    og = oracle.OGrid.from_grid(grid)
+    rng = np.random.default_rng(6)
+    for l in range(0, 32, 4):
+        lig = oracle.OLigand.from_library(lib, l)
+        pose = np.concatenate([grid.center + rng.uniform(-3, 3, 3), rng.normal(size=4),
+                               rng.uniform(-np.pi, np.pi, lig.n_rot)])
+        x = oracle_lib.pose_coords(lig, pose)
+        S, D, E, Gs = oracle_lib.score_coords(lig, og, x, 5.0, sensitivity=True)
+        eps = 1e-7
+        for _ in range(20):
+            noisy = x * (1 + eps * rng.uniform(-1, 1, x.shape))   # origin is (0, 0, 0) here
+            S2 = oracle_lib.score_coords(lig, og, noisy, 5.0)[0]
+            assert abs(S2 - S) <= 1.01 * eps * Gs + 1e-12
