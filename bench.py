@@ -55,13 +55,38 @@ def dist_env():
     return rank, world, local
 
 
-def workload(n_ligands=None, rank=0):
+def shard_spec(rank: int, n_ligands=None) -> dict:
+    """Workload of one rank: the same recipe and size on every rank, with the
+    library and restart seeds offset by the rank, so each GPU docks its own
+    shard of a world_size-times larger library (weak scaling)."""
     import gen
-    w = gen.scaled(WORKLOAD, n_ligands) if n_ligands else gen.scaled(WORKLOAD, gen.WORKLOADS[WORKLOAD]
-                                                                         ["library"]["n_ligands"])
+    w = gen.scaled(WORKLOAD, n_ligands or gen.WORKLOADS[WORKLOAD]["library"]["n_ligands"])
     w["library"]["seed"] = int(w["library"]["seed"]) + 1000 * rank
     w["search"]["seed"] = int(w["search"]["seed"]) + 1000 * rank
+    return w
+
+
+def workload(n_ligands=None, rank=0):
+    import gen
+    w = shard_spec(rank, n_ligands)
     return w, gen.make_library(w["library"]), gen.make_grid(w["grid"])
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """Max of a per-rank number over all ranks (timing: the slowest rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ligands_per_rank: int, world: int, steps: int, ms_total_max: float) -> float:
+    """Whole-job ligands/s: every rank's ligands over the slowest rank's time."""
+    return ligands_per_rank * world * steps / (ms_total_max * 1e-3)
 
 
 def algorithmic_counts(lib, s, frag_sizes):
@@ -250,14 +275,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    ms_total = t0.elapsed_time(t1)
     stage = out.stage_ms.copy()
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(t0.elapsed_time(t1), world)
     ms_step = ms_total / args.steps
-    value = lib.n_ligands * world * args.steps / (ms_total * 1e-3)
+    value = job_throughput(lib.n_ligands, world, args.steps, ms_total)
 
     # roofline of the docking kernel: algorithmic bytes / its event-timed duration
     dock = float(np.mean(dock_ms))
@@ -304,14 +325,10 @@ def run_ours(args):
         e0 = time.perf_counter()
         for _ in range(args.steps):
             lg.dock_batch(Lh, Gh, out=outh, **kw)   # copies in, runs, copies out, synchronises
-        e_ms = (time.perf_counter() - e0) * 1e3
-        if world > 1:
-            tt = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
+        e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3, world)
         h2d = Lh.nbytes() + Gh.values.numel() * 4
         d2h = (outh.poses.numel() + outh.scores.numel() + outh.status.numel()) * 4
-        result["e2e"] = {"value": lib.n_ligands * world * args.steps / (e_ms * 1e-3), "unit": "ligands/s",
+        result["e2e"] = {"value": job_throughput(lib.n_ligands, world, args.steps, e_ms), "unit": "ligands/s",
                          "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                          "how": "ligen_dock_batch with pinned host inputs and outputs: H2D, kernels, D2H "
                                 "and a stream sync per step, host wall clock"}

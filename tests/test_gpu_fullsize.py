@@ -67,12 +67,12 @@ def test_sampled_ligands_match_oracle(run, oracle_lib):
         l = r_["ligand"]
         gt = parity.ligand_trace(trace, lib.rot_off, R, s["passes"], l)
         final = {int(top[l, k]): float(scores[l, k]) for k in range(K)}
-        st = parity.check_dock_ligand(l, r_, gt, {r: final[r] for r in rs if r in final} or None)
+        st = parity.check_dock_ligand(l, r_, gt, final)
         for k in tot:
             tot[k] += st[k]
     print(tot)
     assert tot["restarts"] == len(pick) * len(rs)
-    assert tot["clean"] >= 0.8 * tot["restarts"]
+    assert tot["clean"] >= 0.9 * tot["restarts"]
 
 
 def test_kept_poses_rescore_to_their_scores(run, oracle_lib):
@@ -99,13 +99,21 @@ def test_full_top_k_matches_oracle_on_two_ligands(run, oracle_lib):
     small = [int(l) for l in np.argsort(lib.n_atoms * (1 + lib.n_rot))[:2]]
     ref = oracle_lib.dock_library(lib, grid, s, ligands=small)
     top = res.top_restart.cpu().numpy()
+    trace = res.trace.cpu().numpy()
+    compared = 0
     for r_ in ref:
         l = r_["ligand"]
-        clean = [parity.clean_restart(r_, j) for j in range(s["restarts"])]
-        if not all(clean):
-            continue
-        os_ = np.sort(r_["score"])[::-1]
+        gt = parity.ligand_trace(trace, lib.rot_off, s["restarts"], s["passes"], l)
+        clean = np.array([parity.clean_restart(r_, j, gt[j]) for j in range(s["restarts"])])
+        sc = r_["score"]
+        os_ = np.sort(sc)[::-1]
         tol = parity.gap_tol(r_["dnorm"][:, -1].max(), r_["gsens"][:, -1].max())
         for k in range(K):
-            if (k == 0 or os_[k - 1] - os_[k] > tol) and os_[k] - os_[k + 1] > tol:
-                assert top[l, k] == r_["top_restart"][k]
+            # rank k is determined when it is separated from its neighbours and
+            # every restart that could reach it took only clear decisions
+            sep = (k == 0 or os_[k - 1] - os_[k] > tol) and os_[k] - os_[k + 1] > tol
+            if sep and clean[sc >= os_[k] - tol].all():
+                assert top[l, k] == r_["top_restart"][k], (l, k)
+                compared += 1
+    print("ranks compared", compared)
+    assert compared > 0

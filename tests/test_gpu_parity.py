@@ -139,7 +139,7 @@ def test_dock_screen_sample_matches_oracle(lg, oracle_lib, screen_sample):
     _, _, tot = _dock_and_compare(lg, oracle_lib, w, lib, grid, restarts=range(0, 24),
                                   ligands=range(0, 64, 2))
     print(tot)
-    assert tot["clean"] >= 0.8 * tot["restarts"] and tot["scores"] > 0
+    assert tot["clean"] >= 0.9 * tot["restarts"] and tot["scores"] > 0
 
 
 def test_dock_top_k_and_poses(lg, oracle_lib, small32):
@@ -147,7 +147,8 @@ def test_dock_top_k_and_poses(lg, oracle_lib, small32):
     s = w["search"]
     Ld, Gd = _dev(lg, lib, grid)
     full = lg.dock_batch(Ld, Gd, restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"],
-                         passes=s["passes"], top_k=s["restarts"], seed=s["seed"], top_restart=True)
+                         passes=s["passes"], top_k=s["restarts"], seed=s["seed"], top_restart=True, trace=True)
+    trace = full.trace.cpu().numpy()
     kept = lg.dock_batch(Ld, Gd, restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"],
                          passes=s["passes"], top_k=s["top_k"], seed=s["seed"], top_restart=True)
     K = s["top_k"]
@@ -172,7 +173,8 @@ def test_dock_top_k_and_poses(lg, oracle_lib, small32):
         # where the oracle's top-K is separated by more than the gap tolerance,
         # the kept restarts and their poses agree
         r_ = ref[l]
-        if all(parity.clean_restart(r_, j) for j in range(len(r_["score"]))):
+        gt = parity.ligand_trace(trace, lib.rot_off, s["restarts"], s["passes"], l)
+        if all(parity.clean_restart(r_, j, gt[j]) for j in range(len(r_["score"]))):
             os_ = np.sort(r_["score"])[::-1]
             tol = parity.gap_tol(r_["dnorm"][:, -1].max(), r_["gsens"][:, -1].max())
             for k in range(K):
@@ -201,7 +203,7 @@ def test_dock_search_variants(lg, oracle_lib, small32, variant):
         s["torsion_step_deg"] = 45
     sub = lib.subset(range(0, 32, 4))
     _, _, tot = _dock_and_compare(lg, oracle_lib, w, sub, grid)
-    assert tot["restarts"] > 0 and tot["clean"] >= 0.8 * tot["restarts"]
+    assert tot["restarts"] > 0 and tot["clean"] >= 0.9 * tot["restarts"]
 
 
 def test_dock_edge_ligands(lg, oracle_lib, small32):

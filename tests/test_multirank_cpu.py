@@ -1,0 +1,50 @@
+"""The benchmark's multi-rank path on CPU: two gloo ranks, no GPU.
+
+Every rank docks its own shard (distinct seeds, same size) with no data
+exchange; only the timing is reduced (max over ranks) and the job throughput
+counts every rank's ligands."""
+import os
+import socket
+import sys
+
+import numpy as np
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    import gen
+    w = bench.shard_spec(rank, 6)
+    lib = gen.make_library(w["library"])
+    local_ms = 100.0 + 50.0 * rank
+    out[rank] = dict(lseed=w["library"]["seed"], sseed=w["search"]["seed"], xyz0=lib.xyz[:5].tolist(),
+                     n=lib.n_ligands, max_ms=bench.max_over_ranks(local_ms, world),
+                     value=bench.job_throughput(lib.n_ligands, world, 3, bench.max_over_ranks(local_ms, world)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_and_time():
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    a, b = res[0], res[1]
+    assert a["n"] == b["n"] == 6
+    assert a["lseed"] != b["lseed"] and a["sseed"] != b["sseed"]
+    assert not np.allclose(a["xyz0"], b["xyz0"])         # different molecules per shard
+    assert a["max_ms"] == b["max_ms"] == 150.0             # slowest rank
+    assert abs(a["value"] - 6 * 2 * 3 / 0.150) < 1e-9       # all ranks' ligands / slowest time
