@@ -168,8 +168,12 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(samples_per_launch_full: int):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+def recorded_traffic():
+    """DRAM bytes of one full-size docking launch from the committed ncu capture.
+
+    The docking kernel's DRAM traffic is the grid's hot region read once, so it
+    does not grow with the number of ligands and a small-case capture cannot be
+    scaled; only a full-size capture of the unchanged kernel is reported."""
     path = os.path.join(ROOT, "profiles", "dock_kernel_traffic.txt")
     if not os.path.exists(path):
         return None, "no ncu summary"
@@ -179,12 +183,11 @@ def recorded_traffic(samples_per_launch_full: int):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
     if kv.get("kernel_source_hash") != kernel_source_hash():
-        return None, "kernel changed since the ncu capture"
+        return None, "kernel changed since the full-size ncu capture"
     try:
-        per_sample = float(kv["dram_bytes_per_launch"]) / float(kv["samples_per_launch"])
-    except (KeyError, ValueError, ZeroDivisionError):
-        return None, "summary incomplete"
-    return per_sample * samples_per_launch_full, kv.get("note", "")
+        return float(kv["dram_bytes_per_launch"]), kv.get("command", "")
+    except (KeyError, ValueError):
+        return None, "no full-size figure"
 
 
 def cpu_baseline(lib, grid, s, n_sample=96, threads=None):
@@ -287,7 +290,7 @@ def run_ours(args):
     # buffer the size of the grid's hot region (20 MB, L2-resident)
     probe_buf = torch.randn((20 << 20) // 32, 8, device=dev)
     probe = lg.probe_gather(probe_buf, 512)
-    traffic, traffic_note = recorded_traffic(samples_step)
+    traffic, traffic_note = recorded_traffic()
     roofline = {"bound": "l2", "achieved": achieved, "peak": probe["gbs"], "unit": "GB/s",
                 "frac": achieved / probe["gbs"], "traffic": traffic,
                 "kernel": "dock_kernel", "kernel_ms": dock,

@@ -303,9 +303,9 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
   LibShape sh;
   if ((rc = check_ligands(ligands, params->passes, &sh)) != LIGEN_OK) return rc;
   if ((rc = check_grid(grid)) != LIGEN_OK) return rc;
-  if (!out_poses || !out_scores) return fail(LIGEN_ERR_INVALID_ARG, "out_poses and out_scores are required");
   const int L = ligands->n_ligands;
-  if (L == 0) return LIGEN_OK;
+  if (L == 0) return LIGEN_OK;   // nothing to dock; outputs may be empty (NULL)
+  if (!out_poses || !out_scores) return fail(LIGEN_ERR_INVALID_ARG, "out_poses and out_scores are required");
   cudaStream_t s = (cudaStream_t)params->stream;
   const int R = params->restarts, K = params->top_k, P = params->passes;
 

@@ -98,6 +98,16 @@ def test_bad_shapes_rejected_on_host(abi, case, code):
     assert rc == code, abi.load().ligen_last_error()
 
 
+def test_empty_library_needs_no_outputs(abi):
+    lib = abi.load()
+    a = _arrays()
+    a["L"] = 0
+    vals = np.zeros((4, 4, 4, 2), np.float32)
+    rc = lib.ligen_dock_batch(C.byref(_lig_struct(abi, a)), C.byref(_grid(abi, vals)), C.byref(_params(abi)),
+                              None, None)
+    assert rc == 0
+
+
 def test_null_structs_rejected(abi):
     lib = abi.load()
     assert lib.ligen_dock_batch(None, None, None, None, None) == -1
