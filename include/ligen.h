@@ -153,6 +153,31 @@ typedef struct ligen_params {
 int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                      const ligen_params_t* params, float* out_poses, float* out_scores);
 
+/* ligen_dock_batch for callers that must not allocate device memory: a
+ * host framework whose caching allocator already owns the device's memory,
+ * or a latency-bound service that cannot take the device-wide
+ * synchronisation a cudaMalloc/cudaFree implies. The paper has no
+ * counterpart. Same arguments, search and outputs as ligen_dock_batch, with
+ * these differences:
+ *   - Its scratch is one file-scope device array of LIGEN_STATIC_SCRATCH_BYTES
+ *     inside this library (every GPU that loads the library holds it until
+ *     the process exits); the call itself allocates nothing. A batch whose
+ *     scratch would exceed it is rejected with LIGEN_ERR_UNSUPPORTED before
+ *     any device work. Scratch bytes, each term rounded up to 256: grid
+ *     cells (nx-1)(ny-1)(nz-1) * nc * 32; 16 per atom; 132 per rotatable
+ *     bond; 4 per ligand; restarts * (5 per ligand + 1 per rotatable bond).
+ *   - Ligands, grid and every output must be device memory.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array: two calls that overlap on the GPU (for
+ *     instance on different streams without ordering) race and corrupt each
+ *     other's results. Each call writes every scratch region before reading
+ *     it, so the contents left by the previous call do not matter.
+ *   - stage_ms is ignored. */
+#define LIGEN_STATIC_SCRATCH_BYTES (32u << 20)
+int ligen_dock_batch_static(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
+                            const ligen_params_t* params, float* out_poses, float* out_scores);
+
 /* Score given poses (same pose packing as ligen_dock_batch with K =
  * poses_per_ligand): out_scores[l][p] = S of pose p of ligand l, or
  * -INFINITY for an invalid ligand. `poses` and `out_scores` share one memory

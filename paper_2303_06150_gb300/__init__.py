@@ -5,9 +5,11 @@ ImportError when it has not been built. There is no fallback path.
 """
 from . import _abi
 from ._abi import LigenError, load
-from .api import (DockResult, Ligands, PocketGrid, abi_version, bucket_size, dock_batch, last_error,
+from .api import (DockResult, Ligands, PocketGrid, abi_version, bucket_size, dock_batch, dock_batch_static,
+                  last_error,
                   pack_ligands, pose_offsets, probe_gather, release_workspaces, score_poses)
 
 __all__ = ["DockResult", "Ligands", "LigenError", "PocketGrid", "abi_version", "bucket_size", "dock_batch",
+           "dock_batch_static",
            "last_error", "load", "pack_ligands", "pose_offsets", "probe_gather", "release_workspaces",
            "score_poses"]

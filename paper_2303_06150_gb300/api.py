@@ -150,6 +150,30 @@ def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_ste
     return out
 
 
+def dock_batch_static(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_step_deg: int, passes: int,
+                      top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
+                      out: DockResult | None = None) -> DockResult:
+    """ligen_dock_batch_static: ligen_dock_batch with the library's fixed
+    device scratch instead of an allocated workspace (device tensors only).
+
+    Pass `out` (device tensors allocated beforehand) to make the call itself
+    allocate nothing; without it the binding allocates the outputs with torch.
+    """
+    lib = _abi.load()
+    L, dev = ligands.n_ligands, ligands.device
+    n_sum = int(ligands.h_rot_off[-1])
+    if out is None:
+        out = DockResult(poses=_empty((top_k * (7 * L + n_sum),), torch.float32, dev),
+                         scores=_empty((L, top_k), torch.float32, dev),
+                         status=_empty((L,), torch.int32, dev), trace=None, top_restart=None, stage_ms=None)
+    p = ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
+                float(jitter), float(out_penalty), _stream_handle(dev), _ptr(out.status), _ptr(out.trace),
+                _ptr(out.top_restart), None)
+    check(lib.ligen_dock_batch_static(C.byref(ligands._s), C.byref(grid._s), C.byref(p), _ptr(out.poses),
+                                      _ptr(out.scores)))
+    return out
+
+
 def score_poses(ligands: Ligands, grid: PocketGrid, poses: torch.Tensor, poses_per_ligand: int,
                 out_penalty: float = 5.0, out: torch.Tensor | None = None) -> torch.Tensor:
     """ligen_score_poses: scores [L, poses_per_ligand] of packed poses."""

@@ -589,3 +589,138 @@ int ligen_probe_gather(const float* records, int64_t n_records, int32_t loads_pe
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------
+// ligen_dock_batch_static: the docking call for callers that must not
+// allocate device memory. Its scratch is the file-scope device array below,
+// of LIGEN_STATIC_SCRATCH_BYTES; every device that loads this library holds
+// it until the process exits. Host code reaches the array only through
+// cudaGetSymbolAddress (the array's name is a host-side stand-in, not a
+// device address); the address is looked up once per device, with that
+// device current, on the first call made on it.
+static __device__ __align__(256) unsigned char g_static_scratch[LIGEN_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+char* g_static_base[kMaxDevices] = {};
+
+int static_scratch_base(char** out) {
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(LIGEN_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    if (!p || (uintptr_t)p % 256 != 0) return fail(LIGEN_ERR_CUDA, "static scratch address not 256-byte aligned");
+    g_static_base[dev] = (char*)p;
+  }
+  *out = g_static_base[dev];
+  return LIGEN_OK;
+}
+
+}  // namespace
+
+extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
+                                       const ligen_params_t* params, float* out_poses, float* out_scores) {
+  g_err.clear();
+  int rc;
+  if ((rc = check_params(params)) != LIGEN_OK) return rc;
+  LibShape sh;
+  if ((rc = check_ligands(ligands, params->passes, &sh)) != LIGEN_OK) return rc;
+  if ((rc = check_grid(grid)) != LIGEN_OK) return rc;
+  const int L = ligands->n_ligands;
+  if (L == 0) return LIGEN_OK;
+  if (!out_poses || !out_scores) return fail(LIGEN_ERR_INVALID_ARG, "out_poses and out_scores are required");
+  const int R = params->restarts, K = params->top_k;
+
+  // Scratch plan (the same regions as the device path of ligen_dock_batch);
+  // checked against the static maximum before any device call.
+  Arena ar;
+  const size_t o_coef = ar.take(grid_coef_bytes(grid));
+  const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
+  const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
+  const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
+  const size_t o_status = ar.take(4 * (size_t)L);
+  const size_t o_rs = ar.take(4 * (size_t)L * R);
+  const size_t o_rk = ar.take((size_t)L * R);
+  const size_t o_rc = ar.take((size_t)sh.rot * R);
+  if (ar.used > (size_t)LIGEN_STATIC_SCRATCH_BYTES)
+    return fail(LIGEN_ERR_UNSUPPORTED,
+                "this batch needs %zu bytes of scratch; ligen_dock_batch_static has %zu "
+                "(use fewer ligands or restarts, a smaller grid, or ligen_dock_batch)",
+                ar.used, (size_t)LIGEN_STATIC_SCRATCH_BYTES);
+
+  const int lhost = space_of({ligands->atom_off, ligands->xyz, ligands->type, ligands->bonds,
+                              ligands->rot_off, ligands->rot_edge});
+  const int ghost = space_of({grid->data});
+  const int ohost = space_of({out_poses, out_scores, params->status, params->trace, params->top_restart});
+  if (lhost != 0 || ghost != 0 || ohost != 0)
+    return fail(LIGEN_ERR_INVALID_ARG, "ligen_dock_batch_static takes device memory only "
+                                       "(ligands, grid and outputs)");
+  if ((rc = static_scratch_base(&ar.base)) != LIGEN_OK) return rc;
+  cudaStream_t s = (cudaStream_t)params->stream;
+
+  // Every scratch region is written in full before it is read within this
+  // call, so nothing is cleared between calls.
+  LigandsDev lig;
+  lig.L = L;
+  lig.atom_off = ligands->atom_off; lig.xyz = ligands->xyz; lig.type = ligands->type;
+  lig.bonds = ligands->bonds; lig.rot_off = ligands->rot_off; lig.rot_edge = ligands->rot_edge;
+  float* coef = ar.at<float>(o_coef);
+  LG_CUDA(launch_grid_prep((const float*)grid->data, grid->nx, grid->ny, grid->nz, grid->nc, coef, s));
+  Packed pk{};
+  pk.xc = ar.at<float4>(o_xc);
+  pk.binfo = ar.at<uchar4>(o_binfo);
+  pk.frag = ar.at<uint8_t>(o_frag);
+  pk.status = ar.at<int32_t>(o_status);
+  LG_CUDA(launch_pack(lig, grid->nc, pk, s));
+
+  DockArgs da{};
+  da.lig = lig;
+  da.pk = pk;
+  da.grid = make_view(grid, coef, params->out_penalty);
+  const float h = grid->spacing;
+  const int np[3] = {grid->nx, grid->ny, grid->nz};
+  for (int k = 0; k < 3; ++k) {
+    da.origin[k] = grid->origin[k];
+    da.center[k] = (float)((double)grid->origin[k] + (double)h * (np[k] - 1) / 2.0);
+  }
+  da.inv_h = (float)(1.0 / (double)h);
+  da.jitter = params->jitter;
+  da.seed = params->seed;
+  da.R = R;
+  da.n_rigid = params->n_rigid;
+  da.step_deg = params->torsion_step_deg;
+  da.n_theta = 360 / params->torsion_step_deg;
+  da.passes = params->passes;
+  da.rpc = dock_restarts_per_cta(R);
+  da.chunks = (R + da.rpc - 1) / da.rpc;
+  da.max_atoms = sh.max_atoms;
+  da.max_rot = sh.max_rot;
+  da.max_frag = (int)sh.max_frag;
+  da.res_score = ar.at<float>(o_rs);
+  da.res_k = ar.at<uint8_t>(o_rk);
+  da.res_cnt = ar.at<uint8_t>(o_rc);
+  da.trace = params->trace;
+  LG_CUDA(launch_dock(da, s));
+
+  TopkArgs ta{};
+  ta.L = L; ta.R = R; ta.K = K; ta.step_deg = params->torsion_step_deg;
+  ta.rot_off = lig.rot_off;
+  ta.status = pk.status;
+  ta.res_score = da.res_score; ta.res_k = da.res_k; ta.res_cnt = da.res_cnt;
+  ta.seed = params->seed;
+  for (int k = 0; k < 3; ++k) ta.center[k] = da.center[k];
+  ta.jitter = params->jitter;
+  ta.out_poses = out_poses;
+  ta.out_scores = out_scores;
+  ta.top_restart = params->top_restart;
+  LG_CUDA(launch_topk(ta, s));
+  if (params->status)
+    LG_CUDA(cudaMemcpyAsync(params->status, pk.status, 4 * (size_t)L, cudaMemcpyDeviceToDevice, s));
+  return LIGEN_OK;
+}
