@@ -289,13 +289,13 @@ def run_ours(args):
     # gather ceiling: same access pattern (random 32-byte records), no pose math, on a
     # buffer the size of the grid's hot region (20 MB, L2-resident)
     probe_buf = torch.randn((20 << 20) // 32, 8, device=dev)
-    probe = lg.probe_gather(probe_buf, 512)
+    probe = max((lg.probe_gather(probe_buf, 512) for _ in range(5)), key=lambda p: p["gbs"])
     traffic, traffic_note = recorded_traffic()
     roofline = {"bound": "l2", "achieved": achieved, "peak": probe["gbs"], "unit": "GB/s",
                 "frac": achieved / probe["gbs"], "traffic": traffic,
                 "kernel": "dock_kernel", "kernel_ms": dock,
                 "peak_source": "measured in this run: ligen_probe_gather, random 32-byte records over a "
-                               "20 MB L2-resident buffer",
+                               "20 MB L2-resident buffer, best of 5",
                 "algorithmic_bytes": samples_step * BYTES_PER_SAMPLE,
                 "hbm_context": {"peak_gbs": 6801.0, "source": "MEASURED_PEAKS.json hbm_gbs",
                                 "frac_if_hbm": achieved / 6801.0},
