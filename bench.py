@@ -89,19 +89,24 @@ def job_throughput(ligands_per_rank: int, world: int, steps: int, ms_total_max: 
     return ligands_per_rank * world * steps / (ms_total_max * 1e-3)
 
 
-def algorithmic_counts(lib, s, frag_sizes):
+def algorithmic_counts(lib, s, moving_atoms):
     """Nominal poses and algorithmic atom samples of one step.
 
     poses   = R * (24 + P * n * n_theta) per ligand
-    samples = R * (24 * N + P * sum_b (n_theta - 1) * m_b) per ligand, with m_b
-              the size of bond b's moving fragment.
+    samples = R * (24 * N + P * sum_b (n_theta - 1) * (m_b - 1)) per ligand:
+              every atom of every rigid candidate, and in the sweep only the
+              atoms whose position changes (the moving side of bond b has m_b
+              atoms; its axis atom does not move) for the n_theta - 1
+              increments other than the current one. `moving_atoms` is
+              sum_b m_b over the library.
     """
     R, P = s["restarts"], s["passes"]
     nt = 360 // s["torsion_step_deg"]
     n = lib.n_rot.astype(np.int64)
     N = lib.n_atoms.astype(np.int64)
     poses = int(np.sum(R * (s.get("n_rigid", 24) + P * n * nt)))
-    samples = int(np.sum(R * s.get("n_rigid", 24) * N) + R * P * (nt - 1) * int(np.sum(frag_sizes)))
+    moved = int(moving_atoms) - int(n.sum())
+    samples = int(np.sum(R * s.get("n_rigid", 24) * N) + R * P * (nt - 1) * moved)
     return poses, samples
 
 
@@ -252,8 +257,8 @@ def run_ours(args):
     L = lg.Ligands.from_arrays(lib, dev)
     G = lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, dev)
     bits, _, _, _ = lg.pack_ligands(L, grid.dims[3])
-    frag_sizes = np.unpackbits(bits.cpu().numpy().view(np.uint8), bitorder="little").sum() if bits.numel() else 0
-    poses_step, samples_step = algorithmic_counts(lib, s, frag_sizes)
+    moving = np.unpackbits(bits.cpu().numpy().view(np.uint8), bitorder="little").sum() if bits.numel() else 0
+    poses_step, samples_step = algorithmic_counts(lib, s, moving)
     out = lg.dock_batch(L, G, stage_ms=True, **kw)        # allocates outputs and the workspace
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > L2: written between steps
     for _ in range(args.warmup):

@@ -208,15 +208,16 @@ int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t
 
 /* Measurement utility (the paper has no counterpart): the achievable rate of
  * the docking kernel's memory access pattern on this device. Every thread of
- * a full-device launch makes `loads_per_thread` aligned 32-byte loads from
- * uniformly random records of `records` (DEVICE, n_records * 8 floats,
- * 32-byte aligned) and discards the values (`sink`, DEVICE, 1 float, is
- * written only to keep the loads alive). *loads_done receives the number of
- * 32-byte loads made and *ms_out their device time (CUDA events on `stream`;
- * the call synchronises). A buffer that fits in L2 gives the L2 gather
- * ceiling. Returns LIGEN_OK or an error code. */
-int ligen_probe_gather(const float* records, int64_t n_records, int32_t loads_per_thread, float* sink,
-                       double* loads_done, float* ms_out, void* stream);
+ * a full-device launch makes `loads_per_thread` aligned loads of
+ * `bytes_per_load` (4, 8, 16 or 32) bytes, each from the start of a uniformly
+ * random 32-byte record of `records` (DEVICE, n_records * 8 floats, 32-byte
+ * aligned), and discards the values (`sink`, DEVICE, 1 float, is written
+ * only to keep the loads alive). *loads_done receives the number of loads
+ * made and *ms_out their device time (CUDA events on `stream`; the call
+ * synchronises). With 32-byte loads over a buffer that fits in L2 this is
+ * the docking kernel's gather ceiling. Returns LIGEN_OK or an error code. */
+int ligen_probe_gather(const float* records, int64_t n_records, int32_t bytes_per_load, int32_t loads_per_thread,
+                       float* sink, double* loads_done, float* ms_out, void* stream);
 
 /* Release every cached workspace of the calling thread's current device. */
 int ligen_release_workspaces(void);

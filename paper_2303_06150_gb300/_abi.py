@@ -50,7 +50,7 @@ SIGNATURES = {
     "ligen_score_poses": (C.c_int, [P, P, C.c_int32, P, C.c_float, P, P]),
     "ligen_pack_ligands": (C.c_int, [P, C.c_int32, P, P, P, P, P]),
     "ligen_bucket_size": (C.c_int64, [C.c_int32, P, P, P, P]),
-    "ligen_probe_gather": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P, P]),
+    "ligen_probe_gather": (C.c_int, [P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P]),
     "ligen_release_workspaces": (C.c_int, []),
     "ligen_last_error": (C.c_char_p, []),
     "ligen_abi_version": (C.c_int, []),

@@ -208,16 +208,17 @@ def bucket_size(max_atoms: int) -> dict:
     return dict(l=int(l), b=b.value, sm=sm.value, t=t.value, ws=ws.value)
 
 
-def probe_gather(records: torch.Tensor, loads_per_thread: int = 256) -> dict:
-    """ligen_probe_gather: random 32-byte-record load rate over `records` (device, [n, 8] float32)."""
+def probe_gather(records: torch.Tensor, loads_per_thread: int = 256, bytes_per_load: int = 32) -> dict:
+    """ligen_probe_gather: random-record load rate over `records` (device, [n, 8] float32)."""
     lib = _abi.load()
     assert records.is_cuda and records.dtype == torch.float32 and records.shape[-1] == 8
     sink = torch.zeros(1, dtype=torch.float32, device=records.device)
     ms = C.c_float()
     loads = C.c_double()
-    check(lib.ligen_probe_gather(_ptr(records), records.numel() // 8, loads_per_thread, _ptr(sink),
-                                 C.byref(loads), C.byref(ms), _stream_handle(records.device)))
-    return dict(loads=loads.value, ms=ms.value, gbs=loads.value * 32 / (ms.value * 1e-3) / 1e9)
+    check(lib.ligen_probe_gather(_ptr(records), records.numel() // 8, bytes_per_load, loads_per_thread,
+                                 _ptr(sink), C.byref(loads), C.byref(ms), _stream_handle(records.device)))
+    return dict(loads=loads.value, ms=ms.value, loads_per_s=loads.value / (ms.value * 1e-3),
+                gbs=loads.value * bytes_per_load / (ms.value * 1e-3) / 1e9)
 
 
 def release_workspaces() -> None:

@@ -118,8 +118,15 @@ __device__ __forceinline__ void torsion_cs(int j, int step_deg, float* c, float*
 // axz fx fz + ayz fy fz + axyz fx fy fz with f the position inside the cell.
 // One 32-byte record per (cell, channel) makes one sample one aligned 32-byte
 // load (one L2 sector) instead of eight scattered corner loads.
+//
+// Records are channel-major, [c][iz][iy][ix][8]. With the channel innermost
+// instead, all lanes sampling atoms of one type would hit the same 32-byte
+// position inside their 128-byte lines: measured on GB300, such 256-bit
+// gathers run at two thirds of the rate of gathers at mixed positions (the
+// L1 data banks serve one position per cycle). Channel-major puts the
+// position at ix mod 4, which varies from lane to lane.
 struct GridView {
-  const float* coef;   // [(cz*cy + iy)*cx + ix][nc][8], 256-byte aligned
+  const float* coef;   // [c][(iz*cy + iy)*cx + ix][8], 256-byte aligned
   int cx, cy, cz;      // cells per axis (points - 1)
   int nc;
   float mx, my, mz;    // points - 1 per axis, as float: upper box bound in grid units
@@ -147,7 +154,7 @@ __device__ __forceinline__ float grid_sample(const GridView& g, float ux, float 
     float fz = fminf(floorf(uz), g.mz - 1.f);
     int ix = (int)fx, iy = (int)fy, iz = (int)fz;
     float dx = ux - fx, dy = uy - fy, dz = uz - fz;
-    const float* rec = g.coef + ((size_t)((iz * g.cy + iy) * g.cx + ix) * g.nc + c) * 8;
+    const float* rec = g.coef + ((size_t)c * g.cz * g.cy * g.cx + (size_t)((iz * g.cy + iy) * g.cx + ix)) * 8;
     float a[8];
     ld_global_v8(rec, a);
     float t1 = fmaf(dz, a[7], a[4]);

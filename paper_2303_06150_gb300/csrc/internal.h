@@ -88,8 +88,8 @@ int dock_threads_per_block(int rpc);
 cudaError_t dock_occupancy(int rpc, size_t smem, int* blocks_per_sm);
 cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s);
-cudaError_t launch_probe(const float* rec, uint32_t n_rec, int iters, uint64_t seed, float* sink, int blocks,
-                         cudaStream_t s);
+cudaError_t launch_probe(const float* rec, uint32_t n_rec, int bytes, int iters, uint64_t seed, float* sink,
+                         int blocks, cudaStream_t s);
 int probe_streams();
 int probe_threads();
 

@@ -1,7 +1,8 @@
 // Grid preparation: node values [z][y][x][c] -> per-(cell, channel) records
-// of the 8 coefficients of the cell's trilinear polynomial (see GridView).
-// One thread per (cell, channel); consecutive threads read consecutive
-// channels of the same corners and write consecutive 32-byte records.
+// of the 8 coefficients of the cell's trilinear polynomial, stored
+// channel-major (see GridView). One thread per (cell, channel); consecutive
+// threads read consecutive channels of the same corners (coalesced reads)
+// and write 32-byte records nc records apart.
 #include "internal.h"
 
 namespace ligen {
@@ -33,7 +34,8 @@ __global__ void grid_prep_kernel(const float* __restrict__ v, int nx, int ny, in
     hi.y = (float)(c101 - c100 - c001 + c000);            // axz
     hi.z = (float)(c011 - c010 - c001 + c000);            // ayz
     hi.w = (float)(c111 - c110 - c101 - c011 + c100 + c010 + c001 - c000);  // axyz
-    float4* rec = reinterpret_cast<float4*>(coef + t * 8);
+    const size_t cells = (size_t)cx * cy * cz;
+    float4* rec = reinterpret_cast<float4*>(coef + ((size_t)c * cells + t / nc) * 8);
     rec[0] = lo;
     rec[1] = hi;
   }

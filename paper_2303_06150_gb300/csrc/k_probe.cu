@@ -1,5 +1,5 @@
-// Gather-ceiling probe: random 32-byte record loads from a buffer, with no
-// pose arithmetic. It measures the achievable rate of the docking kernel's
+// Gather-ceiling probe: loads from uniformly random 32-byte records of a
+// buffer (4, 8, 16 or all 32 bytes of each), with no pose arithmetic. It measures the achievable rate of the docking kernel's
 // access pattern (one aligned 256-bit load per atom sample) on this device,
 // which is the denominator of the docking kernel's roofline. The paper has
 // no counterpart; this is a measurement utility.
@@ -12,6 +12,25 @@ namespace {
 constexpr int kProbeThreads = 256;
 constexpr int kProbeStreams = 8;   // independent loads in flight per thread
 
+template <int BYTES>
+__device__ __forceinline__ float probe_load(const float* p) {
+  if constexpr (BYTES == 32) {
+    float v[8];
+    ld_global_v8(p, v);
+    return (v[0] + v[1]) + (v[2] + v[3]) + (v[4] + v[5]) + (v[6] + v[7]);
+  } else if constexpr (BYTES == 16) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return (v.x + v.y) + (v.z + v.w);
+  } else if constexpr (BYTES == 8) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return v.x + v.y;
+  } else {
+    return __ldg(p);
+  }
+}
+
+// Each load reads BYTES bytes at the start of a uniformly random 32-byte record.
+template <int BYTES>
 __global__ void __launch_bounds__(kProbeThreads) probe_kernel(const float* __restrict__ rec, uint32_t n_rec,
                                                               int iters, uint64_t seed, float* sink) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -24,9 +43,7 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(const float* __res
     for (int s = 0; s < kProbeStreams; ++s) {
       x[s] ^= x[s] << 13; x[s] ^= x[s] >> 17; x[s] ^= x[s] << 5;   // xorshift32
       const uint32_t idx = __umulhi(x[s], n_rec);
-      float v[8];
-      ld_global_v8(rec + (size_t)idx * 8, v);
-      acc += (v[0] + v[1]) + (v[2] + v[3]) + (v[4] + v[5]) + (v[6] + v[7]);
+      acc += probe_load<BYTES>(rec + (size_t)idx * 8);
     }
   }
   if (acc == 1.2345e-30f) sink[0] = acc;   // keeps the loads alive
@@ -36,9 +53,14 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(const float* __res
 
 int probe_streams() { return kProbeStreams; }
 
-cudaError_t launch_probe(const float* rec, uint32_t n_rec, int iters, uint64_t seed, float* sink, int blocks,
-                         cudaStream_t s) {
-  probe_kernel<<<blocks, kProbeThreads, 0, s>>>(rec, n_rec, iters, seed, sink);
+cudaError_t launch_probe(const float* rec, uint32_t n_rec, int bytes, int iters, uint64_t seed, float* sink,
+                         int blocks, cudaStream_t s) {
+  switch (bytes) {
+    case 32: probe_kernel<32><<<blocks, kProbeThreads, 0, s>>>(rec, n_rec, iters, seed, sink); break;
+    case 16: probe_kernel<16><<<blocks, kProbeThreads, 0, s>>>(rec, n_rec, iters, seed, sink); break;
+    case 8: probe_kernel<8><<<blocks, kProbeThreads, 0, s>>>(rec, n_rec, iters, seed, sink); break;
+    default: probe_kernel<4><<<blocks, kProbeThreads, 0, s>>>(rec, n_rec, iters, seed, sink); break;
+  }
   return cudaGetLastError();
 }
 

@@ -560,10 +560,12 @@ int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t
   return (int64_t)blocks * nsm * threads / warp;
 }
 
-int ligen_probe_gather(const float* records, int64_t n_records, int32_t loads_per_thread, float* sink,
-                       double* loads_done, float* ms_out, void* stream) {
+int ligen_probe_gather(const float* records, int64_t n_records, int32_t bytes_per_load, int32_t loads_per_thread,
+                       float* sink, double* loads_done, float* ms_out, void* stream) {
   g_err.clear();
   if (!records || !sink || !ms_out || !loads_done) return fail(LIGEN_ERR_INVALID_ARG, "NULL argument");
+  if (bytes_per_load != 4 && bytes_per_load != 8 && bytes_per_load != 16 && bytes_per_load != 32)
+    return fail(LIGEN_ERR_INVALID_ARG, "bytes_per_load must be 4, 8, 16 or 32");
   if (n_records < 1 || n_records > (int64_t)UINT32_MAX) return fail(LIGEN_ERR_INVALID_ARG, "n_records out of range");
   if ((uintptr_t)records % 32 != 0) return fail(LIGEN_ERR_INVALID_ARG, "records must be 32-byte aligned");
   const int iters = loads_per_thread / probe_streams();
@@ -576,9 +578,9 @@ int ligen_probe_gather(const float* records, int64_t n_records, int32_t loads_pe
   cudaEvent_t e0, e1;
   LG_CUDA(cudaEventCreate(&e0));
   LG_CUDA(cudaEventCreate(&e1));
-  LG_CUDA(launch_probe(records, (uint32_t)n_records, 1, 7, sink, blocks, s));   // warm the cache
+  LG_CUDA(launch_probe(records, (uint32_t)n_records, bytes_per_load, 1, 7, sink, blocks, s));   // warm the cache
   LG_CUDA(cudaEventRecord(e0, s));
-  LG_CUDA(launch_probe(records, (uint32_t)n_records, iters, 11, sink, blocks, s));
+  LG_CUDA(launch_probe(records, (uint32_t)n_records, bytes_per_load, iters, 11, sink, blocks, s));
   LG_CUDA(cudaEventRecord(e1, s));
   LG_CUDA(cudaEventSynchronize(e1));
   LG_CUDA(cudaEventElapsedTime(ms_out, e0, e1));
