@@ -9,7 +9,6 @@
 namespace ligen {
 
 constexpr int kFragStride = 128;   // bytes per rotatable bond in the moving-atom lists
-constexpr int kLanesPerRestart = 4;
 
 // Device-resident ligand library (CSR, see ligen_ligands_t).
 struct LigandsDev {
@@ -43,8 +42,13 @@ struct DockArgs {
   float jitter;
   uint64_t seed;
   int R, n_rigid, step_deg, n_theta, passes;
-  int rpc;            // restarts per CTA
-  int chunks;         // CTAs per ligand
+  int lanes;          // G: lanes per restart (2, 4 or 8)
+  int rpc;            // restarts per work item (a multiple of 32 / lanes)
+  int chunks;         // work items per ligand: ceil(R / rpc)
+  const int32_t* list;  // ligands to dock (NULL: 0 .. n_items / chunks - 1)
+  int n_items;        // work items: (list length or L) * chunks
+  int* queue;         // persistent mode: device counter of taken items (zeroed
+                      // before the launch); NULL: one CTA per item
   int max_atoms, max_rot, max_frag;   // shared-memory carve-up bounds
   float* res_score;   // [L][R]
   uint8_t* res_k;     // [L][R]
@@ -83,9 +87,10 @@ cudaError_t launch_grid_prep(const float* values, int nx, int ny, int nz, int nc
                              cudaStream_t s);
 cudaError_t launch_pack(const LigandsDev& lig, int nc, const Packed& out, cudaStream_t s);
 size_t dock_smem_bytes(int max_atoms, int max_rot, int max_frag, int rpc);
-cudaError_t launch_dock(const DockArgs& a, cudaStream_t s);
-int dock_threads_per_block(int rpc);
-cudaError_t dock_occupancy(int rpc, size_t smem, int* blocks_per_sm);
+bool dock_lanes_supported(int lanes);
+// grid_ctas: CTAs of a persistent launch (ignored when a.queue is NULL).
+cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s);
+cudaError_t dock_occupancy(int lanes, int n_theta, int rpc, size_t smem, int* blocks_per_sm);
 cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s);
 cudaError_t launch_probe(const float* rec, uint32_t n_rec, int bytes, int iters, uint64_t seed, float* sink,

@@ -1,27 +1,32 @@
 // Docking kernel: restarts -> rigid stage -> torsion sweeps -> final score.
 //
-// Mapping. A CTA docks one ligand over `rpc` consecutive restarts; each
-// restart is owned by a group of G = 4 adjacent lanes, so one warp runs 8
-// restarts of the same ligand in lockstep (identical atom counts, bonds and
-// fragment sizes: no divergence). Inside a group the lanes split the
-// *candidates* of a stage (cube rotations in the rigid stage, torsion
+// Mapping. A work item is one ligand over `rpc` consecutive restarts; each
+// restart is owned by a group of G adjacent lanes (G = 2, 4 or 8), so a warp
+// runs 32/G restarts of the same ligand in lockstep (identical atom counts,
+// bonds and fragment sizes: no divergence). Inside a group the lanes split
+// the *candidates* of a stage (cube rotations in the rigid stage, torsion
 // increments in the sweep) and each lane sums its candidates' atom terms on
-// its own, so a stage needs no per-candidate reduction, only a 2-step
-// shuffle argmax across the group.
+// its own, so a stage needs no per-candidate reduction, only a log2(G)-step
+// shuffle argmax across the group. A lane holds SLOTS increments, so SLOTS
+// independent 256-bit gathers are in flight per moving atom.
 //
 // Shared memory per CTA: the ligand (centred coordinates + type, bond axes,
 // moving-atom lists) and the current coordinates of every restart, in grid
-// units, as [atom][restart] planes so that the 8 restarts of a warp read 8
+// units, as [atom][restart] planes so that the restarts of a warp read
 // consecutive words. The sweep caches nothing: the moving side of a bond is
 // re-sampled for each increment j, the fixed side is a constant of the
 // decision and is not sampled at all (the argmax is over moving-side sums).
+//
+// Work distribution. Either one CTA per work item (grid = items), or a
+// persistent grid whose CTAs take items from a device counter (atomicAdd,
+// no waiting) until the list is exhausted; items may come from a ligand list
+// (a bucket of similar ligands) instead of the whole library.
 #include "../../include/ligen.h"
 #include "internal.h"
 
 namespace ligen {
 namespace {
 
-constexpr int G = kLanesPerRestart;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct SmemLayout {
@@ -55,6 +60,7 @@ __host__ __device__ inline size_t carve(int max_atoms, int max_rot, int max_frag
 }
 
 // Argmax over the G lanes of a group: higher score wins, lower index on ties.
+template <int G>
 __device__ __forceinline__ void group_argmax(float& s, int& idx) {
 #pragma unroll
   for (int o = 1; o < G; o <<= 1) {
@@ -64,14 +70,9 @@ __device__ __forceinline__ void group_argmax(float& s, int& idx) {
   }
 }
 
-template <int SLOTS>
-__global__ void __launch_bounds__(128) dock_kernel(const DockArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int l = blockIdx.x / a.chunks;
-  const int chunk = blockIdx.x - l * a.chunks;
-  if (a.pk.status[l] != 0) return;   // uniform over the CTA
-  SmemLayout S;
-  carve(a.max_atoms, a.max_rot, a.max_frag, a.rpc, smem, &S);
+// One work item: ligand l, restarts [chunk * rpc, chunk * rpc + rpc).
+template <int G, int SLOTS>
+__device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S, int l, int chunk) {
   const int rpc = a.rpc;
   const int tid = threadIdx.x;
   const int a0 = a.lig.atom_off[l];
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(128) dock_kernel(const DockArgs a) {
     }
     if (acc > best) { best = acc; kb = k; }
   }
-  group_argmax(best, kb);
+  group_argmax<G>(best, kb);
   const int D = 1 + a.passes * n;
   int16_t* trace = nullptr;
   if (a.trace && active)
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(128) dock_kernel(const DockArgs a) {
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) torsion_cs(sub + G * s, a.step_deg, &cs[s], &sn[s]);
       }
-      group_argmax(bs, jb);
+      group_argmax<G>(bs, jb);
       if (jb != 0) {
         float c, s;
         torsion_cs(jb, a.step_deg, &c, &s);
@@ -254,36 +255,87 @@ __global__ void __launch_bounds__(128) dock_kernel(const DockArgs a) {
   }
 }
 
+template <int G, int SLOTS>
+__global__ void __launch_bounds__(128) dock_kernel(const DockArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int next_item;
+  SmemLayout S;
+  carve(a.max_atoms, a.max_rot, a.max_frag, a.rpc, smem, &S);
+  int item = blockIdx.x;
+  while (true) {
+    if (a.queue) {   // persistent: take the next item from the device counter
+      if (threadIdx.x == 0) next_item = atomicAdd(a.queue, 1);
+      __syncthreads();
+      item = next_item;
+      __syncthreads();
+    }
+    if (item >= a.n_items) break;
+    const int li = item / a.chunks;
+    const int l = a.list ? a.list[li] : li;
+    if (a.pk.status[l] == 0)   // uniform over the CTA
+      dock_item<G, SLOTS>(a, S, l, item - li * a.chunks);
+    if (!a.queue) break;
+    __syncthreads();   // shared memory is reused by the next item
+  }
+}
+
 }  // namespace
 
 size_t dock_smem_bytes(int max_atoms, int max_rot, int max_frag, int rpc) {
   return carve(max_atoms, max_rot, max_frag, rpc, nullptr, nullptr);
 }
 
-int dock_threads_per_block(int rpc) { return rpc * G; }
+namespace {
 
-template <int SLOTS>
-static cudaError_t launch_slots(const DockArgs& a, size_t smem, cudaStream_t s) {
-  auto* k = dock_kernel<SLOTS>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+using KernelFn = void (*)(DockArgs);
+
+// Instantiated (G, SLOTS) shapes; G * SLOTS increments per chunk of the sweep.
+struct Shape {
+  int G, SLOTS;
+  KernelFn fn;
+};
+const Shape kShapes[] = {
+    {2, 6, dock_kernel<2, 6>},  {2, 18, dock_kernel<2, 18>}, {4, 3, dock_kernel<4, 3>},
+    {4, 9, dock_kernel<4, 9>},  {8, 2, dock_kernel<8, 2>},   {8, 5, dock_kernel<8, 5>},
+};
+
+// The instantiation for G lanes and n_theta increments: the fewest slots that
+// cover n_theta in one chunk, else the largest (several chunks).
+const Shape* pick_shape(int G, int n_theta) {
+  const Shape* best = nullptr;
+  for (const Shape& sh : kShapes) {
+    if (sh.G != G) continue;
+    if (sh.G * sh.SLOTS >= n_theta) {
+      if (!best || best->G * best->SLOTS < n_theta || sh.SLOTS < best->SLOTS) best = &sh;
+    } else if (!best || (best->G * best->SLOTS < n_theta && sh.SLOTS > best->SLOTS)) {
+      best = &sh;
+    }
+  }
+  return best;
+}
+
+}  // namespace
+
+bool dock_lanes_supported(int G) { return G == 2 || G == 4 || G == 8; }
+
+cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s) {
+  if (a.n_items == 0) return cudaSuccess;
+  const Shape* sh = pick_shape(a.lanes, a.n_theta);
+  if (!sh) return cudaErrorInvalidValue;
+  const size_t smem = dock_smem_bytes(a.max_atoms, a.max_rot, a.max_frag, a.rpc);
+  cudaError_t e = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const size_t blocks = (size_t)a.lig.L * a.chunks;
-  k<<<(unsigned)blocks, a.rpc * G, smem, s>>>(a);
+  const unsigned blocks = a.queue ? (unsigned)grid_ctas : (unsigned)a.n_items;
+  sh->fn<<<blocks, a.rpc * a.lanes, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dock(const DockArgs& a, cudaStream_t s) {
-  if (a.lig.L == 0) return cudaSuccess;
-  const size_t smem = dock_smem_bytes(a.max_atoms, a.max_rot, a.max_frag, a.rpc);
-  if (a.n_theta <= 3 * G) return launch_slots<3>(a, smem, s);
-  return launch_slots<9>(a, smem, s);
-}
-
-cudaError_t dock_occupancy(int rpc, size_t smem, int* blocks_per_sm) {
-  auto* k = dock_kernel<9>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t dock_occupancy(int lanes, int n_theta, int rpc, size_t smem, int* blocks_per_sm) {
+  const Shape* sh = pick_shape(lanes, n_theta);
+  if (!sh) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, rpc * G, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sh->fn, rpc * lanes, smem);
 }
 
 }  // namespace ligen

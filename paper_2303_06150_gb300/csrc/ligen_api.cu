@@ -266,9 +266,16 @@ struct Timer {
   }
 };
 
-int dock_restarts_per_cta(int R) {
-  int rpc = ((R + 7) / 8) * 8;
-  return rpc < 32 ? rpc : 32;
+// Default launch shape: 8 lanes per restart, up to 16 restarts per CTA
+// (measured on GB300: faster than 2 or 4 lanes for both small and large
+// ligands; 72 registers and half the shared memory of 4 lanes per CTA).
+constexpr int kDefaultLanes = 8;
+
+int dock_restarts_per_cta(int R, int lanes) {
+  const int per_warp = 32 / lanes;
+  const int cap = 128 / lanes;
+  int rpc = ((R + per_warp - 1) / per_warp) * per_warp;
+  return rpc < cap ? rpc : cap;
 }
 
 }  // namespace
@@ -383,8 +390,12 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
   da.step_deg = params->torsion_step_deg;
   da.n_theta = 360 / params->torsion_step_deg;
   da.passes = P;
-  da.rpc = dock_restarts_per_cta(R);
+  da.lanes = kDefaultLanes;
+  da.rpc = dock_restarts_per_cta(R, da.lanes);
   da.chunks = (R + da.rpc - 1) / da.rpc;
+  da.list = nullptr;
+  da.n_items = L * da.chunks;
+  da.queue = nullptr;
   da.max_atoms = sh.max_atoms;
   da.max_rot = sh.max_rot;
   da.max_frag = (int)sh.max_frag;
@@ -392,7 +403,7 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
   da.res_k = ar.at<uint8_t>(o_rk);
   da.res_cnt = ar.at<uint8_t>(o_rc);
   da.trace = d_trace;
-  LG_CUDA(launch_dock(da, s));
+  LG_CUDA(launch_dock(da, 0, s));
   tm.mark();
 
   TopkArgs ta{};
@@ -549,10 +560,10 @@ int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t
   LG_CUDA(cudaGetDevice(&dev));
   LG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   LG_CUDA(cudaDeviceGetAttribute(&warp, cudaDevAttrWarpSize, dev));
-  const int rpc = 32;
+  const int rpc = dock_restarts_per_cta(256, kDefaultLanes);
   const size_t smem = dock_smem_bytes(max_atoms, LIGEN_MAX_ROT, LIGEN_MAX_ROT * (max_atoms / 2), rpc);
-  LG_CUDA(dock_occupancy(rpc, smem, &blocks));
-  const int threads = dock_threads_per_block(rpc);
+  LG_CUDA(dock_occupancy(kDefaultLanes, 36, rpc, smem, &blocks));
+  const int threads = rpc * kDefaultLanes;
   if (b) *b = blocks;
   if (sm) *sm = nsm;
   if (t) *t = threads;
@@ -699,8 +710,12 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
   da.step_deg = params->torsion_step_deg;
   da.n_theta = 360 / params->torsion_step_deg;
   da.passes = params->passes;
-  da.rpc = dock_restarts_per_cta(R);
+  da.lanes = kDefaultLanes;
+  da.rpc = dock_restarts_per_cta(R, da.lanes);
   da.chunks = (R + da.rpc - 1) / da.rpc;
+  da.list = nullptr;
+  da.n_items = L * da.chunks;
+  da.queue = nullptr;
   da.max_atoms = sh.max_atoms;
   da.max_rot = sh.max_rot;
   da.max_frag = (int)sh.max_frag;
@@ -708,7 +723,7 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
   da.res_k = ar.at<uint8_t>(o_rk);
   da.res_cnt = ar.at<uint8_t>(o_rc);
   da.trace = params->trace;
-  LG_CUDA(launch_dock(da, s));
+  LG_CUDA(launch_dock(da, 0, s));
 
   TopkArgs ta{};
   ta.L = L; ta.R = R; ta.K = K; ta.step_deg = params->torsion_step_deg;
