@@ -30,9 +30,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ligands/s and poses/s on 1 GB300: chosen form vs plain FP32 at <=1e-3 score err"
 WORKLOAD = "screen20k"
-WORKLOAD_DESC = ("screen20k: 20,000 synthetic ligands (atoms ~N(38,14) in [8,100], rotatable bonds "
-                 "~Poisson(6) in [0,24]), 96^3x8 FP32 pocket grid at 0.375 A, 256 restarts x 24 cube "
-                 "rotations, 10 deg torsion steps, 3 passes, top-30")
+WORKLOAD_DESCS = {
+    "screen20k": ("screen20k: 20,000 synthetic ligands (atoms ~N(38,14) in [8,100], rotatable bonds "
+                  "~Poisson(6) in [0,24]), 96^3x8 FP32 pocket grid at 0.375 A, 256 restarts x 24 cube "
+                  "rotations, 10 deg torsion steps, 3 passes, top-30"),
+    "bimodal200k": ("bimodal200k: 200,000 synthetic ligands, 70% with 15-35 atoms and 0-8 rotatable bonds, "
+                    "30% with 60-120 atoms and 8-30; 96^3x8 FP32 grid at 0.375 A, 256 restarts x 24 cube "
+                    "rotations, 10 deg steps, 3 passes, top-30"),
+}
+WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 BYTES_PER_SAMPLE = 32   # one trilinear sample = 8 FP32 corner values (one 32-byte record)
 
 
@@ -45,6 +51,9 @@ def parse():
     ap.add_argument("--ligands", type=int, default=None, help="cut the library (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCS))
+    ap.add_argument("--forms", default="plain,buckets",
+                    help="docking layouts to time; the fastest is the reported form")
     return ap.parse_args()
 
 
@@ -55,20 +64,20 @@ def dist_env():
     return rank, world, local
 
 
-def shard_spec(rank: int, n_ligands=None) -> dict:
+def shard_spec(rank: int, n_ligands=None, workload: str = WORKLOAD) -> dict:
     """Workload of one rank: the same recipe and size on every rank, with the
     library and restart seeds offset by the rank, so each GPU docks its own
     shard of a world_size-times larger library (weak scaling)."""
     import gen
-    w = gen.scaled(WORKLOAD, n_ligands or gen.WORKLOADS[WORKLOAD]["library"]["n_ligands"])
+    w = gen.scaled(workload, n_ligands or gen.WORKLOADS[workload]["library"]["n_ligands"])
     w["library"]["seed"] = int(w["library"]["seed"]) + 1000 * rank
     w["search"]["seed"] = int(w["search"]["seed"]) + 1000 * rank
     return w
 
 
-def workload(n_ligands=None, rank=0):
+def workload(n_ligands=None, rank=0, name: str = WORKLOAD):
     import gen
-    w = shard_spec(rank, n_ligands)
+    w = shard_spec(rank, n_ligands, name)
     return w, gen.make_library(w["library"]), gen.make_grid(w["grid"])
 
 
@@ -211,7 +220,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w, lib, grid = workload(args.ligands)
+    w, lib, grid = workload(args.ligands, 0, args.workload)
     s = w["search"]
     import oracle
     oracle.lib()
@@ -231,7 +240,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ligands/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "parallelism": "host threads"},
+           "data": "synthetic", "config": {"workload": WORKLOAD_DESCS[args.workload], "parallelism": "host threads"},
            "cpu_baseline": {"value": value, "unit": "ligands/s", "cores": threads, "kind": "oracle",
                             "sample": f"{per_step} random ligands of the library per step, all restarts"},
            "e2e": {"value": value, "unit": "ligands/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -249,47 +258,62 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w, lib, grid = workload(args.ligands, rank)
+    w, lib, grid = workload(args.ligands, rank, args.workload)
     s = w["search"]
     kw = dict(restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"], passes=s["passes"],
               top_k=s["top_k"], seed=s["seed"], n_rigid=s["n_rigid"], jitter=s["jitter"],
               out_penalty=s["out_penalty"])
     L = lg.Ligands.from_arrays(lib, dev)
     G = lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, dev)
-    bits, _, _, _ = lg.pack_ligands(L, grid.dims[3])
+    bits, _, buckets, _ = lg.pack_ligands(L, grid.dims[3])
+    present = sorted({int(b) for b in buckets.cpu().numpy()})
     moving = np.unpackbits(bits.cpu().numpy().view(np.uint8), bitorder="little").sum() if bits.numel() else 0
     poses_step, samples_step = algorithmic_counts(lib, s, moving)
-    out = lg.dock_batch(L, G, stage_ms=True, **kw)        # allocates outputs and the workspace
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > L2: written between steps
-    for _ in range(args.warmup):
-        flush.fill_(1)
-        lg.dock_batch(L, G, out=out, **kw)
-    torch.cuda.synchronize()
-
     stream = torch.cuda.current_stream(dev)
-    dock_ms = []
-    with ClockSampler(local) as clk:
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for _ in range(args.steps):
+    forms = [f for f in args.forms.split(",") if f]
+    tuned = None
+    if "buckets" in forms:
+        # per-bucket kernel shapes for this library (not timed)
+        tuned = lg.autotune(L, G, sample=256, **kw)
+
+    def time_form(form):
+        out = lg.dock_batch(L, G, stage_ms=True, batching=form, **kw)   # allocates outputs and workspace
+        for _ in range(args.warmup):
             flush.fill_(1)
-            lg.dock_batch(L, G, out=out, **kw)
-            dock_ms.append(float(out.stage_ms[3]))
-        t1.record(stream)
+            lg.dock_batch(L, G, out=out, batching=form, **kw)
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-    stage = out.stage_ms.copy()
-    ms_total = max_over_ranks(t0.elapsed_time(t1), world)
+        dock_ms = []
+        with ClockSampler(local) as clk:
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(args.steps):
+                flush.fill_(1)
+                lg.dock_batch(L, G, out=out, batching=form, **kw)
+                dock_ms.append(float(out.stage_ms[3]))
+            t1.record(stream)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+        ms_total = max_over_ranks(t0.elapsed_time(t1), world)
+        return dict(ms_total=ms_total, dock_ms=float(np.mean(dock_ms)), stage=out.stage_ms.copy(),
+                    clocks=clk.summary(), out=out)
+
+    timed = {f: time_form(f) for f in forms}
+    form = min(timed, key=lambda f: timed[f]["ms_total"])
+    best = timed[form]
+    stage = best["stage"]
+    ms_total = best["ms_total"]
     ms_step = ms_total / args.steps
     value = job_throughput(lib.n_ligands, world, args.steps, ms_total)
+    out = best["out"]
 
     # roofline of the docking kernel: algorithmic bytes / its event-timed duration
-    dock = float(np.mean(dock_ms))
+    dock = best["dock_ms"]
     achieved = samples_step * BYTES_PER_SAMPLE / (dock * 1e-3) / 1e9
     # gather ceiling: same access pattern (random 32-byte records), no pose math, on a
     # buffer the size of the grid's hot region (20 MB, L2-resident)
@@ -309,30 +333,44 @@ def run_ours(args):
     result = {"metric": METRIC, "value": value, "unit": "ligands/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-              "config": {"workload": WORKLOAD_DESC, "ligands": lib.n_ligands, "restarts": s["restarts"],
-                         "torsion_step_deg": s["torsion_step_deg"], "passes": s["passes"], "top_k": s["top_k"],
-                         "form": "plain FP32", "l2": "flushed between steps (512 MB write)",
+              "config": {"workload": WORKLOAD_DESCS[args.workload], "ligands": lib.n_ligands,
+                         "restarts": s["restarts"], "torsion_step_deg": s["torsion_step_deg"],
+                         "passes": s["passes"], "top_k": s["top_k"],
+                         "form": f"FP32 grid, {form} layout (fastest of {'/'.join(forms)})",
+                         "l2": "flushed between steps (512 MB write)",
                          "parallelism": f"replicas x{world} (one library shard per GPU, no collective)"},
+              "forms": {f: {"value": job_throughput(lib.n_ligands, world, args.steps, t["ms_total"]),
+                            "ms_per_step": t["ms_total"] / args.steps, "dock_ms": t["dock_ms"],
+                            "vs_plain_fp32": (timed["plain"]["ms_total"] / t["ms_total"]) if "plain" in timed
+                            else None}
+                        for f, t in timed.items()},
               "poses_per_s": poses_step * world * args.steps / (ms_total * 1e-3),
               "samples_per_s": samples_step * world * args.steps / (ms_total * 1e-3),
               "stage_ms_last_step": dict(zip(["h2d", "grid_prep", "pack", "dock", "topk_d2h"],
                                              [float(x) for x in stage])),
               "roofline": roofline,
-              "gpu_launches": 4 * args.steps,
-              "clocks": clk.summary()}
+              "gpu_launches": None,
+              "clocks": best["clocks"]}
+    # our kernels per step: grid preparation, packer, top-K, and one docking
+    # launch (plain) or one per (atom class, kernel shape) group (buckets)
+    table = lg.tune_get()
+    per_step = 3 + (len({(b // 11, table[b]) for b in present}) if form == "buckets" else 1)
+    result["gpu_launches"] = per_step * args.steps
+    if tuned is not None:
+        result["tuning"] = {str(b): list(v[:2]) for b, v in sorted(tuned.items())}
 
     if not args.no_e2e:
         Lh = lg.Ligands.from_arrays(lib, "cpu", pin=True)
         Gh = lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, "cpu", pin=True)
-        outh = lg.dock_batch(Lh, Gh, **kw)
+        outh = lg.dock_batch(Lh, Gh, batching=form, **kw)
         for _ in range(max(1, args.warmup // 2)):
-            lg.dock_batch(Lh, Gh, out=outh, **kw)
+            lg.dock_batch(Lh, Gh, out=outh, batching=form, **kw)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         e0 = time.perf_counter()
         for _ in range(args.steps):
-            lg.dock_batch(Lh, Gh, out=outh, **kw)   # copies in, runs, copies out, synchronises
+            lg.dock_batch(Lh, Gh, out=outh, batching=form, **kw)   # copies in, runs, copies out, syncs
         e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3, world)
         h2d = Lh.nbytes() + Gh.values.numel() * 4
         d2h = (outh.poses.numel() + outh.scores.numel() + outh.status.numel()) * 4
@@ -340,7 +378,7 @@ def run_ours(args):
                          "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                          "how": "ligen_dock_batch with pinned host inputs and outputs: H2D, kernels, D2H "
                                 "and a stream sync per step, host wall clock"}
-        result["gpu_launches"] += 4 * args.steps
+        result["gpu_launches"] += per_step * args.steps
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(lib, grid, s)

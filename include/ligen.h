@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define LIGEN_ABI_VERSION 1
+#define LIGEN_ABI_VERSION 2
 #define LIGEN_MAX_ATOMS 256
 #define LIGEN_MAX_ROT 32
 #define LIGEN_MAX_CHANNELS 64
@@ -118,6 +118,26 @@ typedef struct ligen_grid {
  * device time of each stage measured with CUDA events on `stream`; passing it
  * makes the call synchronise the stream. */
 #define LIGEN_N_STAGES 5 /* h2d, grid prep, pack, dock, top-k + d2h */
+
+/* How the docking work of a call is laid out on the GPU (same results).
+ *   LIGEN_BATCH_PLAIN    one launch over the library, one CTA per (ligand,
+ *                        restart chunk), shared memory sized for the largest
+ *                        ligand of the call;
+ *   LIGEN_BATCH_BUCKETS  paper §3: ligands are grouped by atom class x
+ *                        rotamer class (the bucket ids of ligen_pack_ligands)
+ *                        and ordered largest-cost first; each atom class runs
+ *                        as one persistent launch (CTAs take work items from a
+ *                        device counter) with shared memory sized for that
+ *                        class, Eq. 1's b x SM CTAs (b from the occupancy query)
+ *                        and the lanes-per-restart / restarts-per-CTA shape
+ *                        of the tuning table (ligen_tune_set, ligen_autotune);
+ *                        the classes run on forked streams and the whole
+ *                        sequence is captured once into a CUDA graph and
+ *                        replayed while the call's shape is unchanged. */
+#define LIGEN_BATCH_PLAIN 0
+#define LIGEN_BATCH_BUCKETS 1
+#define LIGEN_N_BUCKETS 44 /* 4 atom classes x 11 rotamer classes */
+
 typedef struct ligen_params {
   int32_t restarts;
   int32_t n_rigid;
@@ -133,6 +153,8 @@ typedef struct ligen_params {
   int16_t* trace;
   int32_t* top_restart;
   float* stage_ms;
+  int32_t batching;   /* LIGEN_BATCH_PLAIN or LIGEN_BATCH_BUCKETS */
+  int32_t reserved2;
 } ligen_params_t;
 
 /* Dock every ligand (paper §2, the dock task; cost per §3 follows atoms and
@@ -177,6 +199,24 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
 #define LIGEN_STATIC_SCRATCH_BYTES (32u << 20)
 int ligen_dock_batch_static(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                             const ligen_params_t* params, float* out_poses, float* out_scores);
+
+/* Tuning table of the bucketed layout, one per device (the current one):
+ * for bucket b (atom_class * 11 + rotamer_class, 0 .. LIGEN_N_BUCKETS-1) the
+ * lanes per restart (2, 4 or 8) and restarts per CTA (a multiple of 32/lanes,
+ * lanes * restarts <= 128). Defaults: 8 lanes, 16 restarts. */
+int ligen_tune_set(int32_t bucket, int32_t lanes, int32_t restarts_per_cta);
+int ligen_tune_get(int32_t bucket, int32_t* lanes, int32_t* restarts_per_cta);
+
+/* Autotuner: for every bucket present in `ligands` (at most `sample`
+ * ligands of each), dock with every candidate shape (lanes 4 or 8, 8 to 32
+ * restarts per CTA), time the docking kernel with CUDA events on
+ * params->stream, and store the fastest shape per ligand in the tuning table.
+ * Writes the chosen shapes to out_lanes / out_rpc ([LIGEN_N_BUCKETS], HOST,
+ * 0 for absent buckets) and each bucket's best time per ligand in
+ * out_ms_per_ligand (HOST, nullable). Ligands and grid in device memory.
+ * Synchronises the stream. */
+int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, const ligen_params_t* params,
+                   int32_t sample, int32_t* out_lanes, int32_t* out_rpc, float* out_ms_per_ligand);
 
 /* Score given poses (same pose packing as ligen_dock_batch with K =
  * poses_per_ligand): out_scores[l][p] = S of pose p of ligand l, or

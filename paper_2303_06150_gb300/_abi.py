@@ -20,6 +20,9 @@ LIGEN_ERR_CUDA = -4
 LIGEN_ERR_TIMEOUT = -5
 LIGEN_ERR_BAD_LIGAND = -6
 LIGEN_N_STAGES = 5
+LIGEN_BATCH_PLAIN = 0
+LIGEN_BATCH_BUCKETS = 1
+LIGEN_N_BUCKETS = 44
 STAGE_NAMES = ("h2d", "grid_prep", "pack", "dock", "topk_d2h")
 
 P = C.c_void_p
@@ -40,7 +43,8 @@ class ParamsT(C.Structure):
     _fields_ = [("restarts", C.c_int32), ("n_rigid", C.c_int32), ("torsion_step_deg", C.c_int32),
                 ("passes", C.c_int32), ("top_k", C.c_int32), ("mode", C.c_int32), ("seed", C.c_uint64),
                 ("jitter", C.c_float), ("out_penalty", C.c_float), ("stream", P), ("status", P),
-                ("trace", P), ("top_restart", P), ("stage_ms", P)]
+                ("trace", P), ("top_restart", P), ("stage_ms", P), ("batching", C.c_int32),
+                ("reserved2", C.c_int32)]
 
 
 # Every function include/ligen.h declares, with its ctypes signature.
@@ -51,6 +55,9 @@ SIGNATURES = {
     "ligen_pack_ligands": (C.c_int, [P, C.c_int32, P, P, P, P, P]),
     "ligen_bucket_size": (C.c_int64, [C.c_int32, P, P, P, P]),
     "ligen_probe_gather": (C.c_int, [P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P]),
+    "ligen_tune_set": (C.c_int, [C.c_int32, C.c_int32, C.c_int32]),
+    "ligen_tune_get": (C.c_int, [C.c_int32, P, P]),
+    "ligen_autotune": (C.c_int, [P, P, P, C.c_int32, P, P, P]),
     "ligen_release_workspaces": (C.c_int, []),
     "ligen_last_error": (C.c_char_p, []),
     "ligen_abi_version": (C.c_int, []),

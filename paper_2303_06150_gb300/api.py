@@ -123,11 +123,17 @@ class DockResult:
         return self.poses[off[l]:off[l + 1]].reshape(K, 7 + n)
 
 
+BATCHING = {"plain": _abi.LIGEN_BATCH_PLAIN, "buckets": _abi.LIGEN_BATCH_BUCKETS}
+
+
 def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_step_deg: int, passes: int,
                top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
                status: bool = True, trace: bool = False, top_restart: bool = False,
-               stage_ms: bool = False, out: DockResult | None = None) -> DockResult:
-    """ligen_dock_batch: dock every ligand, keep the top_k poses of each."""
+               stage_ms: bool = False, batching: str = "plain", out: DockResult | None = None) -> DockResult:
+    """ligen_dock_batch: dock every ligand, keep the top_k poses of each.
+
+    batching: "plain" (one launch) or "buckets" (paper §3 classes, one
+    persistent launch per atom class, replayed from a CUDA graph)."""
     lib = _abi.load()
     L, dev = ligands.n_ligands, ligands.device
     n_sum = int(ligands.h_rot_off[-1])
@@ -144,7 +150,7 @@ def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_ste
     p = ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
                 float(jitter), float(out_penalty), _stream_handle(dev), _ptr(out.status), _ptr(out.trace),
                 _ptr(out.top_restart),
-                out.stage_ms.ctypes.data if out.stage_ms is not None else None)
+                out.stage_ms.ctypes.data if out.stage_ms is not None else None, BATCHING[batching], 0)
     check(lib.ligen_dock_batch(C.byref(ligands._s), C.byref(grid._s), C.byref(p), _ptr(out.poses),
                                _ptr(out.scores)))
     return out
@@ -168,7 +174,7 @@ def dock_batch_static(ligands: Ligands, grid: PocketGrid, *, restarts: int, tors
                          status=_empty((L,), torch.int32, dev), trace=None, top_restart=None, stage_ms=None)
     p = ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
                 float(jitter), float(out_penalty), _stream_handle(dev), _ptr(out.status), _ptr(out.trace),
-                _ptr(out.top_restart), None)
+                _ptr(out.top_restart), None, _abi.LIGEN_BATCH_PLAIN, 0)
     check(lib.ligen_dock_batch_static(C.byref(ligands._s), C.byref(grid._s), C.byref(p), _ptr(out.poses),
                                       _ptr(out.scores)))
     return out
@@ -219,6 +225,64 @@ def probe_gather(records: torch.Tensor, loads_per_thread: int = 256, bytes_per_l
                                  _ptr(sink), C.byref(loads), C.byref(ms), _stream_handle(records.device)))
     return dict(loads=loads.value, ms=ms.value, loads_per_s=loads.value / (ms.value * 1e-3),
                 gbs=loads.value * bytes_per_load / (ms.value * 1e-3) / 1e9)
+
+
+def tune_get() -> list:
+    """ligen_tune_get for every bucket: [(lanes, restarts_per_cta)] * 44."""
+    lib = _abi.load()
+    out = []
+    for b in range(_abi.LIGEN_N_BUCKETS):
+        lanes, rpc = C.c_int32(), C.c_int32()
+        check(lib.ligen_tune_get(b, C.byref(lanes), C.byref(rpc)))
+        out.append((lanes.value, rpc.value))
+    return out
+
+
+def tune_set(table) -> None:
+    """ligen_tune_set from {bucket: (lanes, restarts_per_cta)} or a 44-list."""
+    lib = _abi.load()
+    items = table.items() if isinstance(table, dict) else enumerate(table)
+    for b, (lanes, rpc) in items:
+        check(lib.ligen_tune_set(int(b), int(lanes), int(rpc)))
+
+
+def autotune(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_step_deg: int, passes: int,
+             top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
+             sample: int = 256) -> dict:
+    """ligen_autotune: time the candidate shapes per bucket on (a sample of)
+    this library and store the fastest; returns {bucket: (lanes, rpc, ms per ligand)}."""
+    lib = _abi.load()
+    p = ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
+                float(jitter), float(out_penalty), _stream_handle(ligands.device), None, None, None, None,
+                _abi.LIGEN_BATCH_PLAIN, 0)
+    lanes = np.zeros(_abi.LIGEN_N_BUCKETS, np.int32)
+    rpc = np.zeros(_abi.LIGEN_N_BUCKETS, np.int32)
+    ms = np.zeros(_abi.LIGEN_N_BUCKETS, np.float32)
+    check(lib.ligen_autotune(C.byref(ligands._s), C.byref(grid._s), C.byref(p), int(sample),
+                             lanes.ctypes.data, rpc.ctypes.data, ms.ctypes.data))
+    return {b: (int(lanes[b]), int(rpc[b]), float(ms[b])) for b in range(len(lanes)) if lanes[b]}
+
+
+def save_tuning(path: str) -> None:
+    """Write the current device's tuning table as JSON keyed by GPU name."""
+    import json
+    import os
+    name = torch.cuda.get_device_name()
+    data = json.load(open(path)) if os.path.exists(path) else {}
+    data[name] = {str(b): list(v) for b, v in enumerate(tune_get())}
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+
+
+def load_tuning(path: str) -> bool:
+    """Load this GPU's entry of a JSON tuning file, if present."""
+    import json
+    data = json.load(open(path))
+    entry = data.get(torch.cuda.get_device_name())
+    if not entry:
+        return False
+    tune_set({int(b): tuple(v) for b, v in entry.items()})
+    return True
 
 
 def release_workspaces() -> None:

@@ -89,7 +89,14 @@ cudaError_t launch_pack(const LigandsDev& lig, int nc, const Packed& out, cudaSt
 size_t dock_smem_bytes(int max_atoms, int max_rot, int max_frag, int rpc);
 bool dock_lanes_supported(int lanes);
 // grid_ctas: CTAs of a persistent launch (ignored when a.queue is NULL).
-cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s);
+// set_attr: set the kernel's dynamic shared-memory limit first (false when
+// dock_occupancy already did, e.g. before a stream capture).
+cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s, bool set_attr);
+// The kernel of (lanes, n_theta) accepts up to `smem` bytes of dynamic
+// shared memory from now on (a per-kernel setting: set the largest value any
+// pending launch of that kernel needs).
+cudaError_t dock_set_smem_limit(int lanes, int n_theta, size_t smem);
+// Resident CTAs per SM for a launch with `smem` bytes (within the limit).
 cudaError_t dock_occupancy(int lanes, int n_theta, int rpc, size_t smem, int* blocks_per_sm);
 cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s);

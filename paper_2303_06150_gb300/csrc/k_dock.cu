@@ -318,23 +318,29 @@ const Shape* pick_shape(int G, int n_theta) {
 
 bool dock_lanes_supported(int G) { return G == 2 || G == 4 || G == 8; }
 
-cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s) {
+cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s, bool set_attr) {
   if (a.n_items == 0) return cudaSuccess;
   const Shape* sh = pick_shape(a.lanes, a.n_theta);
   if (!sh) return cudaErrorInvalidValue;
   const size_t smem = dock_smem_bytes(a.max_atoms, a.max_rot, a.max_frag, a.rpc);
-  cudaError_t e = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  if (set_attr) {
+    cudaError_t e = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   const unsigned blocks = a.queue ? (unsigned)grid_ctas : (unsigned)a.n_items;
   sh->fn<<<blocks, a.rpc * a.lanes, smem, s>>>(a);
   return cudaGetLastError();
 }
 
+cudaError_t dock_set_smem_limit(int lanes, int n_theta, size_t smem) {
+  const Shape* sh = pick_shape(lanes, n_theta);
+  if (!sh) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 cudaError_t dock_occupancy(int lanes, int n_theta, int rpc, size_t smem, int* blocks_per_sm) {
   const Shape* sh = pick_shape(lanes, n_theta);
   if (!sh) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sh->fn, rpc * lanes, smem);
 }
 

@@ -5,8 +5,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <utility>
 #include <vector>
@@ -64,6 +66,8 @@ int space_of(std::initializer_list<const void*> ptrs) {
   return s == -2 ? 0 : s;
 }
 
+void forget_orders(int dev);   // cached ligand orders live in workspaces
+
 // ------------------------------------------------------------ workspace --
 struct Workspace {
   char* base = nullptr;
@@ -94,6 +98,7 @@ int get_workspace(cudaStream_t s, size_t bytes, char** out) {
   if (w.cap < bytes) {
     if (w.base) {
       LG_CUDA(cudaStreamSynchronize(s));
+      forget_orders(dev);
       cudaFree(w.base);
       w.base = nullptr;
       w.cap = 0;
@@ -174,6 +179,8 @@ int check_params(const ligen_params_t* p) {
   if (p->passes < 0 || p->passes > 1000) return fail(LIGEN_ERR_INVALID_ARG, "passes must be 0..1000");
   if (p->top_k < 1 || p->top_k > p->restarts) return fail(LIGEN_ERR_INVALID_ARG, "top_k must be 1..restarts");
   if (p->mode != 0) return fail(LIGEN_ERR_UNSUPPORTED, "mode %d not supported", p->mode);
+  if (p->batching != LIGEN_BATCH_PLAIN && p->batching != LIGEN_BATCH_BUCKETS)
+    return fail(LIGEN_ERR_INVALID_ARG, "batching must be LIGEN_BATCH_PLAIN or LIGEN_BATCH_BUCKETS");
   if (!std::isfinite(p->jitter) || p->jitter < 0.f) return fail(LIGEN_ERR_INVALID_ARG, "jitter must be >= 0");
   if (!std::isfinite(p->out_penalty)) return fail(LIGEN_ERR_INVALID_ARG, "out_penalty not finite");
   return LIGEN_OK;
@@ -278,6 +285,263 @@ int dock_restarts_per_cta(int R, int lanes) {
   return rpc < cap ? rpc : cap;
 }
 
+// ------------------------------------------------------------- buckets --
+// Paper §3: ligands are classified by atom count and rotamer count. Atom
+// classes on warp multiples (<=32, <=64, <=128, larger); rotamer classes with
+// upper edges 0,1,2,3,4,6,8,12,16,24,32 (finer at low counts).
+int atom_class_of(int N) { return N <= 32 ? 0 : N <= 64 ? 1 : N <= 128 ? 2 : 3; }
+int rot_class_of(int n) {
+  static const int edges[11] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
+  for (int c = 0; c < 11; ++c)
+    if (n <= edges[c]) return c;
+  return 10;
+}
+
+constexpr int kMaxDev = 64;
+
+struct TuneEntry {
+  int lanes = kDefaultLanes;
+  int rpc = 128 / kDefaultLanes;
+};
+std::mutex g_tune_mu;
+TuneEntry g_tune[kMaxDev][LIGEN_N_BUCKETS];
+
+bool valid_shape(int lanes, int rpc) {
+  return dock_lanes_supported(lanes) && rpc >= 1 && rpc % (32 / lanes) == 0 && rpc * lanes <= 128;
+}
+
+// One persistent launch: ligands order[beg..end) with one kernel shape.
+struct Group {
+  int lanes = 0, rpc = 0;
+  int beg = 0, end = 0;
+  int max_atoms = 0, max_rot = 0, max_frag = 0;
+  double cost = 0.0;
+};
+
+// Host plan of the bucketed layout: groups keyed by (atom class, tuned
+// shape); inside a group ligands go by decreasing estimated cost
+// (R * (n_rigid * N + passes * n * n_theta * N / 4)), and the groups by
+// decreasing total cost, so the longest work starts first.
+void plan_groups(const ligen_ligands_t* g, const ligen_params_t* p, int dev, std::vector<int32_t>& order,
+                 std::vector<Group>& groups) {
+  const int L = g->n_ligands;
+  const int nt = 360 / p->torsion_step_deg;
+  struct Item {
+    int32_t l;
+    double cost;
+  };
+  std::map<std::tuple<int, int, int>, std::vector<Item>> by;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int l = 0; l < L; ++l) {
+      const int N = g->h_atom_off[l + 1] - g->h_atom_off[l];
+      const int n = g->h_rot_off[l + 1] - g->h_rot_off[l];
+      const int ac = atom_class_of(N);
+      const TuneEntry& t = g_tune[dev][ac * 11 + rot_class_of(n)];
+      const double cost = (double)N * p->n_rigid + (double)p->passes * n * nt * (0.25 * N + 1.0);
+      by[std::make_tuple(ac, t.lanes, t.rpc)].push_back({l, cost});
+    }
+  }
+  order.clear();
+  groups.clear();
+  for (auto& kv : by) {
+    auto& items = kv.second;
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
+    Group gr;
+    gr.lanes = std::get<1>(kv.first);
+    gr.rpc = std::get<2>(kv.first);
+    gr.beg = (int)order.size();
+    for (const Item& it : items) {
+      order.push_back(it.l);
+      const int N = g->h_atom_off[it.l + 1] - g->h_atom_off[it.l];
+      const int n = g->h_rot_off[it.l + 1] - g->h_rot_off[it.l];
+      gr.max_atoms = std::max(gr.max_atoms, N);
+      gr.max_rot = std::max(gr.max_rot, n);
+      gr.max_frag = std::max(gr.max_frag, n * (N / 2));
+      gr.cost += it.cost;
+    }
+    gr.end = (int)order.size();
+    groups.push_back(gr);
+  }
+  std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.cost > b.cost; });
+}
+
+// The ligand order last uploaded to each workspace region, so that docking
+// the same library again (the usual case: one library, many batches or
+// sites) skips the upload.
+std::mutex g_order_mu;
+std::map<std::tuple<int, cudaStream_t, const void*>, std::vector<int32_t>> g_order;
+
+bool order_is_current(cudaStream_t s, const void* d_order, const std::vector<int32_t>& order) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_order_mu);
+  auto it = g_order.find(std::make_tuple(dev, s, d_order));
+  return it != g_order.end() && it->second == order;
+}
+
+void remember_order(cudaStream_t s, const void* d_order, const std::vector<int32_t>& order) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_order_mu);
+  g_order[std::make_tuple(dev, s, d_order)] = order;
+}
+
+void forget_orders(int dev) {
+  std::lock_guard<std::mutex> lk(g_order_mu);
+  for (auto it = g_order.begin(); it != g_order.end();)
+    it = (std::get<0>(it->first) == dev) ? g_order.erase(it) : std::next(it);
+}
+
+// Side streams and events for the forked launches, per device.
+struct Fork {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t start = nullptr;
+};
+std::mutex g_fork_mu;
+std::map<int, Fork> g_fork;
+
+int get_fork(int dev, int n, Fork** out) {
+  std::lock_guard<std::mutex> lk(g_fork_mu);
+  Fork& f = g_fork[dev];
+  if (!f.start) LG_CUDA(cudaEventCreateWithFlags(&f.start, cudaEventDisableTiming));
+  while ((int)f.streams.size() < n) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    LG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    LG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    f.streams.push_back(st);
+    f.done.push_back(ev);
+  }
+  *out = &f;
+  return LIGEN_OK;
+}
+
+// Instantiated graphs of the bucketed launch sequence, keyed by everything
+// the launches capture by value (pointers, sizes, shapes, grid sizes).
+struct GraphEntry {
+  std::string key;
+  cudaGraphExec_t exec;
+};
+std::mutex g_graph_mu;
+std::map<std::pair<int, cudaStream_t>, std::vector<GraphEntry>> g_graphs;
+constexpr size_t kGraphsPerStream = 4;
+
+void append_key(std::string& k, const void* p, size_t n) { k.append((const char*)p, n); }
+
+std::string launch_key(const std::vector<DockArgs>& args, const std::vector<int>& ctas) {
+  std::string k;
+  for (size_t i = 0; i < args.size(); ++i) {
+    const DockArgs& a = args[i];
+    const void* ptrs[] = {a.lig.atom_off, a.lig.xyz, a.lig.type, a.lig.bonds, a.lig.rot_off, a.lig.rot_edge,
+                          a.pk.xc, a.pk.binfo, a.pk.frag, a.pk.status, a.grid.coef, a.res_score, a.res_k,
+                          a.res_cnt, a.trace, a.list, a.queue};
+    append_key(k, ptrs, sizeof ptrs);
+    const int ints[] = {a.lig.L, a.grid.cx, a.grid.cy, a.grid.cz, a.grid.nc, a.R, a.n_rigid, a.step_deg,
+                        a.n_theta, a.passes, a.lanes, a.rpc, a.chunks, a.n_items, a.max_atoms, a.max_rot,
+                        a.max_frag, ctas[i]};
+    append_key(k, ints, sizeof ints);
+    const float fl[] = {a.origin[0], a.origin[1], a.origin[2], a.inv_h, a.center[0], a.center[1], a.center[2],
+                        a.jitter, a.grid.penalty, a.grid.mx, a.grid.my, a.grid.mz};
+    append_key(k, fl, sizeof fl);
+    append_key(k, &a.seed, sizeof a.seed);
+  }
+  return k;
+}
+
+// Issue the groups' persistent launches forked from `s` and joined back.
+int issue_groups(const std::vector<DockArgs>& args, const std::vector<int>& ctas, int dev, cudaStream_t s) {
+  Fork* f = nullptr;
+  int rc = get_fork(dev, (int)args.size(), &f);
+  if (rc != LIGEN_OK) return rc;
+  LG_CUDA(cudaEventRecord(f->start, s));
+  for (size_t i = 0; i < args.size(); ++i) {
+    cudaStream_t st = f->streams[i];
+    LG_CUDA(cudaStreamWaitEvent(st, f->start, 0));
+    LG_CUDA(cudaMemsetAsync(args[i].queue, 0, sizeof(int), st));
+    LG_CUDA(launch_dock(args[i], ctas[i], st, false));
+    LG_CUDA(cudaEventRecord(f->done[i], st));
+    LG_CUDA(cudaStreamWaitEvent(s, f->done[i], 0));
+  }
+  return LIGEN_OK;
+}
+
+// The bucketed layout: one persistent launch per group, sized by Eq. 1
+// (b blocks per SM from the occupancy query, times the SM count), run from a
+// cached CUDA graph when `s` can be captured.
+int run_bucketed(const DockArgs& base, const std::vector<Group>& groups, int32_t* d_order, int* d_queue,
+                 cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  LG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // one dynamic shared-memory limit per kernel shape: the largest its groups need
+  std::map<int, size_t> limit;
+  for (const Group& gr : groups) {
+    const size_t smem = dock_smem_bytes(gr.max_atoms, gr.max_rot, gr.max_frag, gr.rpc);
+    size_t& l = limit[gr.lanes];
+    l = std::max(l, smem);
+  }
+  for (const auto& kv : limit) LG_CUDA(dock_set_smem_limit(kv.first, base.n_theta, kv.second));
+  std::vector<DockArgs> args;
+  std::vector<int> ctas;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const Group& gr = groups[gi];
+    DockArgs a = base;
+    a.lanes = gr.lanes;
+    a.rpc = gr.rpc;
+    a.chunks = (a.R + a.rpc - 1) / a.rpc;
+    a.list = d_order + gr.beg;
+    a.n_items = (gr.end - gr.beg) * a.chunks;
+    a.queue = d_queue + gi;
+    a.max_atoms = gr.max_atoms;
+    a.max_rot = gr.max_rot;
+    a.max_frag = gr.max_frag;
+    const size_t smem = dock_smem_bytes(a.max_atoms, a.max_rot, a.max_frag, a.rpc);
+    int b = 0;
+    LG_CUDA(dock_occupancy(a.lanes, a.n_theta, a.rpc, smem, &b));
+    if (b < 1) return fail(LIGEN_ERR_UNSUPPORTED, "no CTA of shape (%d lanes, %d restarts) fits an SM", a.lanes, a.rpc);
+    ctas.push_back((int)std::min<int64_t>((int64_t)b * nsm, a.n_items));
+    args.push_back(a);
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  LG_CUDA(cudaStreamIsCapturing(s, &cs));
+  const bool can_graph = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread &&
+                         cs == cudaStreamCaptureStatusNone;
+  if (!can_graph) return issue_groups(args, ctas, dev, s);
+
+  const std::string key = launch_key(args, ctas);
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto& e : g_graphs[{dev, s}])
+      if (e.key == key) exec = e.exec;
+  }
+  if (!exec) {
+    LG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = issue_groups(args, ctas, dev, s);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc != LIGEN_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto& v = g_graphs[{dev, s}];
+    if (v.size() >= kGraphsPerStream) {
+      cudaGraphExecDestroy(v.front().exec);
+      v.erase(v.begin());
+    }
+    v.push_back({key, exec});
+  }
+  LG_CUDA(cudaGraphLaunch(exec, s));
+  return LIGEN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -289,6 +553,18 @@ const char* ligen_last_error(void) { return g_err.c_str(); }
 int ligen_release_workspaces(void) {
   int dev = 0;
   LG_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> gl(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+      if (it->first.first == dev) {
+        for (auto& e : it->second) cudaGraphExecDestroy(e.exec);
+        it = g_graphs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  forget_orders(dev);
   std::lock_guard<std::mutex> lk(g_ws_mu);
   for (auto it = g_ws.begin(); it != g_ws.end();) {
     if (it->first.first == dev) {
@@ -343,6 +619,18 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
     o_scores = ar.take(4 * (size_t)L * K);
     if (params->trace) o_trace = ar.take(2 * trace_elems);
     if (params->top_restart) o_top = ar.take(4 * (size_t)L * K);
+  }
+  const bool buckets = params->batching == LIGEN_BATCH_BUCKETS;
+  std::vector<int32_t> order;
+  std::vector<Group> groups;
+  size_t o_order = 0, o_queue = 0;
+  if (buckets) {
+    int dev = 0;
+    LG_CUDA(cudaGetDevice(&dev));
+    if (dev >= kMaxDev) return fail(LIGEN_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDev);
+    plan_groups(ligands, params, dev, order, groups);
+    o_order = ar.take(4 * (size_t)L);
+    o_queue = ar.take(sizeof(int) * groups.size());
   }
   if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
 
@@ -403,7 +691,17 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
   da.res_k = ar.at<uint8_t>(o_rk);
   da.res_cnt = ar.at<uint8_t>(o_rc);
   da.trace = d_trace;
-  LG_CUDA(launch_dock(da, 0, s));
+  if (buckets) {
+    int32_t* d_order = ar.at<int32_t>(o_order);
+    if (!order_is_current(s, d_order, order)) {
+      // pageable source: the copy is staged before the call returns
+      LG_CUDA(cudaMemcpyAsync(d_order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, s));
+      remember_order(s, d_order, order);
+    }
+    if ((rc = run_bucketed(da, groups, d_order, ar.at<int>(o_queue), s)) != LIGEN_OK) return rc;
+  } else {
+    LG_CUDA(launch_dock(da, 0, s, true));
+  }
   tm.mark();
 
   TopkArgs ta{};
@@ -562,6 +860,7 @@ int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t
   LG_CUDA(cudaDeviceGetAttribute(&warp, cudaDevAttrWarpSize, dev));
   const int rpc = dock_restarts_per_cta(256, kDefaultLanes);
   const size_t smem = dock_smem_bytes(max_atoms, LIGEN_MAX_ROT, LIGEN_MAX_ROT * (max_atoms / 2), rpc);
+  LG_CUDA(dock_set_smem_limit(kDefaultLanes, 36, smem));
   LG_CUDA(dock_occupancy(kDefaultLanes, 36, rpc, smem, &blocks));
   const int threads = rpc * kDefaultLanes;
   if (b) *b = blocks;
@@ -569,6 +868,189 @@ int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t
   if (t) *t = threads;
   if (ws) *ws = warp;
   return (int64_t)blocks * nsm * threads / warp;
+}
+
+int ligen_tune_set(int32_t bucket, int32_t lanes, int32_t restarts_per_cta) {
+  g_err.clear();
+  if (bucket < 0 || bucket >= LIGEN_N_BUCKETS) return fail(LIGEN_ERR_INVALID_ARG, "bucket must be 0..%d", LIGEN_N_BUCKETS - 1);
+  if (!valid_shape(lanes, restarts_per_cta))
+    return fail(LIGEN_ERR_INVALID_ARG, "shape (%d lanes, %d restarts) is not supported", lanes, restarts_per_cta);
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  if (dev >= kMaxDev) return fail(LIGEN_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDev);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[dev][bucket].lanes = lanes;
+  g_tune[dev][bucket].rpc = restarts_per_cta;
+  return LIGEN_OK;
+}
+
+int ligen_tune_get(int32_t bucket, int32_t* lanes, int32_t* restarts_per_cta) {
+  g_err.clear();
+  if (bucket < 0 || bucket >= LIGEN_N_BUCKETS) return fail(LIGEN_ERR_INVALID_ARG, "bucket must be 0..%d", LIGEN_N_BUCKETS - 1);
+  if (!lanes || !restarts_per_cta) return fail(LIGEN_ERR_INVALID_ARG, "NULL output");
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  if (dev >= kMaxDev) return fail(LIGEN_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDev);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  *lanes = g_tune[dev][bucket].lanes;
+  *restarts_per_cta = g_tune[dev][bucket].rpc;
+  return LIGEN_OK;
+}
+
+int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, const ligen_params_t* params,
+                   int32_t sample, int32_t* out_lanes, int32_t* out_rpc, float* out_ms_per_ligand) {
+  g_err.clear();
+  int rc;
+  if ((rc = check_params(params)) != LIGEN_OK) return rc;
+  LibShape sh;
+  if ((rc = check_ligands(ligands, params->passes, &sh)) != LIGEN_OK) return rc;
+  if ((rc = check_grid(grid)) != LIGEN_OK) return rc;
+  if (sample < 1) return fail(LIGEN_ERR_INVALID_ARG, "sample must be >= 1");
+  if (!out_lanes || !out_rpc) return fail(LIGEN_ERR_INVALID_ARG, "out_lanes and out_rpc are required");
+  for (int b = 0; b < LIGEN_N_BUCKETS; ++b) {
+    out_lanes[b] = 0;
+    out_rpc[b] = 0;
+    if (out_ms_per_ligand) out_ms_per_ligand[b] = 0.f;
+  }
+  const int L = ligands->n_ligands;
+  if (L == 0) return LIGEN_OK;
+  if (space_of({ligands->atom_off, ligands->xyz, ligands->type, ligands->bonds, ligands->rot_off,
+                ligands->rot_edge}) != 0 || space_of({grid->data}) != 0)
+    return fail(LIGEN_ERR_INVALID_ARG, "ligen_autotune takes device memory only");
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  if (dev >= kMaxDev) return fail(LIGEN_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDev);
+  cudaStream_t s = (cudaStream_t)params->stream;
+  const int R = params->restarts;
+
+  // up to `sample` ligands of each bucket, bucket by bucket
+  std::vector<std::vector<int32_t>> members(LIGEN_N_BUCKETS);
+  for (int l = 0; l < L; ++l) {
+    const int N = ligands->h_atom_off[l + 1] - ligands->h_atom_off[l];
+    const int n = ligands->h_rot_off[l + 1] - ligands->h_rot_off[l];
+    auto& m = members[atom_class_of(N) * 11 + rot_class_of(n)];
+    if ((int)m.size() < sample) m.push_back(l);
+  }
+  std::vector<int32_t> order;
+  std::vector<Group> bucket(LIGEN_N_BUCKETS);
+  for (int b = 0; b < LIGEN_N_BUCKETS; ++b) {
+    bucket[b].beg = (int)order.size();
+    for (int32_t l : members[b]) {
+      order.push_back(l);
+      const int N = ligands->h_atom_off[l + 1] - ligands->h_atom_off[l];
+      const int n = ligands->h_rot_off[l + 1] - ligands->h_rot_off[l];
+      bucket[b].max_atoms = std::max(bucket[b].max_atoms, N);
+      bucket[b].max_rot = std::max(bucket[b].max_rot, n);
+      bucket[b].max_frag = std::max(bucket[b].max_frag, n * (N / 2));
+    }
+    bucket[b].end = (int)order.size();
+  }
+
+  Arena ar;
+  const size_t o_coef = ar.take(grid_coef_bytes(grid));
+  const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
+  const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
+  const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
+  const size_t o_status = ar.take(4 * (size_t)L);
+  const size_t o_rs = ar.take(4 * (size_t)L * R);
+  const size_t o_rk = ar.take((size_t)L * R);
+  const size_t o_rc = ar.take((size_t)sh.rot * R);
+  const size_t o_order = ar.take(4 * order.size());
+  if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+  forget_orders(dev);   // the order region is overwritten below
+
+  LigandsDev lig;
+  lig.L = L;
+  lig.atom_off = ligands->atom_off; lig.xyz = ligands->xyz; lig.type = ligands->type;
+  lig.bonds = ligands->bonds; lig.rot_off = ligands->rot_off; lig.rot_edge = ligands->rot_edge;
+  float* coef = ar.at<float>(o_coef);
+  LG_CUDA(launch_grid_prep((const float*)grid->data, grid->nx, grid->ny, grid->nz, grid->nc, coef, s));
+  Packed pk{};
+  pk.xc = ar.at<float4>(o_xc);
+  pk.binfo = ar.at<uchar4>(o_binfo);
+  pk.frag = ar.at<uint8_t>(o_frag);
+  pk.status = ar.at<int32_t>(o_status);
+  LG_CUDA(launch_pack(lig, grid->nc, pk, s));
+  int32_t* d_order = ar.at<int32_t>(o_order);
+  LG_CUDA(cudaMemcpyAsync(d_order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, s));
+
+  DockArgs base{};
+  base.lig = lig;
+  base.pk = pk;
+  base.grid = make_view(grid, coef, params->out_penalty);
+  const float h = grid->spacing;
+  const int np[3] = {grid->nx, grid->ny, grid->nz};
+  for (int k = 0; k < 3; ++k) {
+    base.origin[k] = grid->origin[k];
+    base.center[k] = (float)((double)grid->origin[k] + (double)h * (np[k] - 1) / 2.0);
+  }
+  base.inv_h = (float)(1.0 / (double)h);
+  base.jitter = params->jitter;
+  base.seed = params->seed;
+  base.R = R;
+  base.n_rigid = params->n_rigid;
+  base.step_deg = params->torsion_step_deg;
+  base.n_theta = 360 / params->torsion_step_deg;
+  base.passes = params->passes;
+  base.res_score = ar.at<float>(o_rs);
+  base.res_k = ar.at<uint8_t>(o_rk);
+  base.res_cnt = ar.at<uint8_t>(o_rc);
+
+  static const int kCand[][2] = {{4, 32}, {4, 16}, {8, 16}, {8, 8}, {2, 64}};
+  cudaEvent_t e0, e1;
+  LG_CUDA(cudaEventCreate(&e0));
+  LG_CUDA(cudaEventCreate(&e1));
+  int result = LIGEN_OK;
+  for (int b = 0; b < LIGEN_N_BUCKETS && result == LIGEN_OK; ++b) {
+    const int cnt = bucket[b].end - bucket[b].beg;
+    if (cnt == 0) continue;
+    float best_ms = 0.f;
+    int best = -1;
+    for (int c = 0; c < (int)(sizeof kCand / sizeof kCand[0]); ++c) {
+      if (!valid_shape(kCand[c][0], kCand[c][1])) continue;
+      DockArgs a = base;
+      a.lanes = kCand[c][0];
+      a.rpc = kCand[c][1];
+      a.chunks = (R + a.rpc - 1) / a.rpc;
+      a.list = d_order + bucket[b].beg;
+      a.n_items = cnt * a.chunks;
+      a.queue = nullptr;
+      a.max_atoms = bucket[b].max_atoms;
+      a.max_rot = bucket[b].max_rot;
+      a.max_frag = bucket[b].max_frag;
+      float ms = 0.f;
+      for (int rep = 0; rep < 3; ++rep) {   // first run warms up
+        cudaError_t e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = launch_dock(a, 0, s, true);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e != cudaSuccess) {
+          result = cuda_fail(e, "autotune launch");
+          break;
+        }
+        if (rep == 1 || (rep == 2 && t < ms)) ms = t;
+      }
+      if (result != LIGEN_OK) break;
+      if (best < 0 || ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    if (result != LIGEN_OK || best < 0) break;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[dev][b].lanes = kCand[best][0];
+      g_tune[dev][b].rpc = kCand[best][1];
+    }
+    out_lanes[b] = kCand[best][0];
+    out_rpc[b] = kCand[best][1];
+    if (out_ms_per_ligand) out_ms_per_ligand[b] = best_ms / cnt;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return result;
 }
 
 int ligen_probe_gather(const float* records, int64_t n_records, int32_t bytes_per_load, int32_t loads_per_thread,
@@ -723,7 +1205,7 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
   da.res_k = ar.at<uint8_t>(o_rk);
   da.res_cnt = ar.at<uint8_t>(o_rc);
   da.trace = params->trace;
-  LG_CUDA(launch_dock(da, 0, s));
+  LG_CUDA(launch_dock(da, 0, s, true));
 
   TopkArgs ta{};
   ta.L = L; ta.R = R; ta.K = K; ta.step_deg = params->torsion_step_deg;

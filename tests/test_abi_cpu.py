@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(abi):
     for name in declared:
         assert hasattr(lib, name), name
     assert set(abi.SIGNATURES) == declared
-    assert lib.ligen_abi_version() == 1
+    assert lib.ligen_abi_version() == 2
 
 
 def _lig_struct(abi, arrays):
@@ -66,7 +66,7 @@ def _params(abi, **kw):
 @pytest.mark.parametrize("bad, code", [
     (dict(torsion_step_deg=7), -1), (dict(torsion_step_deg=1), -1), (dict(top_k=9), -1),
     (dict(restarts=0), -1), (dict(n_rigid=25), -1), (dict(passes=-1), -1), (dict(mode=1), -2),
-    (dict(jitter=float("nan")), -1),
+    (dict(jitter=float("nan")), -1), (dict(batching=2), -1),
 ])
 def test_bad_params_rejected_on_host(abi, bad, code):
     lib = abi.load()
@@ -114,6 +114,9 @@ def test_null_structs_rejected(abi):
     assert lib.ligen_score_poses(None, None, 1, None, 5.0, None, None) == -1
     assert lib.ligen_pack_ligands(None, 4, None, None, None, None, None) == -1
     assert lib.ligen_bucket_size(0, None, None, None, None) == -1
+    assert lib.ligen_tune_set(44, 8, 16) == -1 and lib.ligen_tune_set(0, 3, 16) == -1
+    assert lib.ligen_tune_set(0, 8, 10) == -1 and lib.ligen_tune_set(0, 4, 64) == -1
+    assert lib.ligen_autotune(None, None, None, 1, None, None, None) == -1
 
 
 def test_package_refuses_to_load_without_library(tmp_path):
