@@ -75,6 +75,7 @@ def lib():
                 "or_score_coords": (C.c_double, [P, P, P, C.c_double, P, P, P]),
                 "or_pose_coords": (None, [P, P, P, P, P]),
                 "or_score_pose": (C.c_double, [P, P, P, P, P, C.c_double, P, P, P]),
+                "or_pose_grad": (C.c_double, [P, P, P, P, P, C.c_double, P]),
                 "or_torsion_angle": (C.c_double, [C.c_int32, C.c_int32]),
                 "or_restart_init": (None, [P, P, C.c_int64, C.c_int64, P, P]),
                 "or_dock_ligand": (C.c_int32, [P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P, P, P]),
@@ -262,6 +263,16 @@ def score_pose(lig: OLigand, grid: OGrid, pose, penalty: float = 5.0, sensitivit
     s = lib().or_score_pose(C.byref(lig.s), C.byref(grid.s), _ptr(mask), _ptr(axis), _ptr(pose),
                             penalty, C.byref(D), _ptr(E), C.byref(G))
     return (float(s), float(D.value), E, float(G.value)) if sensitivity else (float(s), float(D.value), E)
+
+
+def pose_grad(lig: OLigand, grid: OGrid, pose, penalty: float = 5.0):
+    """(S, dS/dpose [7 + n]) of pose (t[3], q[4], theta[n]) in FP64."""
+    mask, axis = _frag_arrays(lig)
+    pose = np.ascontiguousarray(pose, np.float64)
+    g = np.zeros(7 + lig.n_rot)
+    S = lib().or_pose_grad(C.byref(lig.s), C.byref(grid.s), _ptr(mask), _ptr(axis), _ptr(pose), penalty,
+                           _ptr(g))
+    return float(S), g
 
 
 def torsion_angle(count: int, step_deg: int) -> float:

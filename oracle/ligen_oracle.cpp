@@ -420,6 +420,75 @@ double or_score_pose(const or_ligand* L, const or_grid* g, const uint8_t* mask, 
   return or_score_coords(L, g, x.data(), penalty, D, E, Gs);
 }
 
+// Analytic gradient of S(pose) = -sum_i E(x_i) with respect to the pose
+// parameters (t[3], q[4], theta[n]); returns S.
+//   x_i = R(q^) y_i + t, y_i = T_theta(X0)_i - c0, q^ = q / |q|.
+//   dS/dx_i = g_i = -grad E(x_i) (zero outside the box, one-sided at cell
+//   faces: the derivative inside the cell that holds x_i);
+//   dS/dt = sum_i g_i;
+//   dS/dq^_k = sum_i g_i . (dR/dq^_k) y_i, with R written as the polynomial
+//   in (w, x, y, z) of or_quat_to_mat, and dS/dq = (I - q^ q^T) dS/dq^ / |q|;
+//   dS/dtheta_b = sum_{i in M_b} g_i . (w_b x (x_i - x_v)), w_b the unit axis
+//   of bond b from x_u to x_v in the final pose: torsions commute, so theta_b
+//   may be taken as the last rotation applied.
+double or_pose_grad(const or_ligand* L, const or_grid* g, const uint8_t* mask, const int32_t* axis,
+                    const double* pose, double penalty, double* grad) {
+  const int N = L->n_atoms, n = L->n_rot;
+  std::vector<double> x(3 * (size_t)N);
+  or_pose_coords(L, mask, axis, pose, x.data());
+  // body coordinates y_i = R^T (x_i - t)
+  double qn = std::sqrt(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
+  double w = pose[3] / qn, qx = pose[4] / qn, qy = pose[5] / qn, qz = pose[6] / qn;
+  double m[9];
+  or_quat_to_mat(pose + 3, m);
+  // dR/dq^ for R(w,x,y,z) = [[1-2(y2+z2), 2(xy-wz), 2(xz+wy)], [2(xy+wz), 1-2(x2+z2), 2(yz-wx)],
+  //                          [2(xz-wy), 2(yz+wx), 1-2(x2+y2)]]
+  const double dR[4][9] = {
+      {0, -2 * qz, 2 * qy, 2 * qz, 0, -2 * qx, -2 * qy, 2 * qx, 0},
+      {0, 2 * qy, 2 * qz, 2 * qy, -4 * qx, -2 * w, 2 * qz, 2 * w, -4 * qx},
+      {-4 * qy, 2 * qx, 2 * w, 2 * qx, 0, 2 * qz, -2 * w, 2 * qz, -4 * qy},
+      {-4 * qz, -2 * w, 2 * qx, 2 * w, -4 * qz, 2 * qy, 2 * qx, 2 * qy, 0}};
+  for (int a = 0; a < 7 + n; ++a) grad[a] = 0.0;
+  double S = 0.0, dqh[4] = {0, 0, 0, 0};
+  std::vector<double> gi(3 * (size_t)N);
+  for (int i = 0; i < N; ++i) {
+    int32_t inb = 0;
+    double gr[3];
+    double e = or_trilinear_grad(g, L->type[i], &x[3 * i], gr, &inb);
+    if (!inb) e = penalty;
+    S -= e;
+    for (int a = 0; a < 3; ++a) {
+      gi[3 * i + a] = -gr[a];
+      grad[a] += -gr[a];
+    }
+    double d[3] = {x[3 * i] - pose[0], x[3 * i + 1] - pose[1], x[3 * i + 2] - pose[2]};
+    double y[3];
+    for (int r = 0; r < 3; ++r) y[r] = m[r] * d[0] + m[3 + r] * d[1] + m[6 + r] * d[2];
+    for (int k = 0; k < 4; ++k)
+      for (int r = 0; r < 3; ++r)
+        dqh[k] += gi[3 * i + r] * (dR[k][3 * r] * y[0] + dR[k][3 * r + 1] * y[1] + dR[k][3 * r + 2] * y[2]);
+  }
+  const double qh[4] = {w, qx, qy, qz};
+  double proj = 0.0;
+  for (int k = 0; k < 4; ++k) proj += qh[k] * dqh[k];
+  for (int k = 0; k < 4; ++k) grad[3 + k] = (dqh[k] - qh[k] * proj) / qn;
+  for (int b = 0; b < n; ++b) {
+    const int u = axis[2 * b], v = axis[2 * b + 1];
+    double om[3] = {x[3 * v] - x[3 * u], x[3 * v + 1] - x[3 * u + 1], x[3 * v + 2] - x[3 * u + 2]};
+    double len = std::sqrt(om[0] * om[0] + om[1] * om[1] + om[2] * om[2]);
+    for (int a = 0; a < 3; ++a) om[a] /= len;
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) {
+      if (!mask[(size_t)b * N + i]) continue;
+      double d[3] = {x[3 * i] - x[3 * v], x[3 * i + 1] - x[3 * v + 1], x[3 * i + 2] - x[3 * v + 2]};
+      double c[3] = {om[1] * d[2] - om[2] * d[1], om[2] * d[0] - om[0] * d[2], om[0] * d[1] - om[1] * d[0]};
+      acc += gi[3 * i] * c[0] + gi[3 * i + 1] * c[1] + gi[3 * i + 2] * c[2];
+    }
+    grad[7 + b] = acc;
+  }
+  return S;
+}
+
 // Torsion angle of `count` increments of step_deg degrees, wrapped to
 // [-180, 180) degrees, in radians.
 double or_torsion_angle(int32_t count, int32_t step_deg) {

@@ -145,3 +145,74 @@ def test_position_sensitivity_bounds_relative_coordinate_noise(oracle_lib, small
             noisy = x * (1 + eps * rng.uniform(-1, 1, x.shape))   # origin is (0, 0, 0) here
             S2 = oracle_lib.score_coords(lig, og, noisy, 5.0)[0]
             assert abs(S2 - S) <= 1.01 * eps * Gs + 1e-12
+
+
+def _face_safe(lig, og, oracle_lib, pose, a, h, spacing, origin, dims):
+    """True when moving parameter a by +-h keeps every atom inside one cell
+    and on the same side of the box boundary (no kink in the interval)."""
+    cells = []
+    for sgn in (-1, 1):
+        p = pose.copy()
+        p[a] += sgn * h
+        u = (oracle_lib.pose_coords(lig, p) - np.asarray(origin)) / spacing
+        inside = np.all((u >= 0) & (u <= np.asarray(dims) - 1), axis=1)
+        cells.append((np.floor(u).astype(int), inside))
+    return np.array_equal(cells[0][0], cells[1][0]) and np.array_equal(cells[0][1], cells[1][1])
+
+
+def test_pose_gradient_matches_central_differences(oracle_lib, small32, screen_sample):
+    import oracle
+    rng = np.random.default_rng(12)
+    h = 1e-4
+    checked = 0
+    for _, lib, grid in (small32, screen_sample):
+        og = oracle.OGrid.from_grid(grid)
+        nx, ny, nz, _ = grid.dims
+        for l in range(0, lib.n_ligands, 2):
+            lig = oracle.OLigand.from_library(lib, l)
+            pose = np.concatenate([grid.center + rng.uniform(-2, 2, 3), rng.normal(size=4),
+                                   rng.uniform(-np.pi, np.pi, lig.n_rot)])
+            S, g = oracle_lib.pose_grad(lig, og, pose)
+            assert abs(S - oracle_lib.score_pose(lig, og, pose)[0]) <= 1e-12 * max(1, abs(S))
+            for a in range(7 + lig.n_rot):
+                if not _face_safe(lig, og, oracle_lib, pose, a, h, grid.spacing, grid.origin, (nx, ny, nz)):
+                    continue
+                p1, p0 = pose.copy(), pose.copy()
+                p1[a] += h
+                p0[a] -= h
+                fd = (oracle_lib.score_pose(lig, og, p1)[0] - oracle_lib.score_pose(lig, og, p0)[0]) / (2 * h)
+                assert abs(fd - g[a]) <= 1e-5 * (1 + np.abs(g).max()), (l, a, fd, g[a])
+                checked += 1
+    assert checked > 300
+
+
+def test_pose_gradient_invariances(oracle_lib, small32):
+    # scaling q leaves the pose unchanged: dS/dq is orthogonal to q; a pure
+    # translation field E = a + b.x gives dS/dt = -N_in * b
+    import oracle
+    _, lib, grid = small32
+    og = oracle.OGrid.from_grid(grid)
+    rng = np.random.default_rng(13)
+    for l in range(8):
+        lig = oracle.OLigand.from_library(lib, l)
+        pose = np.concatenate([grid.center, rng.normal(size=4), rng.uniform(-np.pi, np.pi, lig.n_rot)])
+        _, g = oracle_lib.pose_grad(lig, og, pose)
+        assert abs(g[3:7] @ pose[3:7]) <= 1e-10 * (1 + np.abs(g).max())
+    nz, ny, nx, nc = 30, 30, 30, 4
+    zz, yy, xx = np.meshgrid(*(0.5 * np.arange(30),) * 3, indexing="ij")
+    b = np.array([0.2, -0.4, 0.7])
+    vals = np.repeat((1.0 + b[0] * xx + b[1] * yy + b[2] * zz)[..., None], nc, axis=3)
+    lin = oracle.OGrid(vals, (0.0, 0.0, 0.0), 0.5)
+    lig = oracle.OLigand.from_library(lib, 0)
+    pose = np.concatenate([[7.2, 7.3, 7.4], rng.normal(size=4), rng.uniform(-np.pi, np.pi, lig.n_rot)])
+    _, g = oracle_lib.pose_grad(lig, lin, pose)
+    np.testing.assert_allclose(g[:3], -lig.n_atoms * b, atol=1e-10)
+    # and then rotations and torsions cannot change a linear field's sum
+    # except through the atom positions' moment: compare with differences
+    h = 1e-5
+    for a in range(3, 7 + lig.n_rot):
+        p1, p0 = pose.copy(), pose.copy()
+        p1[a] += h
+        p0[a] -= h
+        fd = (oracle_lib.score_pose(lig, lin, p1)[0] - oracle_lib.score_pose(lig, lin, p0)[0]) / (2 * h)
+        assert abs(fd - g[a]) <= 1e-7 * (1 + abs(g[a]))
