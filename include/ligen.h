@@ -226,6 +226,31 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                       int32_t poses_per_ligand, const float* poses, float out_penalty,
                       float* out_scores, void* stream);
 
+/* Gradient of the pose score (task text: differentiation of the score with
+ * respect to translation, rotation and torsions). For pose p of ligand l
+ * (packing as ligen_score_poses), out_scores[l][p] = S and out_grads holds
+ * dS/dpose in the pose's own slot: dS/dt[3], dS/dq[4] (through q/|q|, so
+ * orthogonal to q), dS/dtheta[n_l]. E is differentiated inside the cell that
+ * holds the atom (one-sided at cell faces); atoms outside the box contribute
+ * no gradient. Atom coordinates are rebuilt from the pose, never stored.
+ * Invalid ligands: S = -INFINITY, zero gradient. `poses`, `out_scores` and
+ * `out_grads` share one memory space. */
+int ligen_pose_grad(const ligen_ligands_t* ligands, const ligen_grid_t* grid, int32_t poses_per_ligand,
+                    const float* poses, float out_penalty, float* out_scores, float* out_grads, void* stream);
+
+/* Gradient refinement of poses in place: for every pose, `steps` iterations
+ * of normalised-step projected ascent. An iteration moves t by step_t (A)
+ * along dS/dt / |dS/dt| (then clamps t to the grid box), q^ = q/|q| by step_q
+ * along dS/dq / |dS/dq| (then renormalises), theta by step_theta (rad) along
+ * dS/dtheta / |dS/dtheta| (then wraps to [-pi, pi)); a block with a zero
+ * gradient does not move. The move is kept when it raises S; otherwise the
+ * three step sizes are halved. On return the pose has w >= 0 and
+ * out_scores[l][p] holds its S. out_accept (nullable, [L * P][steps], same
+ * memory space) records 1 for kept moves. */
+int ligen_refine_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, int32_t poses_per_ligand,
+                       float* poses, float out_penalty, int32_t steps, float step_t, float step_q, float step_theta,
+                       float* out_scores, int8_t* out_accept, void* stream);
+
 /* The ligand packer on its own, for inspection (paper §3: ligands are
  * classified by atom count and rotamer count).
  *   frag_bits [sum n][8]  bit i of word i/32 set when atom i is on the moving

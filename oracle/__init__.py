@@ -76,6 +76,8 @@ def lib():
                 "or_pose_coords": (None, [P, P, P, P, P]),
                 "or_score_pose": (C.c_double, [P, P, P, P, P, C.c_double, P, P, P]),
                 "or_pose_grad": (C.c_double, [P, P, P, P, P, C.c_double, P]),
+                "or_refine_pose": (C.c_double, [P, P, P, P, P, C.c_double, C.c_int32, C.c_double, C.c_double,
+                                                C.c_double, P, P]),
                 "or_torsion_angle": (C.c_double, [C.c_int32, C.c_int32]),
                 "or_restart_init": (None, [P, P, C.c_int64, C.c_int64, P, P]),
                 "or_dock_ligand": (C.c_int32, [P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P, P, P]),
@@ -273,6 +275,18 @@ def pose_grad(lig: OLigand, grid: OGrid, pose, penalty: float = 5.0):
     S = lib().or_pose_grad(C.byref(lig.s), C.byref(grid.s), _ptr(mask), _ptr(axis), _ptr(pose), penalty,
                            _ptr(g))
     return float(S), g
+
+
+def refine_pose(lig: OLigand, grid: OGrid, pose, steps: int = 50, step_t: float = 0.1, step_q: float = 0.02,
+                step_theta: float = 0.05, penalty: float = 5.0):
+    """FP64 gradient refinement: (final pose, final S, accept [steps], gap [steps])."""
+    mask, axis = _frag_arrays(lig)
+    pose = np.array(pose, np.float64)
+    acc = np.zeros(steps, np.int8)
+    gap = np.zeros(steps)
+    S = lib().or_refine_pose(C.byref(lig.s), C.byref(grid.s), _ptr(mask), _ptr(axis), _ptr(pose), penalty,
+                             steps, step_t, step_q, step_theta, _ptr(acc), _ptr(gap))
+    return pose, float(S), acc, gap
 
 
 def torsion_angle(count: int, step_deg: int) -> float:

@@ -489,6 +489,65 @@ double or_pose_grad(const or_ligand* L, const or_grid* g, const uint8_t* mask, c
   return S;
 }
 
+// Gradient refinement of one pose: `steps` iterations of normalised-step
+// projected ascent. Each iteration proposes
+//   t' = clamp_box(t + st * g_t / |g_t|)
+//   q' = (q^ + sq * g_q / |g_q|) / |.|            (q^ = q / |q|)
+//   theta' = wrap(theta + sth * g_theta / |g_theta|)
+// from the gradient g at the current pose (a block with a zero gradient does
+// not move), and accepts it when S(pose') > S(pose); otherwise st, sq and sth
+// are halved and the pose is kept. The final quaternion is made w >= 0.
+// accept[s] = 1 when step s was accepted; gap[s] = S(pose') - S(pose).
+// Returns the final score.
+double or_refine_pose(const or_ligand* L, const or_grid* g, const uint8_t* mask, const int32_t* axis,
+                      double* pose, double penalty, int32_t steps, double st, double sq, double sth,
+                      int8_t* accept, double* gap) {
+  const int n = L->n_rot, plen = 7 + n;
+  std::vector<double> grad(plen), cand(plen);
+  const double lo[3] = {g->origin[0], g->origin[1], g->origin[2]};
+  const double hi[3] = {g->origin[0] + g->spacing * (g->nx - 1), g->origin[1] + g->spacing * (g->ny - 1),
+                        g->origin[2] + g->spacing * (g->nz - 1)};
+  double S = or_pose_grad(L, g, mask, axis, pose, penalty, grad.data());
+  for (int s = 0; s < steps; ++s) {
+    double nt = 0, nq = 0, nth = 0;
+    for (int a = 0; a < 3; ++a) nt += grad[a] * grad[a];
+    for (int a = 3; a < 7; ++a) nq += grad[a] * grad[a];
+    for (int a = 7; a < plen; ++a) nth += grad[a] * grad[a];
+    nt = std::sqrt(nt); nq = std::sqrt(nq); nth = std::sqrt(nth);
+    double qn = std::sqrt(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
+    for (int a = 0; a < 3; ++a) {
+      double v = pose[a] + (nt > 0 ? st * grad[a] / nt : 0.0);
+      cand[a] = std::min(std::max(v, lo[a]), hi[a]);
+    }
+    double qq[4], qm = 0;
+    for (int a = 0; a < 4; ++a) {
+      qq[a] = pose[3 + a] / qn + (nq > 0 ? sq * grad[3 + a] / nq : 0.0);
+      qm += qq[a] * qq[a];
+    }
+    qm = std::sqrt(qm);
+    for (int a = 0; a < 4; ++a) cand[3 + a] = qq[a] / qm;
+    for (int a = 7; a < plen; ++a) {
+      double v = pose[a] + (nth > 0 ? sth * grad[a] / nth : 0.0);
+      v = std::fmod(v + kPi, 2.0 * kPi);
+      if (v < 0) v += 2.0 * kPi;
+      cand[a] = v - kPi;
+    }
+    double S2 = or_score_pose(L, g, mask, axis, cand.data(), penalty, nullptr, nullptr, nullptr);
+    if (gap) gap[s] = S2 - S;
+    if (S2 > S) {
+      for (int a = 0; a < plen; ++a) pose[a] = cand[a];
+      S = or_pose_grad(L, g, mask, axis, pose, penalty, grad.data());
+      if (accept) accept[s] = 1;
+    } else {
+      st *= 0.5; sq *= 0.5; sth *= 0.5;
+      if (accept) accept[s] = 0;
+    }
+  }
+  if (pose[3] < 0)
+    for (int a = 3; a < 7; ++a) pose[a] = -pose[a];
+  return S;
+}
+
 // Torsion angle of `count` increments of step_deg degrees, wrapped to
 // [-180, 180) degrees, in radians.
 double or_torsion_angle(int32_t count, int32_t step_deg) {

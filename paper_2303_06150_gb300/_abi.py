@@ -52,6 +52,9 @@ SIGNATURES = {
     "ligen_dock_batch": (C.c_int, [P, P, P, P, P]),
     "ligen_dock_batch_static": (C.c_int, [P, P, P, P, P]),
     "ligen_score_poses": (C.c_int, [P, P, C.c_int32, P, C.c_float, P, P]),
+    "ligen_pose_grad": (C.c_int, [P, P, C.c_int32, P, C.c_float, P, P, P]),
+    "ligen_refine_poses": (C.c_int, [P, P, C.c_int32, P, C.c_float, C.c_int32, C.c_float, C.c_float, C.c_float,
+                                     P, P, P]),
     "ligen_pack_ligands": (C.c_int, [P, C.c_int32, P, P, P, P, P]),
     "ligen_bucket_size": (C.c_int64, [C.c_int32, P, P, P, P]),
     "ligen_probe_gather": (C.c_int, [P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P]),

@@ -192,6 +192,63 @@ def score_poses(ligands: Ligands, grid: PocketGrid, poses: torch.Tensor, poses_p
     return out
 
 
+def pose_grad(ligands: Ligands, grid: PocketGrid, poses: torch.Tensor, poses_per_ligand: int,
+              out_penalty: float = 5.0):
+    """ligen_pose_grad: (scores [L, P], dS/dpose in the packing of `poses`)."""
+    lib = _abi.load()
+    L = ligands.n_ligands
+    scores = _empty((L, poses_per_ligand), torch.float32, poses.device)
+    grads = _empty(tuple(poses.shape), torch.float32, poses.device)
+    check(lib.ligen_pose_grad(C.byref(ligands._s), C.byref(grid._s), poses_per_ligand, _ptr(poses),
+                              float(out_penalty), _ptr(scores), _ptr(grads), _stream_handle(poses.device)))
+    return scores, grads
+
+
+def refine_poses(ligands: Ligands, grid: PocketGrid, poses: torch.Tensor, poses_per_ligand: int, *,
+                 steps: int = 50, step_t: float = 0.1, step_q: float = 0.02, step_theta: float = 0.05,
+                 out_penalty: float = 5.0, accept: bool = False, inplace: bool = False):
+    """ligen_refine_poses: (refined poses, scores [L, P], accept flags or None)."""
+    lib = _abi.load()
+    L = ligands.n_ligands
+    out = poses if inplace else poses.clone()
+    scores = _empty((L, poses_per_ligand), torch.float32, poses.device)
+    acc = _empty((L * poses_per_ligand, steps), torch.int8, poses.device) if accept else None
+    check(lib.ligen_refine_poses(C.byref(ligands._s), C.byref(grid._s), poses_per_ligand, _ptr(out),
+                                 float(out_penalty), int(steps), float(step_t), float(step_q), float(step_theta),
+                                 _ptr(scores), _ptr(acc), _stream_handle(poses.device)))
+    return out, scores, acc
+
+
+def _pose_lengths(ligands: Ligands, poses_per_ligand: int, device) -> torch.Tensor:
+    n = torch.from_numpy(np.diff(ligands.h_rot_off).astype(np.int64) + 7)
+    return n.repeat_interleave(poses_per_ligand).to(device)
+
+
+class PoseScore(torch.autograd.Function):
+    """Differentiable pose score: forward ligen_score_poses, backward
+    ligen_pose_grad (coordinates rebuilt in the backward pass)."""
+
+    @staticmethod
+    def forward(ctx, poses, ligands, grid, poses_per_ligand, out_penalty):
+        ctx.save_for_backward(poses)
+        ctx.args = (ligands, grid, poses_per_ligand, out_penalty)
+        return score_poses(ligands, grid, poses.detach(), poses_per_ligand, out_penalty)
+
+    @staticmethod
+    def backward(ctx, grad_scores):
+        (poses,) = ctx.saved_tensors
+        ligands, grid, P, pen = ctx.args
+        _, grads = pose_grad(ligands, grid, poses.detach().contiguous(), P, pen)
+        weight = grad_scores.reshape(-1).repeat_interleave(_pose_lengths(ligands, P, poses.device))
+        return grads * weight, None, None, None, None
+
+
+def pose_score(poses: torch.Tensor, ligands: Ligands, grid: PocketGrid, poses_per_ligand: int,
+               out_penalty: float = 5.0) -> torch.Tensor:
+    """Scores [L, P] of packed poses, differentiable with respect to `poses`."""
+    return PoseScore.apply(poses, ligands, grid, poses_per_ligand, out_penalty)
+
+
 def pack_ligands(ligands: Ligands, n_channels: int):
     """ligen_pack_ligands: (frag_bits [sum n, 8] uint32 as int32, axis [sum n, 2], bucket [L], status [L])."""
     lib = _abi.load()

@@ -168,4 +168,34 @@ __device__ __forceinline__ float grid_sample(const GridView& g, float ux, float 
   return e;
 }
 
+// Value and gradient (per grid unit) of channel `c` at grid-unit position u:
+// the derivative of the cell's trilinear polynomial, zero outside the box.
+__device__ __forceinline__ float grid_sample_grad(const GridView& g, float ux, float uy, float uz, int c,
+                                                  float* gx, float* gy, float* gz) {
+  bool inb = (ux >= 0.f) & (ux <= g.mx) & (uy >= 0.f) & (uy <= g.my) & (uz >= 0.f) & (uz <= g.mz);
+  float e = g.penalty;
+  *gx = *gy = *gz = 0.f;
+  if (inb) {
+    float fx = fminf(floorf(ux), g.mx - 1.f);
+    float fy = fminf(floorf(uy), g.my - 1.f);
+    float fz = fminf(floorf(uz), g.mz - 1.f);
+    int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+    float dx = ux - fx, dy = uy - fy, dz = uz - fz;
+    const float* rec = g.coef + ((size_t)c * g.cz * g.cy * g.cx + (size_t)((iz * g.cy + iy) * g.cx + ix)) * 8;
+    float a[8];
+    ld_global_v8(rec, a);
+    float t1 = fmaf(dz, a[7], a[4]);
+    float t2 = fmaf(dy, t1, a[1]);
+    t2 = fmaf(dz, a[5], t2);
+    float t3 = fmaf(dz, a[6], a[2]);
+    e = fmaf(dz, a[3], a[0]);
+    e = fmaf(dy, t3, e);
+    e = fmaf(dx, t2, e);
+    *gx = t2;                                              // ax + axy fy + axz fz + axyz fy fz
+    *gy = fmaf(dx, t1, t3);                                // ay + axy fx + ayz fz + axyz fx fz
+    *gz = fmaf(dx, fmaf(dy, a[7], a[5]), fmaf(dy, a[6], a[3]));  // az + axz fx + ayz fy + axyz fx fy
+  }
+  return e;
+}
+
 }  // namespace ligen

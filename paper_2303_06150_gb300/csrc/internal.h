@@ -83,6 +83,24 @@ struct ScoreArgs {
   float* out_scores;
 };
 
+struct GradArgs {
+  LigandsDev lig;
+  Packed pk;
+  GridView grid;
+  float origin[3];
+  float inv_h;
+  int P;              // poses per ligand
+  int max_atoms;
+  const float* poses;       // gradient: input poses
+  float* inout_poses;       // refinement: poses, refined in place
+  float* out_scores;        // [L][P]
+  float* out_grads;         // gradient: same packing as poses
+  int steps;                // refinement iterations
+  float step_t, step_q, step_theta;
+  float box_lo[3], box_hi[3];
+  int8_t* out_accept;       // refinement: [L * P][steps], optional
+};
+
 cudaError_t launch_grid_prep(const float* values, int nx, int ny, int nz, int nc, float* coef,
                              cudaStream_t s);
 cudaError_t launch_pack(const LigandsDev& lig, int nc, const Packed& out, cudaStream_t s);
@@ -100,6 +118,9 @@ cudaError_t dock_set_smem_limit(int lanes, int n_theta, size_t smem);
 cudaError_t dock_occupancy(int lanes, int n_theta, int rpc, size_t smem, int* blocks_per_sm);
 cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s);
+size_t grad_smem_bytes(int max_atoms);
+// refine = false: dS/dpose of every pose; true: gradient refinement in place.
+cudaError_t launch_grad(const GradArgs& a, bool refine, cudaStream_t s);
 cudaError_t launch_probe(const float* rec, uint32_t n_rec, int bytes, int iters, uint64_t seed, float* sink,
                          int blocks, cudaStream_t s);
 int probe_streams();

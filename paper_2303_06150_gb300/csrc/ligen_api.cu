@@ -804,6 +804,122 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
   return LIGEN_OK;
 }
 
+// Shared body of ligen_pose_grad and ligen_refine_poses: stage inputs, build
+// the grid records, pack the ligands, run the gradient kernel, copy back.
+static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, int32_t poses_per_ligand,
+                     const float* poses_in, float* poses_inout, float out_penalty, float* out_scores,
+                     float* out_grads, int refine, int32_t steps, float step_t, float step_q, float step_theta,
+                     int8_t* out_accept, void* stream) {
+  g_err.clear();
+  int rc;
+  LibShape sh;
+  if ((rc = check_ligands(ligands, 0, &sh)) != LIGEN_OK) return rc;
+  if ((rc = check_grid(grid)) != LIGEN_OK) return rc;
+  if (poses_per_ligand < 0) return fail(LIGEN_ERR_INVALID_ARG, "poses_per_ligand < 0");
+  if (!std::isfinite(out_penalty)) return fail(LIGEN_ERR_INVALID_ARG, "out_penalty not finite");
+  if (refine) {
+    if (steps < 0 || steps > 100000) return fail(LIGEN_ERR_INVALID_ARG, "steps must be 0..100000");
+    if (!(step_t >= 0.f) || !(step_q >= 0.f) || !(step_theta >= 0.f) || !std::isfinite(step_t) ||
+        !std::isfinite(step_q) || !std::isfinite(step_theta))
+      return fail(LIGEN_ERR_INVALID_ARG, "step sizes must be finite and >= 0");
+  }
+  const int L = ligands->n_ligands;
+  if (L == 0 || poses_per_ligand == 0) return LIGEN_OK;
+  const float* pin = refine ? poses_inout : poses_in;
+  if (!pin || !out_scores || (!refine && !out_grads))
+    return fail(LIGEN_ERR_INVALID_ARG, "poses and outputs are required");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int lhost = space_of({ligands->atom_off, ligands->xyz, ligands->type, ligands->bonds,
+                              ligands->rot_off, ligands->rot_edge});
+  const int ghost = space_of({grid->data});
+  const int ohost = space_of({pin, out_scores, out_grads, out_accept});
+  if (lhost < 0 || ohost < 0) return fail(LIGEN_ERR_INVALID_ARG, "arrays mix host and device memory");
+  const size_t pose_floats = (size_t)poses_per_ligand * (7 * (size_t)L + sh.rot);
+  const size_t nposes = (size_t)poses_per_ligand * L;
+  Arena ar;
+  LigandPlan lp;
+  plan_ligands(ar, ligands, sh, lhost == 1, &lp);
+  const size_t o_gval = ghost ? ar.take(grid_values_bytes(grid)) : 0;
+  const size_t o_coef = ar.take(grid_coef_bytes(grid));
+  const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
+  const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
+  const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
+  const size_t o_status = ar.take(4 * (size_t)L);
+  size_t o_poses = 0, o_scores = 0, o_grads = 0, o_acc = 0;
+  if (ohost) {
+    o_poses = ar.take(4 * pose_floats);
+    o_scores = ar.take(4 * nposes);
+    if (!refine) o_grads = ar.take(4 * pose_floats);
+    if (out_accept) o_acc = ar.take(nposes * (size_t)steps);
+  }
+  if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+  LigandsDev lig;
+  if ((rc = stage_ligands(ar, ligands, sh, lp, s, &lig)) != LIGEN_OK) return rc;
+  const float* gvals = (const float*)grid->data;
+  if (ghost) {
+    LG_CUDA(cudaMemcpyAsync(ar.base + o_gval, grid->data, grid_values_bytes(grid), cudaMemcpyHostToDevice, s));
+    gvals = ar.at<float>(o_gval);
+  }
+  float* d_poses = const_cast<float*>(pin);
+  if (ohost) {
+    LG_CUDA(cudaMemcpyAsync(ar.base + o_poses, pin, 4 * pose_floats, cudaMemcpyHostToDevice, s));
+    d_poses = ar.at<float>(o_poses);
+  }
+  float* coef = ar.at<float>(o_coef);
+  LG_CUDA(launch_grid_prep(gvals, grid->nx, grid->ny, grid->nz, grid->nc, coef, s));
+  Packed pk{};
+  pk.xc = ar.at<float4>(o_xc);
+  pk.binfo = ar.at<uchar4>(o_binfo);
+  pk.frag = ar.at<uint8_t>(o_frag);
+  pk.status = ar.at<int32_t>(o_status);
+  LG_CUDA(launch_pack(lig, grid->nc, pk, s));
+  GradArgs ga{};
+  ga.lig = lig;
+  ga.pk = pk;
+  ga.grid = make_view(grid, coef, out_penalty);
+  for (int k = 0; k < 3; ++k) ga.origin[k] = grid->origin[k];
+  ga.inv_h = (float)(1.0 / (double)grid->spacing);
+  ga.P = poses_per_ligand;
+  ga.max_atoms = sh.max_atoms;
+  ga.poses = d_poses;
+  ga.inout_poses = d_poses;
+  ga.out_scores = ohost ? ar.at<float>(o_scores) : out_scores;
+  ga.out_grads = refine ? nullptr : (ohost ? ar.at<float>(o_grads) : out_grads);
+  ga.steps = steps;
+  ga.step_t = step_t;
+  ga.step_q = step_q;
+  ga.step_theta = step_theta;
+  const int np[3] = {grid->nx, grid->ny, grid->nz};
+  for (int k = 0; k < 3; ++k) {
+    ga.box_lo[k] = grid->origin[k];
+    ga.box_hi[k] = (float)((double)grid->origin[k] + (double)grid->spacing * (np[k] - 1));
+  }
+  ga.out_accept = out_accept ? (ohost ? ar.at<int8_t>(o_acc) : out_accept) : nullptr;
+  LG_CUDA(launch_grad(ga, refine != 0, s));
+  if (ohost) {
+    LG_CUDA(cudaMemcpyAsync(out_scores, ga.out_scores, 4 * nposes, cudaMemcpyDeviceToHost, s));
+    if (refine) LG_CUDA(cudaMemcpyAsync(poses_inout, d_poses, 4 * pose_floats, cudaMemcpyDeviceToHost, s));
+    else LG_CUDA(cudaMemcpyAsync(out_grads, ga.out_grads, 4 * pose_floats, cudaMemcpyDeviceToHost, s));
+    if (out_accept)
+      LG_CUDA(cudaMemcpyAsync(out_accept, ga.out_accept, nposes * (size_t)steps, cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaStreamSynchronize(s));
+  }
+  return LIGEN_OK;
+}
+
+int ligen_pose_grad(const ligen_ligands_t* ligands, const ligen_grid_t* grid, int32_t poses_per_ligand,
+                    const float* poses, float out_penalty, float* out_scores, float* out_grads, void* stream) {
+  return grad_call(ligands, grid, poses_per_ligand, poses, nullptr, out_penalty, out_scores, out_grads, 0, 0, 0.f,
+                   0.f, 0.f, nullptr, stream);
+}
+
+int ligen_refine_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, int32_t poses_per_ligand,
+                       float* poses, float out_penalty, int32_t steps, float step_t, float step_q, float step_theta,
+                       float* out_scores, int8_t* out_accept, void* stream) {
+  return grad_call(ligands, grid, poses_per_ligand, nullptr, poses, out_penalty, out_scores, nullptr, 1, steps,
+                   step_t, step_q, step_theta, out_accept, stream);
+}
+
 int ligen_pack_ligands(const ligen_ligands_t* ligands, int32_t n_channels, uint32_t* frag_bits, int32_t* axis,
                        int32_t* bucket, int32_t* status, void* stream) {
   g_err.clear();

@@ -137,3 +137,31 @@ def test_top_k_order(oracle_lib):
         K = int(rng.integers(1, 40))
         ref = sorted(range(40), key=lambda i: (-s[i], i))[:K]
         assert oracle_lib.top_k(s, K).tolist() == ref
+
+
+def test_refinement_is_monotone_and_consistent(oracle_lib, small32):
+    """Accepted steps raise the score, rejected steps halve the steps; the
+    returned pose re-scores to the returned score (independent scorer)."""
+    w, lib, grid = small32
+    og = oracle_lib.OGrid.from_grid(grid)
+    samp = indep.trilinear_sampler(grid.values, grid.origin, grid.spacing)
+    res = oracle_lib.dock_library(lib, grid, w["search"], ligands=range(0, 32, 4))
+    for r_ in res:
+        lig, _, frags = _setup(lib, grid, r_["ligand"])
+        for k in range(2):
+            p0 = r_["top_pose"][k]
+            s0 = oracle_lib.score_pose(lig, og, p0)[0]
+            pose, S, acc, gap = oracle_lib.refine_pose(lig, og, p0, steps=20)
+            assert S >= s0 - 1e-12
+            assert np.all(gap[acc == 1] > 0) and np.all(gap[acc == 0] <= 0)
+            assert pose[3] >= 0 and abs(np.linalg.norm(pose[3:7]) - 1) < 1e-12
+            S2, D = _indep_score(lig, samp, frags, pose[:3], indep.rot_from_wxyz(pose[3:7]), pose[7:], 5.0)
+            assert abs(S2 - S) <= 1e-10 * D
+    # a first step along the gradient of a smooth field is accepted
+    lig = oracle_lib.OLigand.from_library(lib, 0)
+    zz, yy, xx = np.meshgrid(*(0.5 * np.arange(40),) * 3, indexing="ij")
+    vals = np.repeat((-(0.05 * xx + 0.03 * yy - 0.02 * zz))[..., None], 4, axis=3)
+    lin = oracle_lib.OGrid(vals, (0.0, 0.0, 0.0), 0.5)
+    p0 = np.concatenate([grid.center, [1, 0, 0, 0], np.zeros(lig.n_rot)])
+    _, S, acc, _ = oracle_lib.refine_pose(lig, lin, p0, steps=5)
+    assert acc[0] == 1 and S > oracle_lib.score_pose(lig, lin, p0)[0]
