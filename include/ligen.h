@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define LIGEN_ABI_VERSION 2
+#define LIGEN_ABI_VERSION 3
 #define LIGEN_MAX_ATOMS 256
 #define LIGEN_MAX_ROT 32
 #define LIGEN_MAX_CHANNELS 64
@@ -138,6 +138,17 @@ typedef struct ligen_grid {
 #define LIGEN_BATCH_BUCKETS 1
 #define LIGEN_N_BUCKETS 44 /* 4 atom classes x 11 rotamer classes */
 
+/* How the docking kernel stores the grid it samples (built from the
+ * caller's FP32 grid inside the call; coordinates and sums stay FP32).
+ *   LIGEN_GRID_F32   32 bytes per (cell, channel): the FP32 coefficients of
+ *                    the cell's trilinear polynomial;
+ *   LIGEN_GRID_F16   16 bytes: the 8 corner values in FP16;
+ *   LIGEN_GRID_BF16  16 bytes: the 8 corner values in BF16.
+ * The 16-bit formats run with 4 or 8 lanes per restart. */
+#define LIGEN_GRID_F32 0
+#define LIGEN_GRID_F16 1
+#define LIGEN_GRID_BF16 2
+
 typedef struct ligen_params {
   int32_t restarts;
   int32_t n_rigid;
@@ -153,8 +164,16 @@ typedef struct ligen_params {
   int16_t* trace;
   int32_t* top_restart;
   float* stage_ms;
-  int32_t batching;   /* LIGEN_BATCH_PLAIN or LIGEN_BATCH_BUCKETS */
-  int32_t reserved2;
+  int32_t batching;     /* LIGEN_BATCH_PLAIN or LIGEN_BATCH_BUCKETS */
+  int32_t grid_format;  /* LIGEN_GRID_F32, LIGEN_GRID_F16 or LIGEN_GRID_BF16 */
+  int32_t rescore_fp64; /* 1: re-score the K kept poses of every ligand in
+                           FP64 on the GPU (from the caller's FP32 grid
+                           values and coordinates) and re-rank them by that
+                           score (ties: lower restart); out_scores then
+                           holds the FP64 scores rounded to FP32 */
+  int32_t reserved3;
+  double* scores_f64;   /* optional [L][K], same memory space as out_scores:
+                           the FP64 scores (needs rescore_fp64 = 1) */
 } ligen_params_t;
 
 /* Dock every ligand (paper §2, the dock task; cost per §3 follows atoms and

@@ -23,6 +23,9 @@ LIGEN_N_STAGES = 5
 LIGEN_BATCH_PLAIN = 0
 LIGEN_BATCH_BUCKETS = 1
 LIGEN_N_BUCKETS = 44
+LIGEN_GRID_F32 = 0
+LIGEN_GRID_F16 = 1
+LIGEN_GRID_BF16 = 2
 STAGE_NAMES = ("h2d", "grid_prep", "pack", "dock", "topk_d2h")
 
 P = C.c_void_p
@@ -44,7 +47,8 @@ class ParamsT(C.Structure):
                 ("passes", C.c_int32), ("top_k", C.c_int32), ("mode", C.c_int32), ("seed", C.c_uint64),
                 ("jitter", C.c_float), ("out_penalty", C.c_float), ("stream", P), ("status", P),
                 ("trace", P), ("top_restart", P), ("stage_ms", P), ("batching", C.c_int32),
-                ("reserved2", C.c_int32)]
+                ("grid_format", C.c_int32), ("rescore_fp64", C.c_int32), ("reserved3", C.c_int32),
+                ("scores_f64", P)]
 
 
 # Every function include/ligen.h declares, with its ctypes signature.

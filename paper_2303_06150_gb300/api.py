@@ -115,6 +115,7 @@ class DockResult:
     trace: torch.Tensor | None   # flat int16
     top_restart: torch.Tensor | None
     stage_ms: np.ndarray | None
+    scores_f64: torch.Tensor | None = None
 
     def ligand_poses(self, rot_off, l: int) -> torch.Tensor:
         K = self.scores.shape[1]
@@ -124,16 +125,21 @@ class DockResult:
 
 
 BATCHING = {"plain": _abi.LIGEN_BATCH_PLAIN, "buckets": _abi.LIGEN_BATCH_BUCKETS}
+GRID_FORMATS = {"f32": _abi.LIGEN_GRID_F32, "f16": _abi.LIGEN_GRID_F16, "bf16": _abi.LIGEN_GRID_BF16}
 
 
 def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_step_deg: int, passes: int,
                top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
                status: bool = True, trace: bool = False, top_restart: bool = False,
-               stage_ms: bool = False, batching: str = "plain", out: DockResult | None = None) -> DockResult:
+               stage_ms: bool = False, batching: str = "plain", grid_format: str = "f32",
+               rescore_fp64: bool = False, out: DockResult | None = None) -> DockResult:
     """ligen_dock_batch: dock every ligand, keep the top_k poses of each.
 
     batching: "plain" (one launch) or "buckets" (paper §3 classes, one
-    persistent launch per atom class, replayed from a CUDA graph)."""
+    persistent launch per atom class, replayed from a CUDA graph).
+    grid_format: "f32", "f16" or "bf16" grid records in the docking kernel.
+    rescore_fp64: re-score and re-rank the kept poses in FP64 on the GPU;
+    the FP64 scores are returned in `scores_f64`."""
     lib = _abi.load()
     L, dev = ligands.n_ligands, ligands.device
     n_sum = int(ligands.h_rot_off[-1])
@@ -146,11 +152,14 @@ def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_ste
             if trace else None,
             top_restart=_empty((L, top_k), torch.int32, dev) if top_restart else None,
             stage_ms=np.zeros(_abi.LIGEN_N_STAGES, np.float32) if stage_ms else None,
+            scores_f64=_empty((L, top_k), torch.float64, dev) if rescore_fp64 else None,
         )
     p = ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
                 float(jitter), float(out_penalty), _stream_handle(dev), _ptr(out.status), _ptr(out.trace),
                 _ptr(out.top_restart),
-                out.stage_ms.ctypes.data if out.stage_ms is not None else None, BATCHING[batching], 0)
+                out.stage_ms.ctypes.data if out.stage_ms is not None else None, BATCHING[batching],
+                GRID_FORMATS[grid_format], int(bool(rescore_fp64)), 0,
+                _ptr(out.scores_f64) if rescore_fp64 else None)
     check(lib.ligen_dock_batch(C.byref(ligands._s), C.byref(grid._s), C.byref(p), _ptr(out.poses),
                                _ptr(out.scores)))
     return out
@@ -174,7 +183,7 @@ def dock_batch_static(ligands: Ligands, grid: PocketGrid, *, restarts: int, tors
                          status=_empty((L,), torch.int32, dev), trace=None, top_restart=None, stage_ms=None)
     p = ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
                 float(jitter), float(out_penalty), _stream_handle(dev), _ptr(out.status), _ptr(out.trace),
-                _ptr(out.top_restart), None, _abi.LIGEN_BATCH_PLAIN, 0)
+                _ptr(out.top_restart), None, _abi.LIGEN_BATCH_PLAIN, _abi.LIGEN_GRID_F32, 0, 0, None)
     check(lib.ligen_dock_batch_static(C.byref(ligands._s), C.byref(grid._s), C.byref(p), _ptr(out.poses),
                                       _ptr(out.scores)))
     return out
@@ -305,13 +314,13 @@ def tune_set(table) -> None:
 
 def autotune(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_step_deg: int, passes: int,
              top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
-             sample: int = 256) -> dict:
+             sample: int = 256, grid_format: str = "f32") -> dict:
     """ligen_autotune: time the candidate shapes per bucket on (a sample of)
     this library and store the fastest; returns {bucket: (lanes, rpc, ms per ligand)}."""
     lib = _abi.load()
     p = ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
                 float(jitter), float(out_penalty), _stream_handle(ligands.device), None, None, None, None,
-                _abi.LIGEN_BATCH_PLAIN, 0)
+                _abi.LIGEN_BATCH_PLAIN, GRID_FORMATS[grid_format], 0, 0, None)
     lanes = np.zeros(_abi.LIGEN_N_BUCKETS, np.int32)
     rpc = np.zeros(_abi.LIGEN_N_BUCKETS, np.int32)
     ms = np.zeros(_abi.LIGEN_N_BUCKETS, np.float32)

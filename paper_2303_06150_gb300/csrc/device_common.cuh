@@ -2,6 +2,8 @@
 // stream, quaternion algebra, the cube rotation table and the grid sampler.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace ligen {
@@ -166,6 +168,55 @@ __device__ __forceinline__ float grid_sample(const GridView& g, float ux, float 
     e = fmaf(dx, t2, e);
   }
   return e;
+}
+
+// Grid record formats of the docking kernel.
+//   kRecF32:  32-byte records, the 8 FP32 coefficients of the cell's
+//             trilinear polynomial (one 256-bit load, 7 FMA);
+//   kRecF16, kRecBF16: 16-byte records, the 8 corner values of the cell in
+//             FP16 or BF16 (one 128-bit load, FP32 interpolation).
+// Records are channel-major in every format.
+enum RecFormat { kRecF32 = 0, kRecF16 = 1, kRecBF16 = 2 };
+
+__host__ __device__ constexpr int rec_bytes(int fmt) { return fmt == kRecF32 ? 32 : 16; }
+
+template <int FMT>
+__device__ __forceinline__ float2 unpack2(unsigned int w) {
+  if constexpr (FMT == kRecF16) {
+    __half2 h = *reinterpret_cast<__half2*>(&w);
+    return __half22float2(h);
+  } else {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+    return __bfloat1622float2(h);
+  }
+}
+
+// grid_sample for any record format (see RecFormat).
+template <int FMT>
+__device__ __forceinline__ float grid_sample_fmt(const GridView& g, float ux, float uy, float uz, int c) {
+  if constexpr (FMT == kRecF32) {
+    return grid_sample(g, ux, uy, uz, c);
+  } else {
+    bool inb = (ux >= 0.f) & (ux <= g.mx) & (uy >= 0.f) & (uy <= g.my) & (uz >= 0.f) & (uz <= g.mz);
+    float e = g.penalty;
+    if (inb) {
+      float fx = fminf(floorf(ux), g.mx - 1.f);
+      float fy = fminf(floorf(uy), g.my - 1.f);
+      float fz = fminf(floorf(uz), g.mz - 1.f);
+      int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+      float dx = ux - fx, dy = uy - fy, dz = uz - fz;
+      const uint4* rec = reinterpret_cast<const uint4*>(g.coef) +
+                         ((size_t)c * g.cz * g.cy * g.cx + (size_t)((iz * g.cy + iy) * g.cx + ix));
+      const uint4 v = __ldg(rec);
+      const float2 a = unpack2<FMT>(v.x), b = unpack2<FMT>(v.y);   // (c000, c100), (c010, c110)
+      const float2 d = unpack2<FMT>(v.z), f = unpack2<FMT>(v.w);   // (c001, c101), (c011, c111)
+      const float x00 = fmaf(dx, a.y - a.x, a.x), x10 = fmaf(dx, b.y - b.x, b.x);
+      const float x01 = fmaf(dx, d.y - d.x, d.x), x11 = fmaf(dx, f.y - f.x, f.x);
+      const float y0 = fmaf(dy, x10 - x00, x00), y1 = fmaf(dy, x11 - x01, x01);
+      e = fmaf(dz, y1 - y0, y0);
+    }
+    return e;
+  }
 }
 
 // Value and gradient (per grid unit) of channel `c` at grid-unit position u:

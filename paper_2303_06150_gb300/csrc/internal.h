@@ -43,6 +43,7 @@ struct DockArgs {
   uint64_t seed;
   int R, n_rigid, step_deg, n_theta, passes;
   int lanes;          // G: lanes per restart (2, 4 or 8)
+  int fmt;            // grid record format (RecFormat)
   int rpc;            // restarts per work item (a multiple of 32 / lanes)
   int chunks;         // work items per ligand: ceil(R / rpc)
   const int32_t* list;  // ligands to dock (NULL: 0 .. n_items / chunks - 1)
@@ -101,11 +102,34 @@ struct GradArgs {
   int8_t* out_accept;       // refinement: [L * P][steps], optional
 };
 
+struct RescoreArgs {
+  LigandsDev lig;
+  Packed pk;
+  const int32_t* status;
+  const float* values;      // caller's grid [z][y][x][c], FP32
+  int nx, ny, nz, nc;
+  double origin[3];
+  double h;
+  double penalty;
+  int K;                    // kept poses per ligand
+  float* poses;             // outputs, re-ranked in place
+  float* scores;            // [L][K], FP64 scores rounded to FP32
+  int32_t* top_restart;     // [L][K] or NULL
+  double* out_s64;          // [L][K] or NULL: FP64 scores, re-ranked
+  double* s64;              // scratch [L][K]
+  const float* tmp_poses;   // copy of the poses before re-ranking
+  const int32_t* tmp_top;   // copy of top_restart before re-ranking, or NULL
+};
+
 cudaError_t launch_grid_prep(const float* values, int nx, int ny, int nz, int nc, float* coef,
                              cudaStream_t s);
+// Records in format `fmt` (RecFormat) for the docking kernel.
+cudaError_t launch_grid_prep_fmt(const float* values, int nx, int ny, int nz, int nc, int fmt, void* rec,
+                                 cudaStream_t s);
 cudaError_t launch_pack(const LigandsDev& lig, int nc, const Packed& out, cudaStream_t s);
 size_t dock_smem_bytes(int max_atoms, int max_rot, int max_frag, int rpc);
 bool dock_lanes_supported(int lanes);
+bool dock_shape_supported(int lanes, int fmt);
 // grid_ctas: CTAs of a persistent launch (ignored when a.queue is NULL).
 // set_attr: set the kernel's dynamic shared-memory limit first (false when
 // dock_occupancy already did, e.g. before a stream capture).
@@ -113,11 +137,12 @@ cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s, bool s
 // The kernel of (lanes, n_theta) accepts up to `smem` bytes of dynamic
 // shared memory from now on (a per-kernel setting: set the largest value any
 // pending launch of that kernel needs).
-cudaError_t dock_set_smem_limit(int lanes, int n_theta, size_t smem);
+cudaError_t dock_set_smem_limit(int lanes, int n_theta, int fmt, size_t smem);
 // Resident CTAs per SM for a launch with `smem` bytes (within the limit).
-cudaError_t dock_occupancy(int lanes, int n_theta, int rpc, size_t smem, int* blocks_per_sm);
+cudaError_t dock_occupancy(int lanes, int n_theta, int fmt, int rpc, size_t smem, int* blocks_per_sm);
 cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s);
+cudaError_t launch_rescore(const RescoreArgs& a, cudaStream_t s);
 size_t grad_smem_bytes(int max_atoms);
 // refine = false: dS/dpose of every pose; true: gradient refinement in place.
 cudaError_t launch_grad(const GradArgs& a, bool refine, cudaStream_t s);

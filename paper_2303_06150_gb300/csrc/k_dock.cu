@@ -71,7 +71,7 @@ __device__ __forceinline__ void group_argmax(float& s, int& idx) {
 }
 
 // One work item: ligand l, restarts [chunk * rpc, chunk * rpc + rpc).
-template <int G, int SLOTS>
+template <int G, int SLOTS, int FMT>
 __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S, int l, int chunk) {
   const int rpc = a.rpc;
   const int tid = threadIdx.x;
@@ -133,7 +133,7 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
       const float ux = fmaf(Mk[0], X.x, fmaf(Mk[1], X.y, fmaf(Mk[2], X.z, o[0])));
       const float uy = fmaf(Mk[3], X.x, fmaf(Mk[4], X.y, fmaf(Mk[5], X.z, o[1])));
       const float uz = fmaf(Mk[6], X.x, fmaf(Mk[7], X.y, fmaf(Mk[8], X.z, o[2])));
-      acc -= grid_sample(grid, ux, uy, uz, __float_as_int(X.w));
+      acc -= grid_sample_fmt<FMT>(grid, ux, uy, uz, __float_as_int(X.w));
     }
     if (acc > best) { best = acc; kb = k; }
   }
@@ -200,7 +200,7 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
             const float ux = fmaf(ex, cs[s], fmaf(qx, sn[s], px));
             const float uy = fmaf(ey, cs[s], fmaf(qy, sn[s], py));
             const float uz = fmaf(ez, cs[s], fmaf(qz, sn[s], pz));
-            acc[s] -= grid_sample(grid, ux, uy, uz, c);
+            acc[s] -= grid_sample_fmt<FMT>(grid, ux, uy, uz, c);
           }
         }
 #pragma unroll
@@ -242,7 +242,7 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
   // ---- final score of the restart's pose (all atoms)
   float acc = 0.f;
   for (int i = sub; i < N; i += G)
-    acc -= grid_sample(grid, S.cx[i * rpc + rr], S.cy[i * rpc + rr], S.cz[i * rpc + rr],
+    acc -= grid_sample_fmt<FMT>(grid, S.cx[i * rpc + rr], S.cy[i * rpc + rr], S.cz[i * rpc + rr],
                        __float_as_int(S.sx[i].w));
 #pragma unroll
   for (int off = 1; off < G; off <<= 1) acc += __shfl_xor_sync(kFull, acc, off);
@@ -255,7 +255,7 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
   }
 }
 
-template <int G, int SLOTS>
+template <int G, int SLOTS, int FMT>
 __global__ void __launch_bounds__(128) dock_kernel(const DockArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next_item;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(128) dock_kernel(const DockArgs a) {
     const int li = item / a.chunks;
     const int l = a.list ? a.list[li] : li;
     if (a.pk.status[l] == 0)   // uniform over the CTA
-      dock_item<G, SLOTS>(a, S, l, item - li * a.chunks);
+      dock_item<G, SLOTS, FMT>(a, S, l, item - li * a.chunks);
     if (!a.queue) break;
     __syncthreads();   // shared memory is reused by the next item
   }
@@ -289,22 +289,29 @@ namespace {
 
 using KernelFn = void (*)(DockArgs);
 
-// Instantiated (G, SLOTS) shapes; G * SLOTS increments per chunk of the sweep.
+// Instantiated (G, SLOTS, record format) shapes; G * SLOTS increments per
+// chunk of the sweep. The 16-bit record formats exist for 4 and 8 lanes.
 struct Shape {
-  int G, SLOTS;
+  int G, SLOTS, FMT;
   KernelFn fn;
 };
 const Shape kShapes[] = {
-    {2, 6, dock_kernel<2, 6>},  {2, 18, dock_kernel<2, 18>}, {4, 3, dock_kernel<4, 3>},
-    {4, 9, dock_kernel<4, 9>},  {8, 2, dock_kernel<8, 2>},   {8, 5, dock_kernel<8, 5>},
+    {2, 6, kRecF32, dock_kernel<2, 6, kRecF32>},     {2, 18, kRecF32, dock_kernel<2, 18, kRecF32>},
+    {4, 3, kRecF32, dock_kernel<4, 3, kRecF32>},     {4, 9, kRecF32, dock_kernel<4, 9, kRecF32>},
+    {8, 2, kRecF32, dock_kernel<8, 2, kRecF32>},     {8, 5, kRecF32, dock_kernel<8, 5, kRecF32>},
+    {4, 3, kRecF16, dock_kernel<4, 3, kRecF16>},     {4, 9, kRecF16, dock_kernel<4, 9, kRecF16>},
+    {8, 2, kRecF16, dock_kernel<8, 2, kRecF16>},     {8, 5, kRecF16, dock_kernel<8, 5, kRecF16>},
+    {4, 3, kRecBF16, dock_kernel<4, 3, kRecBF16>},   {4, 9, kRecBF16, dock_kernel<4, 9, kRecBF16>},
+    {8, 2, kRecBF16, dock_kernel<8, 2, kRecBF16>},   {8, 5, kRecBF16, dock_kernel<8, 5, kRecBF16>},
 };
 
-// The instantiation for G lanes and n_theta increments: the fewest slots that
-// cover n_theta in one chunk, else the largest (several chunks).
-const Shape* pick_shape(int G, int n_theta) {
+// The instantiation for G lanes, n_theta increments and record format: the
+// fewest slots that cover n_theta in one chunk, else the largest (several
+// chunks).
+const Shape* pick_shape(int G, int n_theta, int fmt) {
   const Shape* best = nullptr;
   for (const Shape& sh : kShapes) {
-    if (sh.G != G) continue;
+    if (sh.G != G || sh.FMT != fmt) continue;
     if (sh.G * sh.SLOTS >= n_theta) {
       if (!best || best->G * best->SLOTS < n_theta || sh.SLOTS < best->SLOTS) best = &sh;
     } else if (!best || (best->G * best->SLOTS < n_theta && sh.SLOTS > best->SLOTS)) {
@@ -318,9 +325,11 @@ const Shape* pick_shape(int G, int n_theta) {
 
 bool dock_lanes_supported(int G) { return G == 2 || G == 4 || G == 8; }
 
+bool dock_shape_supported(int G, int fmt) { return pick_shape(G, 36, fmt) != nullptr; }
+
 cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s, bool set_attr) {
   if (a.n_items == 0) return cudaSuccess;
-  const Shape* sh = pick_shape(a.lanes, a.n_theta);
+  const Shape* sh = pick_shape(a.lanes, a.n_theta, a.fmt);
   if (!sh) return cudaErrorInvalidValue;
   const size_t smem = dock_smem_bytes(a.max_atoms, a.max_rot, a.max_frag, a.rpc);
   if (set_attr) {
@@ -332,14 +341,14 @@ cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s, bool s
   return cudaGetLastError();
 }
 
-cudaError_t dock_set_smem_limit(int lanes, int n_theta, size_t smem) {
-  const Shape* sh = pick_shape(lanes, n_theta);
+cudaError_t dock_set_smem_limit(int lanes, int n_theta, int fmt, size_t smem) {
+  const Shape* sh = pick_shape(lanes, n_theta, fmt);
   if (!sh) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t dock_occupancy(int lanes, int n_theta, int rpc, size_t smem, int* blocks_per_sm) {
-  const Shape* sh = pick_shape(lanes, n_theta);
+cudaError_t dock_occupancy(int lanes, int n_theta, int fmt, int rpc, size_t smem, int* blocks_per_sm) {
+  const Shape* sh = pick_shape(lanes, n_theta, fmt);
   if (!sh) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sh->fn, rpc * lanes, smem);
 }

@@ -41,7 +41,57 @@ __global__ void grid_prep_kernel(const float* __restrict__ v, int nx, int ny, in
   }
 }
 
+// 16-bit records: the 8 corner values of each (cell, channel), order
+// c000, c100, c010, c110, c001, c101, c011, c111, rounded to nearest.
+template <int FMT>
+__global__ void grid_prep16_kernel(const float* __restrict__ v, int nx, int ny, int nz, int nc,
+                                   uint4* __restrict__ out) {
+  const int cx = nx - 1, cy = ny - 1, cz = nz - 1;
+  const size_t cells = (size_t)cx * cy * cz;
+  const size_t total = cells * nc;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t % nc);
+    size_t cell = t / nc;
+    const int ix = (int)(cell % cx);
+    const int iy = (int)((cell / cx) % cy);
+    const int iz = (int)(cell / ((size_t)cx * cy));
+    auto at = [&](int dx, int dy, int dz) -> float {
+      return v[(((size_t)(iz + dz) * ny + (iy + dy)) * nx + (ix + dx)) * nc + c];
+    };
+    unsigned int w[4];
+    const float pairs[4][2] = {{at(0, 0, 0), at(1, 0, 0)}, {at(0, 1, 0), at(1, 1, 0)},
+                               {at(0, 0, 1), at(1, 0, 1)}, {at(0, 1, 1), at(1, 1, 1)}};
+    for (int k = 0; k < 4; ++k) {
+      if constexpr (FMT == kRecF16) {
+        __half2 h = __floats2half2_rn(pairs[k][0], pairs[k][1]);
+        w[k] = *reinterpret_cast<unsigned int*>(&h);
+      } else {
+        __nv_bfloat162 h = __floats2bfloat162_rn(pairs[k][0], pairs[k][1]);
+        w[k] = *reinterpret_cast<unsigned int*>(&h);
+      }
+    }
+    out[(size_t)c * cells + cell] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_grid_prep_fmt(const float* values, int nx, int ny, int nz, int nc, int fmt, void* rec,
+                                 cudaStream_t s) {
+  if (fmt == kRecF32) return launch_grid_prep(values, nx, ny, nz, nc, (float*)rec, s);
+  const size_t total = (size_t)(nx - 1) * (ny - 1) * (nz - 1) * nc;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t want = (total + 255) / 256;
+  const int blocks = (int)(want < (size_t)sms * 16 ? want : (size_t)sms * 16);
+  if (fmt == kRecF16)
+    grid_prep16_kernel<kRecF16><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(values, nx, ny, nz, nc, (uint4*)rec);
+  else
+    grid_prep16_kernel<kRecBF16><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(values, nx, ny, nz, nc, (uint4*)rec);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_grid_prep(const float* values, int nx, int ny, int nz, int nc, float* coef,
                              cudaStream_t s) {

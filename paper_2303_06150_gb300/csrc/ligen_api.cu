@@ -181,6 +181,10 @@ int check_params(const ligen_params_t* p) {
   if (p->mode != 0) return fail(LIGEN_ERR_UNSUPPORTED, "mode %d not supported", p->mode);
   if (p->batching != LIGEN_BATCH_PLAIN && p->batching != LIGEN_BATCH_BUCKETS)
     return fail(LIGEN_ERR_INVALID_ARG, "batching must be LIGEN_BATCH_PLAIN or LIGEN_BATCH_BUCKETS");
+  if (p->grid_format != LIGEN_GRID_F32 && p->grid_format != LIGEN_GRID_F16 && p->grid_format != LIGEN_GRID_BF16)
+    return fail(LIGEN_ERR_INVALID_ARG, "grid_format must be LIGEN_GRID_F32, _F16 or _BF16");
+  if (p->rescore_fp64 != 0 && p->rescore_fp64 != 1) return fail(LIGEN_ERR_INVALID_ARG, "rescore_fp64 must be 0 or 1");
+  if (p->scores_f64 && !p->rescore_fp64) return fail(LIGEN_ERR_INVALID_ARG, "scores_f64 needs rescore_fp64 = 1");
   if (!std::isfinite(p->jitter) || p->jitter < 0.f) return fail(LIGEN_ERR_INVALID_ARG, "jitter must be >= 0");
   if (!std::isfinite(p->out_penalty)) return fail(LIGEN_ERR_INVALID_ARG, "out_penalty not finite");
   return LIGEN_OK;
@@ -234,8 +238,8 @@ int stage_ligands(const Arena& ar, const ligen_ligands_t* g, const LibShape& sh,
 size_t grid_values_bytes(const ligen_grid_t* g) {
   return (size_t)g->nx * g->ny * g->nz * g->nc * sizeof(float);
 }
-size_t grid_coef_bytes(const ligen_grid_t* g) {
-  return (size_t)(g->nx - 1) * (g->ny - 1) * (g->nz - 1) * g->nc * 32;
+size_t grid_coef_bytes(const ligen_grid_t* g, int fmt = kRecF32) {
+  return (size_t)(g->nx - 1) * (g->ny - 1) * (g->nz - 1) * g->nc * rec_bytes(fmt);
 }
 
 GridView make_view(const ligen_grid_t* g, const float* coef, float penalty) {
@@ -337,7 +341,8 @@ void plan_groups(const ligen_ligands_t* g, const ligen_params_t* p, int dev, std
       const int N = g->h_atom_off[l + 1] - g->h_atom_off[l];
       const int n = g->h_rot_off[l + 1] - g->h_rot_off[l];
       const int ac = atom_class_of(N);
-      const TuneEntry& t = g_tune[dev][ac * 11 + rot_class_of(n)];
+      TuneEntry t = g_tune[dev][ac * 11 + rot_class_of(n)];
+      if (!dock_shape_supported(t.lanes, p->grid_format)) t = TuneEntry();   // default shape
       const double cost = (double)N * p->n_rigid + (double)p->passes * n * nt * (0.25 * N + 1.0);
       by[std::make_tuple(ac, t.lanes, t.rpc)].push_back({l, cost});
     }
@@ -439,8 +444,8 @@ std::string launch_key(const std::vector<DockArgs>& args, const std::vector<int>
                           a.res_cnt, a.trace, a.list, a.queue};
     append_key(k, ptrs, sizeof ptrs);
     const int ints[] = {a.lig.L, a.grid.cx, a.grid.cy, a.grid.cz, a.grid.nc, a.R, a.n_rigid, a.step_deg,
-                        a.n_theta, a.passes, a.lanes, a.rpc, a.chunks, a.n_items, a.max_atoms, a.max_rot,
-                        a.max_frag, ctas[i]};
+                        a.n_theta, a.passes, a.lanes, a.fmt, a.rpc, a.chunks, a.n_items, a.max_atoms,
+                        a.max_rot, a.max_frag, ctas[i]};
     append_key(k, ints, sizeof ints);
     const float fl[] = {a.origin[0], a.origin[1], a.origin[2], a.inv_h, a.center[0], a.center[1], a.center[2],
                         a.jitter, a.grid.penalty, a.grid.mx, a.grid.my, a.grid.mz};
@@ -482,7 +487,7 @@ int run_bucketed(const DockArgs& base, const std::vector<Group>& groups, int32_t
     size_t& l = limit[gr.lanes];
     l = std::max(l, smem);
   }
-  for (const auto& kv : limit) LG_CUDA(dock_set_smem_limit(kv.first, base.n_theta, kv.second));
+  for (const auto& kv : limit) LG_CUDA(dock_set_smem_limit(kv.first, base.n_theta, base.fmt, kv.second));
   std::vector<DockArgs> args;
   std::vector<int> ctas;
   for (size_t gi = 0; gi < groups.size(); ++gi) {
@@ -499,7 +504,7 @@ int run_bucketed(const DockArgs& base, const std::vector<Group>& groups, int32_t
     a.max_frag = gr.max_frag;
     const size_t smem = dock_smem_bytes(a.max_atoms, a.max_rot, a.max_frag, a.rpc);
     int b = 0;
-    LG_CUDA(dock_occupancy(a.lanes, a.n_theta, a.rpc, smem, &b));
+    LG_CUDA(dock_occupancy(a.lanes, a.n_theta, a.fmt, a.rpc, smem, &b));
     if (b < 1) return fail(LIGEN_ERR_UNSUPPORTED, "no CTA of shape (%d lanes, %d restarts) fits an SM", a.lanes, a.rpc);
     ctas.push_back((int)std::min<int64_t>((int64_t)b * nsm, a.n_items));
     args.push_back(a);
@@ -605,7 +610,8 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
   LigandPlan lp;
   plan_ligands(ar, ligands, sh, lhost == 1, &lp);
   const size_t o_gval = ghost ? ar.take(grid_values_bytes(grid)) : 0;
-  const size_t o_coef = ar.take(grid_coef_bytes(grid));
+  const int fmt = params->grid_format;
+  const size_t o_coef = ar.take(grid_coef_bytes(grid, fmt));
   const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
   const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
   const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
@@ -619,6 +625,15 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
     o_scores = ar.take(4 * (size_t)L * K);
     if (params->trace) o_trace = ar.take(2 * trace_elems);
     if (params->top_restart) o_top = ar.take(4 * (size_t)L * K);
+  }
+  const bool rescore = params->rescore_fp64 == 1;
+  size_t o_itop = 0, o_tmp_poses = 0, o_tmp_top = 0, o_s64 = 0, o_out64 = 0;
+  if (rescore) {
+    if (!params->top_restart) o_itop = ar.take(4 * (size_t)L * K);   // restart ids for tie-breaks
+    o_tmp_poses = ar.take(4 * pose_floats);
+    o_tmp_top = ar.take(4 * (size_t)L * K);
+    o_s64 = ar.take(8 * (size_t)L * K);
+    if (params->scores_f64 && ohost) o_out64 = ar.take(8 * (size_t)L * K);
   }
   const bool buckets = params->batching == LIGEN_BATCH_BUCKETS;
   std::vector<int32_t> order;
@@ -645,7 +660,7 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
   }
   tm.mark();
   float* coef = ar.at<float>(o_coef);
-  LG_CUDA(launch_grid_prep(gvals, grid->nx, grid->ny, grid->nz, grid->nc, coef, s));
+  LG_CUDA(launch_grid_prep_fmt(gvals, grid->nx, grid->ny, grid->nz, grid->nc, fmt, coef, s));
   tm.mark();
   Packed pk{};
   pk.xc = ar.at<float4>(o_xc);
@@ -659,6 +674,7 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
   float* d_scores = ohost ? ar.at<float>(o_scores) : out_scores;
   int16_t* d_trace = params->trace ? (ohost ? ar.at<int16_t>(o_trace) : params->trace) : nullptr;
   int32_t* d_top = params->top_restart ? (ohost ? ar.at<int32_t>(o_top) : params->top_restart) : nullptr;
+  if (rescore && !d_top) d_top = ar.at<int32_t>(o_itop);
 
   DockArgs da{};
   da.lig = lig;
@@ -679,6 +695,7 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
   da.n_theta = 360 / params->torsion_step_deg;
   da.passes = P;
   da.lanes = kDefaultLanes;
+  da.fmt = fmt;
   da.rpc = dock_restarts_per_cta(R, da.lanes);
   da.chunks = (R + da.rpc - 1) / da.rpc;
   da.list = nullptr;
@@ -716,6 +733,30 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
   ta.out_scores = d_scores;
   ta.top_restart = d_top;
   LG_CUDA(launch_topk(ta, s));
+  double* d_out64 = nullptr;
+  if (rescore) {
+    d_out64 = params->scores_f64 ? (ohost ? ar.at<double>(o_out64) : params->scores_f64) : nullptr;
+    LG_CUDA(cudaMemcpyAsync(ar.base + o_tmp_poses, d_poses, 4 * pose_floats, cudaMemcpyDeviceToDevice, s));
+    LG_CUDA(cudaMemcpyAsync(ar.base + o_tmp_top, d_top, 4 * (size_t)L * K, cudaMemcpyDeviceToDevice, s));
+    RescoreArgs rs{};
+    rs.lig = lig;
+    rs.pk = pk;
+    rs.status = pk.status;
+    rs.values = gvals;
+    rs.nx = grid->nx; rs.ny = grid->ny; rs.nz = grid->nz; rs.nc = grid->nc;
+    for (int k = 0; k < 3; ++k) rs.origin[k] = grid->origin[k];
+    rs.h = grid->spacing;
+    rs.penalty = params->out_penalty;
+    rs.K = K;
+    rs.poses = d_poses;
+    rs.scores = d_scores;
+    rs.top_restart = params->top_restart ? d_top : nullptr;
+    rs.out_s64 = d_out64;
+    rs.s64 = ar.at<double>(o_s64);
+    rs.tmp_poses = ar.at<float>(o_tmp_poses);
+    rs.tmp_top = ar.at<int32_t>(o_tmp_top);
+    LG_CUDA(launch_rescore(rs, s));
+  }
 
   const cudaMemcpyKind back = ohost ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   if (params->status) LG_CUDA(cudaMemcpyAsync(params->status, pk.status, 4 * (size_t)L, back, s));
@@ -723,7 +764,8 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
     LG_CUDA(cudaMemcpyAsync(out_poses, d_poses, 4 * pose_floats, back, s));
     LG_CUDA(cudaMemcpyAsync(out_scores, d_scores, 4 * (size_t)L * K, back, s));
     if (d_trace) LG_CUDA(cudaMemcpyAsync(params->trace, d_trace, 2 * trace_elems, back, s));
-    if (d_top) LG_CUDA(cudaMemcpyAsync(params->top_restart, d_top, 4 * (size_t)L * K, back, s));
+    if (params->top_restart) LG_CUDA(cudaMemcpyAsync(params->top_restart, d_top, 4 * (size_t)L * K, back, s));
+    if (d_out64) LG_CUDA(cudaMemcpyAsync(params->scores_f64, d_out64, 8 * (size_t)L * K, back, s));
   }
   tm.mark();
   tm.finish();
@@ -976,8 +1018,8 @@ int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t
   LG_CUDA(cudaDeviceGetAttribute(&warp, cudaDevAttrWarpSize, dev));
   const int rpc = dock_restarts_per_cta(256, kDefaultLanes);
   const size_t smem = dock_smem_bytes(max_atoms, LIGEN_MAX_ROT, LIGEN_MAX_ROT * (max_atoms / 2), rpc);
-  LG_CUDA(dock_set_smem_limit(kDefaultLanes, 36, smem));
-  LG_CUDA(dock_occupancy(kDefaultLanes, 36, rpc, smem, &blocks));
+  LG_CUDA(dock_set_smem_limit(kDefaultLanes, 36, kRecF32, smem));
+  LG_CUDA(dock_occupancy(kDefaultLanes, 36, kRecF32, rpc, smem, &blocks));
   const int threads = rpc * kDefaultLanes;
   if (b) *b = blocks;
   if (sm) *sm = nsm;
@@ -1063,7 +1105,8 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   }
 
   Arena ar;
-  const size_t o_coef = ar.take(grid_coef_bytes(grid));
+  const int fmt = params->grid_format;
+  const size_t o_coef = ar.take(grid_coef_bytes(grid, fmt));
   const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
   const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
   const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
@@ -1080,7 +1123,7 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   lig.atom_off = ligands->atom_off; lig.xyz = ligands->xyz; lig.type = ligands->type;
   lig.bonds = ligands->bonds; lig.rot_off = ligands->rot_off; lig.rot_edge = ligands->rot_edge;
   float* coef = ar.at<float>(o_coef);
-  LG_CUDA(launch_grid_prep((const float*)grid->data, grid->nx, grid->ny, grid->nz, grid->nc, coef, s));
+  LG_CUDA(launch_grid_prep_fmt((const float*)grid->data, grid->nx, grid->ny, grid->nz, grid->nc, fmt, coef, s));
   Packed pk{};
   pk.xc = ar.at<float4>(o_xc);
   pk.binfo = ar.at<uchar4>(o_binfo);
@@ -1108,6 +1151,7 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   base.step_deg = params->torsion_step_deg;
   base.n_theta = 360 / params->torsion_step_deg;
   base.passes = params->passes;
+  base.fmt = fmt;
   base.res_score = ar.at<float>(o_rs);
   base.res_k = ar.at<uint8_t>(o_rk);
   base.res_cnt = ar.at<uint8_t>(o_rc);
@@ -1123,7 +1167,7 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
     float best_ms = 0.f;
     int best = -1;
     for (int c = 0; c < (int)(sizeof kCand / sizeof kCand[0]); ++c) {
-      if (!valid_shape(kCand[c][0], kCand[c][1])) continue;
+      if (!valid_shape(kCand[c][0], kCand[c][1]) || !dock_shape_supported(kCand[c][0], fmt)) continue;
       DockArgs a = base;
       a.lanes = kCand[c][0];
       a.rpc = kCand[c][1];
