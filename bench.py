@@ -227,7 +227,7 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
+def recorded_traffic(form: str):
     """DRAM bytes of one full-size docking launch from the committed ncu capture.
 
     The docking kernel's DRAM traffic is the grid's hot region read once, so it
@@ -243,6 +243,8 @@ def recorded_traffic():
             kv[k.strip()] = v.strip()
     if kv.get("kernel_source_hash") != kernel_source_hash():
         return None, "kernel changed since the full-size ncu capture"
+    if kv.get("form", "plain") != form:
+        return None, f"the full-size capture is of form {kv.get('form')}, not {form}"
     try:
         return float(kv["dram_bytes_per_launch"]), kv.get("command", "")
     except (KeyError, ValueError):
@@ -370,7 +372,7 @@ def run_ours(args):
     # pose math, on a buffer the size of the grid's hot region (20 MB, L2-resident)
     probe_buf = torch.randn((20 << 20) // 32, 8, device=dev)
     probe = max((lg.probe_gather(probe_buf, 512, rec_bytes) for _ in range(5)), key=lambda p: p["gbs"])
-    traffic, traffic_note = recorded_traffic()
+    traffic, traffic_note = recorded_traffic(form)
     roofline = {"bound": "l2", "achieved": achieved, "peak": probe["gbs"], "unit": "GB/s",
                 "frac": achieved / probe["gbs"], "traffic": traffic,
                 "kernel": "dock_kernel", "kernel_ms": dock,
