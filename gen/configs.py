@@ -43,3 +43,20 @@ def scaled(name: str, n_ligands: int) -> dict:
     w = copy.deepcopy(WORKLOADS[name])
     w["library"]["n_ligands"] = int(n_ligands)
     return w
+
+
+def site_grids(grid_spec: dict, n_sites: int) -> list:
+    """Grid recipes of n_sites docking sites of one synthetic target (§5
+    docks into twelve sites of one protein): site g keeps the channels,
+    points and spacing of `grid_spec`, takes seed 1000 * seed + g, and sits
+    at origin (30 g, -7 g, 11 g) Angstrom (sites are distinct boxes of one
+    frame). Site 0 is `grid_spec` with its own seed and origin."""
+    import copy
+    out = []
+    for g in range(int(n_sites)):
+        s = copy.deepcopy(grid_spec)
+        if g:
+            s["seed"] = 1000 * int(grid_spec["seed"]) + g
+            s["origin"] = (30.0 * g, -7.0 * g, 11.0 * g)
+        out.append(s)
+    return out

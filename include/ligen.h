@@ -194,6 +194,27 @@ typedef struct ligen_params {
 int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                      const ligen_params_t* params, float* out_poses, float* out_scores);
 
+/* Dock one library into n_sites docking sites (paper §2: the library is
+ * ranked per docking site; §5 screens twelve sites of one target, and the
+ * footprint grows with the number of sites). grids[n_sites] are the sites'
+ * pocket grids: same channel count, each its own box and spacing, all in
+ * host memory or all in device memory. The library is staged and packed once;
+ * the grid records of one site at a time live in one buffer sized for the
+ * largest site, so device memory grows with the largest grid, not with the
+ * number of sites.
+ * Outputs are site-major: site g's scores start at out_scores + g * L * K,
+ * its poses at out_poses + g * K * (7 * L + total rotatable bonds); trace,
+ * top_restart and scores_f64 (when given) are likewise [n_sites][...] with
+ * the per-site sizes of ligen_dock_batch; status is written once ([L]; a
+ * ligand's status does not depend on the site, given equal channel counts).
+ * stage_ms sums the stages over the sites. Site g's outputs are those of
+ * ligen_dock_batch(ligands, &grids[g], params, ...), bit for bit: the same
+ * seed, restarts and search run in every site.
+ * Returns LIGEN_OK or an error code; n_sites < 1, NULL grids or channel
+ * counts that differ are LIGEN_ERR_INVALID_ARG. */
+int ligen_dock_sites(const ligen_ligands_t* ligands, const ligen_grid_t* grids, int32_t n_sites,
+                     const ligen_params_t* params, float* out_poses, float* out_scores);
+
 /* ligen_dock_batch for callers that must not allocate device memory: a
  * host framework whose caching allocator already owns the device's memory,
  * or a latency-bound service that cannot take the device-wide

@@ -55,6 +55,7 @@ class ParamsT(C.Structure):
 SIGNATURES = {
     "ligen_dock_batch": (C.c_int, [P, P, P, P, P]),
     "ligen_dock_batch_static": (C.c_int, [P, P, P, P, P]),
+    "ligen_dock_sites": (C.c_int, [P, P, C.c_int32, P, P, P]),
     "ligen_score_poses": (C.c_int, [P, P, C.c_int32, P, C.c_float, P, P]),
     "ligen_pose_grad": (C.c_int, [P, P, C.c_int32, P, C.c_float, P, P, P]),
     "ligen_refine_poses": (C.c_int, [P, P, C.c_int32, P, C.c_float, C.c_int32, C.c_float, C.c_float, C.c_float,

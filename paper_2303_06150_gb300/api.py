@@ -141,27 +141,60 @@ def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_ste
     rescore_fp64: re-score and re-rank the kept poses in FP64 on the GPU;
     the FP64 scores are returned in `scores_f64`."""
     lib = _abi.load()
-    L, dev = ligands.n_ligands, ligands.device
-    n_sum = int(ligands.h_rot_off[-1])
     if out is None:
-        out = DockResult(
-            poses=_empty((top_k * (7 * L + n_sum),), torch.float32, dev),
-            scores=_empty((L, top_k), torch.float32, dev),
-            status=_empty((L,), torch.int32, dev) if status else None,
-            trace=_empty((restarts * int(np.sum(1 + passes * np.diff(ligands.h_rot_off))),), torch.int16, dev)
-            if trace else None,
-            top_restart=_empty((L, top_k), torch.int32, dev) if top_restart else None,
-            stage_ms=np.zeros(_abi.LIGEN_N_STAGES, np.float32) if stage_ms else None,
-            scores_f64=_empty((L, top_k), torch.float64, dev) if rescore_fp64 else None,
-        )
-    p = ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
-                float(jitter), float(out_penalty), _stream_handle(dev), _ptr(out.status), _ptr(out.trace),
-                _ptr(out.top_restart),
-                out.stage_ms.ctypes.data if out.stage_ms is not None else None, BATCHING[batching],
-                GRID_FORMATS[grid_format], int(bool(rescore_fp64)), 0,
-                _ptr(out.scores_f64) if rescore_fp64 else None)
+        out = _dock_outputs(ligands, restarts, passes, top_k, (), status, trace, top_restart, stage_ms, rescore_fp64)
+    p = _dock_params(ligands.device, out, restarts, torsion_step_deg, passes, top_k, seed, n_rigid, jitter,
+                     out_penalty, batching, grid_format, rescore_fp64)
     check(lib.ligen_dock_batch(C.byref(ligands._s), C.byref(grid._s), C.byref(p), _ptr(out.poses),
                                _ptr(out.scores)))
+    return out
+
+
+def _dock_outputs(ligands, restarts, passes, top_k, lead, status, trace, top_restart, stage_ms, rescore_fp64):
+    L, dev = ligands.n_ligands, ligands.device
+    n_sum = int(ligands.h_rot_off[-1])
+    return DockResult(
+        poses=_empty(lead + (top_k * (7 * L + n_sum),), torch.float32, dev),
+        scores=_empty(lead + (L, top_k), torch.float32, dev),
+        status=_empty((L,), torch.int32, dev) if status else None,
+        trace=_empty(lead + (restarts * int(np.sum(1 + passes * np.diff(ligands.h_rot_off))),), torch.int16, dev)
+        if trace else None,
+        top_restart=_empty(lead + (L, top_k), torch.int32, dev) if top_restart else None,
+        stage_ms=np.zeros(_abi.LIGEN_N_STAGES, np.float32) if stage_ms else None,
+        scores_f64=_empty(lead + (L, top_k), torch.float64, dev) if rescore_fp64 else None,
+    )
+
+
+def _dock_params(dev, out, restarts, torsion_step_deg, passes, top_k, seed, n_rigid, jitter, out_penalty,
+                 batching, grid_format, rescore_fp64):
+    return ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
+                   float(jitter), float(out_penalty), _stream_handle(dev), _ptr(out.status), _ptr(out.trace),
+                   _ptr(out.top_restart),
+                   out.stage_ms.ctypes.data if out.stage_ms is not None else None, BATCHING[batching],
+                   GRID_FORMATS[grid_format], int(bool(rescore_fp64)), 0,
+                   _ptr(out.scores_f64) if rescore_fp64 else None)
+
+
+def dock_sites(ligands: Ligands, grids: list, *, restarts: int, torsion_step_deg: int, passes: int,
+               top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
+               status: bool = True, trace: bool = False, top_restart: bool = False,
+               stage_ms: bool = False, batching: str = "plain", grid_format: str = "f32",
+               rescore_fp64: bool = False, out: DockResult | None = None) -> DockResult:
+    """ligen_dock_sites: dock the library into every grid of `grids` (the
+    docking sites). Outputs gain a leading site axis ([n_sites, L, K] scores,
+    [n_sites, pose floats] poses, ...); status stays [L]. Site g's slice
+    equals dock_batch(ligands, grids[g], ...) with the same settings."""
+    lib = _abi.load()
+    n = len(grids)
+    if n < 1:
+        raise ValueError("dock_sites needs at least one grid")
+    if out is None:
+        out = _dock_outputs(ligands, restarts, passes, top_k, (n,), status, trace, top_restart, stage_ms,
+                            rescore_fp64)
+    arr = (GridT * n)(*[g._s for g in grids])
+    p = _dock_params(ligands.device, out, restarts, torsion_step_deg, passes, top_k, seed, n_rigid, jitter,
+                     out_penalty, batching, grid_format, rescore_fp64)
+    check(lib.ligen_dock_sites(C.byref(ligands._s), arr, n, C.byref(p), _ptr(out.poses), _ptr(out.scores)))
     return out
 
 

@@ -135,6 +135,16 @@ struct GridView {
   float penalty;
 };
 
+// Index (in records) of the record of channel c, cell (ix, iy, iz); the
+// grid preparation writes records at the same indices.
+__host__ __device__ __forceinline__ size_t rec_index(int cx, int cy, int cz, int c, int ix, int iy, int iz) {
+  return (size_t)c * cz * cy * cx + (size_t)((iz * cy + iy) * cx + ix);
+}
+// Records to allocate for a grid of cx * cy * cz cells and nc channels.
+__host__ __device__ __forceinline__ size_t rec_count(int cx, int cy, int cz, int nc) {
+  return (size_t)cx * cy * cz * nc;
+}
+
 // 256-bit read-only load (sm_100+): one 32-byte record in one instruction.
 // Not volatile: the load has no side effect, so the compiler may batch it.
 __device__ __forceinline__ void ld_global_v8(const float* p, float (&v)[8]) {
@@ -156,7 +166,7 @@ __device__ __forceinline__ float grid_sample(const GridView& g, float ux, float 
     float fz = fminf(floorf(uz), g.mz - 1.f);
     int ix = (int)fx, iy = (int)fy, iz = (int)fz;
     float dx = ux - fx, dy = uy - fy, dz = uz - fz;
-    const float* rec = g.coef + ((size_t)c * g.cz * g.cy * g.cx + (size_t)((iz * g.cy + iy) * g.cx + ix)) * 8;
+    const float* rec = g.coef + rec_index(g.cx, g.cy, g.cz, c, ix, iy, iz) * 8;
     float a[8];
     ld_global_v8(rec, a);
     float t1 = fmaf(dz, a[7], a[4]);
@@ -205,8 +215,7 @@ __device__ __forceinline__ float grid_sample_fmt(const GridView& g, float ux, fl
       float fz = fminf(floorf(uz), g.mz - 1.f);
       int ix = (int)fx, iy = (int)fy, iz = (int)fz;
       float dx = ux - fx, dy = uy - fy, dz = uz - fz;
-      const uint4* rec = reinterpret_cast<const uint4*>(g.coef) +
-                         ((size_t)c * g.cz * g.cy * g.cx + (size_t)((iz * g.cy + iy) * g.cx + ix));
+      const uint4* rec = reinterpret_cast<const uint4*>(g.coef) + rec_index(g.cx, g.cy, g.cz, c, ix, iy, iz);
       const uint4 v = __ldg(rec);
       const float2 a = unpack2<FMT>(v.x), b = unpack2<FMT>(v.y);   // (c000, c100), (c010, c110)
       const float2 d = unpack2<FMT>(v.z), f = unpack2<FMT>(v.w);   // (c001, c101), (c011, c111)
@@ -232,7 +241,7 @@ __device__ __forceinline__ float grid_sample_grad(const GridView& g, float ux, f
     float fz = fminf(floorf(uz), g.mz - 1.f);
     int ix = (int)fx, iy = (int)fy, iz = (int)fz;
     float dx = ux - fx, dy = uy - fy, dz = uz - fz;
-    const float* rec = g.coef + ((size_t)c * g.cz * g.cy * g.cx + (size_t)((iz * g.cy + iy) * g.cx + ix)) * 8;
+    const float* rec = g.coef + rec_index(g.cx, g.cy, g.cz, c, ix, iy, iz) * 8;
     float a[8];
     ld_global_v8(rec, a);
     float t1 = fmaf(dz, a[7], a[4]);

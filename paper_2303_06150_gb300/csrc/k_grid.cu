@@ -1,8 +1,8 @@
 // Grid preparation: node values [z][y][x][c] -> per-(cell, channel) records
-// of the 8 coefficients of the cell's trilinear polynomial, stored
-// channel-major (see GridView). One thread per (cell, channel); consecutive
-// threads read consecutive channels of the same corners (coalesced reads)
-// and write 32-byte records nc records apart.
+// of the 8 coefficients of the cell's trilinear polynomial (or its 8 corner
+// values in 16 bits), at rec_index (channel-major, see GridView). One thread
+// per (cell, channel); consecutive threads read consecutive channels of the
+// same corners (coalesced reads).
 #include "internal.h"
 
 namespace ligen {
@@ -34,8 +34,7 @@ __global__ void grid_prep_kernel(const float* __restrict__ v, int nx, int ny, in
     hi.y = (float)(c101 - c100 - c001 + c000);            // axz
     hi.z = (float)(c011 - c010 - c001 + c000);            // ayz
     hi.w = (float)(c111 - c110 - c101 - c011 + c100 + c010 + c001 - c000);  // axyz
-    const size_t cells = (size_t)cx * cy * cz;
-    float4* rec = reinterpret_cast<float4*>(coef + ((size_t)c * cells + t / nc) * 8);
+    float4* rec = reinterpret_cast<float4*>(coef + rec_index(cx, cy, cz, c, ix, iy, iz) * 8);
     rec[0] = lo;
     rec[1] = hi;
   }
@@ -71,7 +70,7 @@ __global__ void grid_prep16_kernel(const float* __restrict__ v, int nx, int ny, 
         w[k] = *reinterpret_cast<unsigned int*>(&h);
       }
     }
-    out[(size_t)c * cells + cell] = make_uint4(w[0], w[1], w[2], w[3]);
+    out[rec_index(cx, cy, cz, c, ix, iy, iz)] = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 

@@ -239,7 +239,7 @@ size_t grid_values_bytes(const ligen_grid_t* g) {
   return (size_t)g->nx * g->ny * g->nz * g->nc * sizeof(float);
 }
 size_t grid_coef_bytes(const ligen_grid_t* g, int fmt = kRecF32) {
-  return (size_t)(g->nx - 1) * (g->ny - 1) * (g->nz - 1) * g->nc * rec_bytes(fmt);
+  return rec_count(g->nx - 1, g->ny - 1, g->nz - 1, g->nc) * rec_bytes(fmt);
 }
 
 GridView make_view(const ligen_grid_t* g, const float* coef, float penalty) {
@@ -431,7 +431,7 @@ struct GraphEntry {
 };
 std::mutex g_graph_mu;
 std::map<std::pair<int, cudaStream_t>, std::vector<GraphEntry>> g_graphs;
-constexpr size_t kGraphsPerStream = 4;
+constexpr size_t kGraphsPerStream = 16;
 
 void append_key(std::string& k, const void* p, size_t n) { k.append((const char*)p, n); }
 
@@ -583,14 +583,22 @@ int ligen_release_workspaces(void) {
   return LIGEN_OK;
 }
 
-int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, const ligen_params_t* params,
-                     float* out_poses, float* out_scores) {
+// Docking of one library into n_sites grids (n_sites = 1: ligen_dock_batch).
+// The library is staged and packed once; per site the grid records are built
+// in one shared buffer, then docking, top-K and the optional FP64 re-score
+// write that site's slice of every output.
+static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, int n_sites,
+                     const ligen_params_t* params, float* out_poses, float* out_scores) {
   g_err.clear();
   int rc;
   if ((rc = check_params(params)) != LIGEN_OK) return rc;
   LibShape sh;
   if ((rc = check_ligands(ligands, params->passes, &sh)) != LIGEN_OK) return rc;
-  if ((rc = check_grid(grid)) != LIGEN_OK) return rc;
+  if (!grids || n_sites < 1) return fail(LIGEN_ERR_INVALID_ARG, "grids is NULL or n_sites < 1");
+  for (int g = 0; g < n_sites; ++g) {
+    if ((rc = check_grid(&grids[g])) != LIGEN_OK) return rc;
+    if (grids[g].nc != grids[0].nc) return fail(LIGEN_ERR_INVALID_ARG, "all sites need the same channel count");
+  }
   const int L = ligands->n_ligands;
   if (L == 0) return LIGEN_OK;   // nothing to dock; outputs may be empty (NULL)
   if (!out_poses || !out_scores) return fail(LIGEN_ERR_INVALID_ARG, "out_poses and out_scores are required");
@@ -599,19 +607,30 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
 
   const int lhost = space_of({ligands->atom_off, ligands->xyz, ligands->type, ligands->bonds,
                               ligands->rot_off, ligands->rot_edge});
-  const int ghost = space_of({grid->data});
-  const int ohost = space_of({out_poses, out_scores, params->status, params->trace, params->top_restart});
+  int ghost = -2;
+  for (int g = 0; g < n_sites; ++g) {
+    const int gh = space_of({grids[g].data});
+    if (ghost == -2) ghost = gh;
+    else if (gh != ghost) return fail(LIGEN_ERR_INVALID_ARG, "site grids mix host and device memory");
+  }
+  const int ohost = space_of({out_poses, out_scores, params->status, params->trace, params->top_restart,
+                              params->scores_f64});
   if (lhost < 0) return fail(LIGEN_ERR_INVALID_ARG, "ligand arrays mix host and device memory");
   if (ohost < 0) return fail(LIGEN_ERR_INVALID_ARG, "output arrays mix host and device memory");
 
   const size_t pose_floats = (size_t)K * (7 * (size_t)L + sh.rot);
   const size_t trace_elems = (size_t)R * sh.trace_len;
+  const int fmt = params->grid_format;
+  size_t gval_max = 0, coef_max = 0;
+  for (int g = 0; g < n_sites; ++g) {
+    gval_max = std::max(gval_max, grid_values_bytes(&grids[g]));
+    coef_max = std::max(coef_max, grid_coef_bytes(&grids[g], fmt));
+  }
   Arena ar;
   LigandPlan lp;
   plan_ligands(ar, ligands, sh, lhost == 1, &lp);
-  const size_t o_gval = ghost ? ar.take(grid_values_bytes(grid)) : 0;
-  const int fmt = params->grid_format;
-  const size_t o_coef = ar.take(grid_coef_bytes(grid, fmt));
+  const size_t o_gval = ghost ? ar.take(gval_max) : 0;
+  const size_t o_coef = ar.take(coef_max);
   const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
   const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
   const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
@@ -649,128 +668,162 @@ int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, c
   }
   if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
 
-  Timer tm(params->stage_ms, s);
-  tm.mark();
+  // stage times accumulate over the sites
+  float stage_acc[LIGEN_N_STAGES] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float* stage_out = params->stage_ms;
   LigandsDev lig;
-  if ((rc = stage_ligands(ar, ligands, sh, lp, s, &lig)) != LIGEN_OK) return rc;
-  const float* gvals = (const float*)grid->data;
-  if (ghost) {
-    LG_CUDA(cudaMemcpyAsync(ar.base + o_gval, grid->data, grid_values_bytes(grid), cudaMemcpyHostToDevice, s));
-    gvals = ar.at<float>(o_gval);
-  }
-  tm.mark();
-  float* coef = ar.at<float>(o_coef);
-  LG_CUDA(launch_grid_prep_fmt(gvals, grid->nx, grid->ny, grid->nz, grid->nc, fmt, coef, s));
-  tm.mark();
   Packed pk{};
   pk.xc = ar.at<float4>(o_xc);
   pk.binfo = ar.at<uchar4>(o_binfo);
   pk.frag = ar.at<uint8_t>(o_frag);
   pk.status = ar.at<int32_t>(o_status);
-  LG_CUDA(launch_pack(lig, grid->nc, pk, s));
-  tm.mark();
-
-  float* d_poses = ohost ? ar.at<float>(o_poses) : out_poses;
-  float* d_scores = ohost ? ar.at<float>(o_scores) : out_scores;
-  int16_t* d_trace = params->trace ? (ohost ? ar.at<int16_t>(o_trace) : params->trace) : nullptr;
-  int32_t* d_top = params->top_restart ? (ohost ? ar.at<int32_t>(o_top) : params->top_restart) : nullptr;
-  if (rescore && !d_top) d_top = ar.at<int32_t>(o_itop);
-
-  DockArgs da{};
-  da.lig = lig;
-  da.pk = pk;
-  da.grid = make_view(grid, coef, params->out_penalty);
-  const float h = grid->spacing;
-  const int np[3] = {grid->nx, grid->ny, grid->nz};
-  for (int k = 0; k < 3; ++k) {
-    da.origin[k] = grid->origin[k];
-    da.center[k] = (float)((double)grid->origin[k] + (double)h * (np[k] - 1) / 2.0);
-  }
-  da.inv_h = (float)(1.0 / (double)h);
-  da.jitter = params->jitter;
-  da.seed = params->seed;
-  da.R = R;
-  da.n_rigid = params->n_rigid;
-  da.step_deg = params->torsion_step_deg;
-  da.n_theta = 360 / params->torsion_step_deg;
-  da.passes = P;
-  da.lanes = kDefaultLanes;
-  da.fmt = fmt;
-  da.rpc = dock_restarts_per_cta(R, da.lanes);
-  da.chunks = (R + da.rpc - 1) / da.rpc;
-  da.list = nullptr;
-  da.n_items = L * da.chunks;
-  da.queue = nullptr;
-  da.max_atoms = sh.max_atoms;
-  da.max_rot = sh.max_rot;
-  da.max_frag = (int)sh.max_frag;
-  da.res_score = ar.at<float>(o_rs);
-  da.res_k = ar.at<uint8_t>(o_rk);
-  da.res_cnt = ar.at<uint8_t>(o_rc);
-  da.trace = d_trace;
-  if (buckets) {
-    int32_t* d_order = ar.at<int32_t>(o_order);
-    if (!order_is_current(s, d_order, order)) {
-      // pageable source: the copy is staged before the call returns
-      LG_CUDA(cudaMemcpyAsync(d_order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, s));
-      remember_order(s, d_order, order);
-    }
-    if ((rc = run_bucketed(da, groups, d_order, ar.at<int>(o_queue), s)) != LIGEN_OK) return rc;
-  } else {
-    LG_CUDA(launch_dock(da, 0, s, true));
-  }
-  tm.mark();
-
-  TopkArgs ta{};
-  ta.L = L; ta.R = R; ta.K = K; ta.step_deg = params->torsion_step_deg;
-  ta.rot_off = lig.rot_off;
-  ta.status = pk.status;
-  ta.res_score = da.res_score; ta.res_k = da.res_k; ta.res_cnt = da.res_cnt;
-  ta.seed = params->seed;
-  for (int k = 0; k < 3; ++k) ta.center[k] = da.center[k];
-  ta.jitter = params->jitter;
-  ta.out_poses = d_poses;
-  ta.out_scores = d_scores;
-  ta.top_restart = d_top;
-  LG_CUDA(launch_topk(ta, s));
-  double* d_out64 = nullptr;
-  if (rescore) {
-    d_out64 = params->scores_f64 ? (ohost ? ar.at<double>(o_out64) : params->scores_f64) : nullptr;
-    LG_CUDA(cudaMemcpyAsync(ar.base + o_tmp_poses, d_poses, 4 * pose_floats, cudaMemcpyDeviceToDevice, s));
-    LG_CUDA(cudaMemcpyAsync(ar.base + o_tmp_top, d_top, 4 * (size_t)L * K, cudaMemcpyDeviceToDevice, s));
-    RescoreArgs rs{};
-    rs.lig = lig;
-    rs.pk = pk;
-    rs.status = pk.status;
-    rs.values = gvals;
-    rs.nx = grid->nx; rs.ny = grid->ny; rs.nz = grid->nz; rs.nc = grid->nc;
-    for (int k = 0; k < 3; ++k) rs.origin[k] = grid->origin[k];
-    rs.h = grid->spacing;
-    rs.penalty = params->out_penalty;
-    rs.K = K;
-    rs.poses = d_poses;
-    rs.scores = d_scores;
-    rs.top_restart = params->top_restart ? d_top : nullptr;
-    rs.out_s64 = d_out64;
-    rs.s64 = ar.at<double>(o_s64);
-    rs.tmp_poses = ar.at<float>(o_tmp_poses);
-    rs.tmp_top = ar.at<int32_t>(o_tmp_top);
-    LG_CUDA(launch_rescore(rs, s));
-  }
-
   const cudaMemcpyKind back = ohost ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (params->status) LG_CUDA(cudaMemcpyAsync(params->status, pk.status, 4 * (size_t)L, back, s));
-  if (ohost) {
-    LG_CUDA(cudaMemcpyAsync(out_poses, d_poses, 4 * pose_floats, back, s));
-    LG_CUDA(cudaMemcpyAsync(out_scores, d_scores, 4 * (size_t)L * K, back, s));
-    if (d_trace) LG_CUDA(cudaMemcpyAsync(params->trace, d_trace, 2 * trace_elems, back, s));
-    if (params->top_restart) LG_CUDA(cudaMemcpyAsync(params->top_restart, d_top, 4 * (size_t)L * K, back, s));
-    if (d_out64) LG_CUDA(cudaMemcpyAsync(params->scores_f64, d_out64, 8 * (size_t)L * K, back, s));
+
+  for (int site = 0; site < n_sites; ++site) {
+    const ligen_grid_t* grid = &grids[site];
+    float* site_poses = out_poses + (size_t)site * pose_floats;
+    float* site_scores = out_scores + (size_t)site * L * K;
+    int16_t* site_trace = params->trace ? params->trace + (size_t)site * trace_elems : nullptr;
+    int32_t* site_top = params->top_restart ? params->top_restart + (size_t)site * L * K : nullptr;
+    double* site_s64 = params->scores_f64 ? params->scores_f64 + (size_t)site * L * K : nullptr;
+    float site_ms[LIGEN_N_STAGES];
+    Timer tm(stage_out ? site_ms : nullptr, s);
+    tm.mark();
+    if (site == 0) {
+      if ((rc = stage_ligands(ar, ligands, sh, lp, s, &lig)) != LIGEN_OK) return rc;
+    }
+    const float* gvals = (const float*)grid->data;
+    if (ghost) {
+      LG_CUDA(cudaMemcpyAsync(ar.base + o_gval, grid->data, grid_values_bytes(grid), cudaMemcpyHostToDevice, s));
+      gvals = ar.at<float>(o_gval);
+    }
+    tm.mark();
+    float* coef = ar.at<float>(o_coef);
+    LG_CUDA(launch_grid_prep_fmt(gvals, grid->nx, grid->ny, grid->nz, grid->nc, fmt, coef, s));
+    tm.mark();
+    if (site == 0) LG_CUDA(launch_pack(lig, grid->nc, pk, s));
+    tm.mark();
+
+    float* d_poses = ohost ? ar.at<float>(o_poses) : site_poses;
+    float* d_scores = ohost ? ar.at<float>(o_scores) : site_scores;
+    int16_t* d_trace = site_trace ? (ohost ? ar.at<int16_t>(o_trace) : site_trace) : nullptr;
+    int32_t* d_top = site_top ? (ohost ? ar.at<int32_t>(o_top) : site_top) : nullptr;
+    if (rescore && !d_top) d_top = ar.at<int32_t>(o_itop);
+
+    DockArgs da{};
+    da.lig = lig;
+    da.pk = pk;
+    da.grid = make_view(grid, coef, params->out_penalty);
+    const float h = grid->spacing;
+    const int np[3] = {grid->nx, grid->ny, grid->nz};
+    for (int k = 0; k < 3; ++k) {
+      da.origin[k] = grid->origin[k];
+      da.center[k] = (float)((double)grid->origin[k] + (double)h * (np[k] - 1) / 2.0);
+    }
+    da.inv_h = (float)(1.0 / (double)h);
+    da.jitter = params->jitter;
+    da.seed = params->seed;
+    da.R = R;
+    da.n_rigid = params->n_rigid;
+    da.step_deg = params->torsion_step_deg;
+    da.n_theta = 360 / params->torsion_step_deg;
+    da.passes = P;
+    da.lanes = kDefaultLanes;
+    da.fmt = fmt;
+    da.rpc = dock_restarts_per_cta(R, da.lanes);
+    da.chunks = (R + da.rpc - 1) / da.rpc;
+    da.list = nullptr;
+    da.n_items = L * da.chunks;
+    da.queue = nullptr;
+    da.max_atoms = sh.max_atoms;
+    da.max_rot = sh.max_rot;
+    da.max_frag = (int)sh.max_frag;
+    da.res_score = ar.at<float>(o_rs);
+    da.res_k = ar.at<uint8_t>(o_rk);
+    da.res_cnt = ar.at<uint8_t>(o_rc);
+    da.trace = d_trace;
+    if (buckets) {
+      int32_t* d_order = ar.at<int32_t>(o_order);
+      if (!order_is_current(s, d_order, order)) {
+        // pageable source: the copy is staged before the call returns
+        LG_CUDA(cudaMemcpyAsync(d_order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, s));
+        remember_order(s, d_order, order);
+      }
+      if ((rc = run_bucketed(da, groups, d_order, ar.at<int>(o_queue), s)) != LIGEN_OK) return rc;
+    } else {
+      LG_CUDA(launch_dock(da, 0, s, true));
+    }
+    tm.mark();
+
+    TopkArgs ta{};
+    ta.L = L; ta.R = R; ta.K = K; ta.step_deg = params->torsion_step_deg;
+    ta.rot_off = lig.rot_off;
+    ta.status = pk.status;
+    ta.res_score = da.res_score; ta.res_k = da.res_k; ta.res_cnt = da.res_cnt;
+    ta.seed = params->seed;
+    for (int k = 0; k < 3; ++k) ta.center[k] = da.center[k];
+    ta.jitter = params->jitter;
+    ta.out_poses = d_poses;
+    ta.out_scores = d_scores;
+    ta.top_restart = d_top;
+    LG_CUDA(launch_topk(ta, s));
+    double* d_out64 = nullptr;
+    if (rescore) {
+      d_out64 = site_s64 ? (ohost ? ar.at<double>(o_out64) : site_s64) : nullptr;
+      LG_CUDA(cudaMemcpyAsync(ar.base + o_tmp_poses, d_poses, 4 * pose_floats, cudaMemcpyDeviceToDevice, s));
+      LG_CUDA(cudaMemcpyAsync(ar.base + o_tmp_top, d_top, 4 * (size_t)L * K, cudaMemcpyDeviceToDevice, s));
+      RescoreArgs rsa{};
+      rsa.lig = lig;
+      rsa.pk = pk;
+      rsa.status = pk.status;
+      rsa.values = gvals;
+      rsa.nx = grid->nx; rsa.ny = grid->ny; rsa.nz = grid->nz; rsa.nc = grid->nc;
+      for (int k = 0; k < 3; ++k) rsa.origin[k] = grid->origin[k];
+      rsa.h = grid->spacing;
+      rsa.penalty = params->out_penalty;
+      rsa.K = K;
+      rsa.poses = d_poses;
+      rsa.scores = d_scores;
+      rsa.top_restart = site_top ? d_top : nullptr;
+      rsa.out_s64 = d_out64;
+      rsa.s64 = ar.at<double>(o_s64);
+      rsa.tmp_poses = ar.at<float>(o_tmp_poses);
+      rsa.tmp_top = ar.at<int32_t>(o_tmp_top);
+      LG_CUDA(launch_rescore(rsa, s));
+    }
+
+    if (site == 0 && params->status)
+      LG_CUDA(cudaMemcpyAsync(params->status, pk.status, 4 * (size_t)L, back, s));
+    if (ohost) {
+      LG_CUDA(cudaMemcpyAsync(site_poses, d_poses, 4 * pose_floats, back, s));
+      LG_CUDA(cudaMemcpyAsync(site_scores, d_scores, 4 * (size_t)L * K, back, s));
+      if (d_trace) LG_CUDA(cudaMemcpyAsync(site_trace, d_trace, 2 * trace_elems, back, s));
+      if (site_top) LG_CUDA(cudaMemcpyAsync(site_top, d_top, 4 * (size_t)L * K, back, s));
+      if (d_out64) LG_CUDA(cudaMemcpyAsync(site_s64, d_out64, 8 * (size_t)L * K, back, s));
+    }
+    tm.mark();
+    tm.finish();
+    if (stage_out)
+      for (int k = 0; k < LIGEN_N_STAGES; ++k) stage_acc[k] += site_ms[k];
+    // The next site reuses the staging and record buffers; stream order
+    // keeps its writes behind this site's reads, so no host wait is needed.
   }
-  tm.mark();
-  tm.finish();
+  if (stage_out)
+    for (int k = 0; k < LIGEN_N_STAGES; ++k) stage_out[k] = stage_acc[k];
   if (ohost) LG_CUDA(cudaStreamSynchronize(s));
   return LIGEN_OK;
+}
+
+int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, const ligen_params_t* params,
+                     float* out_poses, float* out_scores) {
+  g_err.clear();
+  if (!grid) return fail(LIGEN_ERR_INVALID_ARG, "grid is NULL");
+  return dock_impl(ligands, grid, 1, params, out_poses, out_scores);
+}
+
+int ligen_dock_sites(const ligen_ligands_t* ligands, const ligen_grid_t* grids, int32_t n_sites,
+                     const ligen_params_t* params, float* out_poses, float* out_scores) {
+  return dock_impl(ligands, grids, n_sites, params, out_poses, out_scores);
 }
 
 int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, int32_t poses_per_ligand,

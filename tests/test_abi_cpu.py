@@ -109,6 +109,20 @@ def test_empty_library_needs_no_outputs(abi):
     assert rc == 0
 
 
+@pytest.mark.parametrize("case", ["no_sites", "null_grids", "mixed_channels"])
+def test_bad_sites_rejected_on_host(abi, case):
+    lib = abi.load()
+    a = _arrays()
+    vals = [np.zeros((4, 4, 4, 2), np.float32),
+            np.zeros((4, 4, 4, 3 if case == "mixed_channels" else 2), np.float32)]
+    g2 = (abi.GridT * 2)(*[_grid(abi, v) for v in vals])
+    n = 0 if case == "no_sites" else 2
+    out = np.zeros(64, np.float32)
+    rc = lib.ligen_dock_sites(C.byref(_lig_struct(abi, a)), None if case == "null_grids" else g2, n,
+                              C.byref(_params(abi)), out.ctypes.data, out.ctypes.data)
+    assert rc == -1 and lib.ligen_last_error()
+
+
 def test_null_structs_rejected(abi):
     lib = abi.load()
     assert lib.ligen_dock_batch(None, None, None, None, None) == -1
