@@ -53,8 +53,10 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB)
+            # LIGEN_ORACLE_LIB: a deliberately broken build of this oracle,
+            # loaded by the mutation tests to show that the pins catch it.
+            path = os.environ.get("LIGEN_ORACLE_LIB") or build()
+            L = C.CDLL(path)
             P = C.c_void_p
             sig = {
                 "or_splitmix64": (C.c_uint64, [C.c_uint64]),

@@ -53,6 +53,7 @@ def test_trilinear_matches_scipy_and_nodes(oracle_lib, small32):
 
 
 def test_trilinear_box_edges_and_continuity(oracle_lib, small32):
+    import oracle
     _, _, grid = small32
     g = _grid(grid.values, grid.origin, grid.spacing)
     nx, ny, nz, nc = grid.dims
@@ -64,6 +65,15 @@ def test_trilinear_box_edges_and_continuity(oracle_lib, small32):
         assert not oracle_lib.trilinear(g, 1, top + np.array(d))[1]
     assert not oracle_lib.trilinear(g, 0, [-1e-9, 1.0, 1.0])[1]
     assert oracle_lib.trilinear(g, 0, [0.0, 1.0, 1.0])[1]
+    # the value-and-gradient sampler (the one the score uses) has the same box:
+    # nodes on the upper faces are inside and take their node value
+    vg, _, inb = oracle_lib.trilinear_grad(g, 1, top)
+    assert inb and abs(vg - grid.values[-1, -1, -1, 1]) < 1e-13
+    for d in ([1e-9, 0, 0], [0, 1e-9, 0], [0, 0, 1e-9]):
+        assert not oracle_lib.trilinear_grad(g, 1, top + np.array(d))[2]
+    one = oracle.OLigand(np.zeros((1, 3)), [1], np.zeros((0, 2)), [])
+    S, _, E = oracle_lib.score_coords(one, g, top[None, :], 5.0)
+    assert S == -E[0] and abs(E[0] - grid.values[-1, -1, -1, 1]) < 1e-13
     rng = np.random.default_rng(3)
     for _ in range(100):
         p = rng.uniform(h, top - h)

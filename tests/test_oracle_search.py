@@ -165,3 +165,73 @@ def test_refinement_is_monotone_and_consistent(oracle_lib, small32):
     p0 = np.concatenate([grid.center, [1, 0, 0, 0], np.zeros(lig.n_rot)])
     _, S, acc, _ = oracle_lib.refine_pose(lig, lin, p0, steps=5)
     assert acc[0] == 1 and S > oracle_lib.score_pose(lig, lin, p0)[0]
+
+
+def test_zero_field_search_is_the_identity(oracle_lib, small32):
+    """On a zero field every candidate scores exactly 0 (all atoms inside a
+    40 A box), so every decision is a tie and the lowest index must win
+    everywhere: k = 0, j = 0, every gap 0, the final pose is the restart's
+    initial pose (canonical quaternion, zero torsions), and the top K are
+    restarts 0..K-1 (equal scores: lower restart first). The exhaustive
+    search keeps its first combination."""
+    w, lib, _ = small32
+    s = w["search"]
+    zero = oracle_lib.OGrid(np.zeros((41, 41, 41, 4)), (0.0, 0.0, 0.0), 1.0)
+    for l in range(0, lib.n_ligands, 3):
+        lig = oracle_lib.OLigand.from_library(lib, l)
+        res = oracle_lib.dock_ligand(lig, zero, s, l)
+        assert np.all(res["score"] == 0.0)
+        assert np.all(res["trace"] == 0) and np.all(res["gap"] == 0.0)
+        for r in range(s["restarts"]):
+            q, t = oracle_lib.restart_init(zero, s, l, r)
+            q = np.sign(q[0]) * q / np.linalg.norm(q)
+            np.testing.assert_allclose(res["pose"][r], np.concatenate([t, q, np.zeros(lig.n_rot)]), atol=1e-15)
+        assert oracle_lib.top_k(res["score"], s["top_k"]).tolist() == list(range(s["top_k"]))
+        if lig.n_rot <= 2:
+            e = oracle_lib.dock_exhaustive(lig, zero, s, l, range(0, 2))
+            np.testing.assert_array_equal(e["score"], 0.0)
+            np.testing.assert_allclose(e["pose"], res["pose"][:2], atol=1e-15)
+
+
+def test_refinement_rules_on_a_one_dimensional_bowl(oracle_lib):
+    """One atom in a field that varies along x only: node values
+    E(x) = (x - 5)^2 on a 0.5 A lattice, linear between nodes. The
+    translation gradient points along +-x, so every step proposes x +- st
+    (the quaternion and the y, z position have zero gradient and stay). The
+    expected accept flags follow from the rules alone, replayed here with
+    numpy's interpolation: accept only a strictly higher score, halve the
+    step on a rejection, never grow it. From x = 3.25 with st = 0.5 the
+    fourth proposal lands on a point of exactly equal score, which must be
+    rejected."""
+    h, n = 0.5, 21
+    xs = h * np.arange(n)
+    ex = (xs - 5.0) ** 2
+    vals = np.ascontiguousarray(np.broadcast_to(ex[None, None, :, None], (n, n, n, 1)))
+    g = oracle_lib.OGrid(vals, (0.0, 0.0, 0.0), h)
+    one = oracle_lib.OLigand(np.zeros((1, 3)), [0], np.zeros((0, 2)), [])
+    start = np.array([3.25, 4.0, 4.0, 1.0, 0.0, 0.0, 0.0])
+    steps = 10
+    pose, S, acc, gap = oracle_lib.refine_pose(one, g, start, steps=steps, step_t=0.5, step_q=0.02,
+                                               step_theta=0.05)
+
+    def energy(x):
+        return float(np.interp(x, xs, ex))
+
+    def slope(x):          # derivative inside the cell that holds x (the upper cell on a node)
+        i = min(int(np.floor(x / h)), n - 2)
+        return (ex[i + 1] - ex[i]) / h
+
+    x, st, want = start[0], 0.5, []
+    for _ in range(steps):
+        prop = min(max(x - st * np.sign(slope(x)), 0.0), xs[-1])
+        if -energy(prop) > -energy(x):
+            x = prop
+            want.append(1)
+        else:
+            st *= 0.5
+            want.append(0)
+    assert want[:5] == [1, 1, 1, 0, 1] and gap[3] == 0.0
+    assert acc.tolist() == want
+    assert pose[0] == x and pose[1] == 4.0 and pose[2] == 4.0
+    np.testing.assert_array_equal(pose[3:], [1.0, 0.0, 0.0, 0.0])
+    assert S == -energy(x)
