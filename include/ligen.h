@@ -133,9 +133,15 @@ typedef struct ligen_grid {
  *                        of the tuning table (ligen_tune_set, ligen_autotune);
  *                        the classes run on forked streams and the whole
  *                        sequence is captured once into a CUDA graph and
- *                        replayed while the call's shape is unchanged. */
+ *                        replayed while the call's shape is unchanged;
+ *   LIGEN_BATCH_BUCKETS_STATIC  the same groups, shapes, streams and graph,
+ *                        but each group is a plain launch of one CTA per
+ *                        work item (no device counter): the static
+ *                        per-bucket launches the persistent form is
+ *                        compared against. */
 #define LIGEN_BATCH_PLAIN 0
 #define LIGEN_BATCH_BUCKETS 1
+#define LIGEN_BATCH_BUCKETS_STATIC 2
 #define LIGEN_N_BUCKETS 44 /* 4 atom classes x 11 rotamer classes */
 
 /* How the docking kernel stores the grid it samples (built from the
@@ -164,7 +170,7 @@ typedef struct ligen_params {
   int16_t* trace;
   int32_t* top_restart;
   float* stage_ms;
-  int32_t batching;     /* LIGEN_BATCH_PLAIN or LIGEN_BATCH_BUCKETS */
+  int32_t batching;     /* LIGEN_BATCH_PLAIN, _BUCKETS or _BUCKETS_STATIC */
   int32_t grid_format;  /* LIGEN_GRID_F32, LIGEN_GRID_F16 or LIGEN_GRID_BF16 */
   int32_t rescore_fp64; /* 1: re-score the K kept poses of every ligand in
                            FP64 on the GPU (from the caller's FP32 grid

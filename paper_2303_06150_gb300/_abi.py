@@ -22,6 +22,7 @@ LIGEN_ERR_BAD_LIGAND = -6
 LIGEN_N_STAGES = 5
 LIGEN_BATCH_PLAIN = 0
 LIGEN_BATCH_BUCKETS = 1
+LIGEN_BATCH_BUCKETS_STATIC = 2
 LIGEN_N_BUCKETS = 44
 LIGEN_GRID_F32 = 0
 LIGEN_GRID_F16 = 1

@@ -124,7 +124,8 @@ class DockResult:
         return self.poses[off[l]:off[l + 1]].reshape(K, 7 + n)
 
 
-BATCHING = {"plain": _abi.LIGEN_BATCH_PLAIN, "buckets": _abi.LIGEN_BATCH_BUCKETS}
+BATCHING = {"plain": _abi.LIGEN_BATCH_PLAIN, "buckets": _abi.LIGEN_BATCH_BUCKETS,
+            "buckets_static": _abi.LIGEN_BATCH_BUCKETS_STATIC}
 GRID_FORMATS = {"f32": _abi.LIGEN_GRID_F32, "f16": _abi.LIGEN_GRID_F16, "bf16": _abi.LIGEN_GRID_BF16}
 
 

@@ -179,8 +179,9 @@ int check_params(const ligen_params_t* p) {
   if (p->passes < 0 || p->passes > 1000) return fail(LIGEN_ERR_INVALID_ARG, "passes must be 0..1000");
   if (p->top_k < 1 || p->top_k > p->restarts) return fail(LIGEN_ERR_INVALID_ARG, "top_k must be 1..restarts");
   if (p->mode != 0) return fail(LIGEN_ERR_UNSUPPORTED, "mode %d not supported", p->mode);
-  if (p->batching != LIGEN_BATCH_PLAIN && p->batching != LIGEN_BATCH_BUCKETS)
-    return fail(LIGEN_ERR_INVALID_ARG, "batching must be LIGEN_BATCH_PLAIN or LIGEN_BATCH_BUCKETS");
+  if (p->batching != LIGEN_BATCH_PLAIN && p->batching != LIGEN_BATCH_BUCKETS &&
+      p->batching != LIGEN_BATCH_BUCKETS_STATIC)
+    return fail(LIGEN_ERR_INVALID_ARG, "batching must be LIGEN_BATCH_PLAIN, _BUCKETS or _BUCKETS_STATIC");
   if (p->grid_format != LIGEN_GRID_F32 && p->grid_format != LIGEN_GRID_F16 && p->grid_format != LIGEN_GRID_BF16)
     return fail(LIGEN_ERR_INVALID_ARG, "grid_format must be LIGEN_GRID_F32, _F16 or _BF16");
   if (p->rescore_fp64 != 0 && p->rescore_fp64 != 1) return fail(LIGEN_ERR_INVALID_ARG, "rescore_fp64 must be 0 or 1");
@@ -464,7 +465,7 @@ int issue_groups(const std::vector<DockArgs>& args, const std::vector<int>& ctas
   for (size_t i = 0; i < args.size(); ++i) {
     cudaStream_t st = f->streams[i];
     LG_CUDA(cudaStreamWaitEvent(st, f->start, 0));
-    LG_CUDA(cudaMemsetAsync(args[i].queue, 0, sizeof(int), st));
+    if (args[i].queue) LG_CUDA(cudaMemsetAsync(args[i].queue, 0, sizeof(int), st));
     LG_CUDA(launch_dock(args[i], ctas[i], st, false));
     LG_CUDA(cudaEventRecord(f->done[i], st));
     LG_CUDA(cudaStreamWaitEvent(s, f->done[i], 0));
@@ -473,10 +474,11 @@ int issue_groups(const std::vector<DockArgs>& args, const std::vector<int>& ctas
 }
 
 // The bucketed layout: one persistent launch per group, sized by Eq. 1
-// (b blocks per SM from the occupancy query, times the SM count), run from a
-// cached CUDA graph when `s` can be captured.
+// (b blocks per SM from the occupancy query, times the SM count), or with
+// `persistent` false one CTA per work item; run from a cached CUDA graph
+// when `s` can be captured.
 int run_bucketed(const DockArgs& base, const std::vector<Group>& groups, int32_t* d_order, int* d_queue,
-                 cudaStream_t s) {
+                 bool persistent, cudaStream_t s) {
   int dev = 0, nsm = 0;
   LG_CUDA(cudaGetDevice(&dev));
   LG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -498,7 +500,7 @@ int run_bucketed(const DockArgs& base, const std::vector<Group>& groups, int32_t
     a.chunks = (a.R + a.rpc - 1) / a.rpc;
     a.list = d_order + gr.beg;
     a.n_items = (gr.end - gr.beg) * a.chunks;
-    a.queue = d_queue + gi;
+    a.queue = persistent ? d_queue + gi : nullptr;
     a.max_atoms = gr.max_atoms;
     a.max_rot = gr.max_rot;
     a.max_frag = gr.max_frag;
@@ -506,7 +508,7 @@ int run_bucketed(const DockArgs& base, const std::vector<Group>& groups, int32_t
     int b = 0;
     LG_CUDA(dock_occupancy(a.lanes, a.n_theta, a.fmt, a.rpc, smem, &b));
     if (b < 1) return fail(LIGEN_ERR_UNSUPPORTED, "no CTA of shape (%d lanes, %d restarts) fits an SM", a.lanes, a.rpc);
-    ctas.push_back((int)std::min<int64_t>((int64_t)b * nsm, a.n_items));
+    ctas.push_back(persistent ? (int)std::min<int64_t>((int64_t)b * nsm, a.n_items) : a.n_items);
     args.push_back(a);
   }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -654,7 +656,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     o_s64 = ar.take(8 * (size_t)L * K);
     if (params->scores_f64 && ohost) o_out64 = ar.take(8 * (size_t)L * K);
   }
-  const bool buckets = params->batching == LIGEN_BATCH_BUCKETS;
+  const bool buckets = params->batching != LIGEN_BATCH_PLAIN;
   std::vector<int32_t> order;
   std::vector<Group> groups;
   size_t o_order = 0, o_queue = 0;
@@ -749,7 +751,9 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
         LG_CUDA(cudaMemcpyAsync(d_order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, s));
         remember_order(s, d_order, order);
       }
-      if ((rc = run_bucketed(da, groups, d_order, ar.at<int>(o_queue), s)) != LIGEN_OK) return rc;
+      if ((rc = run_bucketed(da, groups, d_order, ar.at<int>(o_queue),
+                             params->batching == LIGEN_BATCH_BUCKETS, s)) != LIGEN_OK)
+        return rc;
     } else {
       LG_CUDA(launch_dock(da, 0, s, true));
     }

@@ -60,6 +60,18 @@ def test_buckets_match_plain_and_replay(lg, bimodal):
     assert torch.equal(b1.trace, b2.trace)
 
 
+def test_static_bucket_launches_match_plain(lg, bimodal, small32):
+    for w, lib, grid in (bimodal, small32):
+        L, G = _dev(lg, lib, grid)
+        kw = _kw(w["search"], trace=True, top_restart=True)
+        plain = lg.dock_batch(L, G, batching="plain", **kw)
+        st1 = lg.dock_batch(L, G, batching="buckets_static", **kw)
+        st2 = lg.dock_batch(L, G, batching="buckets_static", **kw)     # graph replay
+        torch.cuda.synchronize()
+        _same_decisions_close_scores(plain, st1)
+        assert torch.equal(st1.scores, st2.scores) and torch.equal(st1.trace, st2.trace)
+
+
 def test_buckets_with_mixed_shapes_after_tuning(lg, bimodal):
     w, lib, grid = bimodal
     L, G = _dev(lg, lib, grid)

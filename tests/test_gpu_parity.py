@@ -290,3 +290,30 @@ def test_bucket_size_eq1(lg):
         assert f["b"] >= 1 and f["sm"] > 0 and f["ws"] == 32
         assert f["l"] == f["b"] * f["sm"] * f["t"] // f["ws"]
     assert lg.bucket_size(32)["b"] >= lg.bucket_size(256)["b"]
+
+
+@pytest.mark.parametrize("fmt", ["f32", "f16"])
+def test_zero_field_ties_take_the_lowest_index(lg, oracle_lib, small32, fmt):
+    """Degenerate case: on a zero field every candidate of every stage scores
+    exactly 0 on both sides, so every decision is an exact tie and the lowest
+    index must win (k = 0, j = 0), the kept poses are restarts 0..K-1 in
+    order, and each pose is the restart's initial pose (the oracle's)."""
+    w, lib, _ = small32
+    s = w["search"]
+    zero = np.zeros((41, 41, 41, 4))
+    L = lg.Ligands.from_arrays(lib, "cuda")
+    G = lg.PocketGrid.from_array(zero, (0.0, 0.0, 0.0), 1.0, "cuda")
+    res = lg.dock_batch(L, G, restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"], passes=s["passes"],
+                        top_k=s["top_k"], seed=s["seed"], trace=True, top_restart=True, grid_format=fmt)
+    torch.cuda.synchronize()
+    assert torch.all(res.trace == 0) and torch.all(res.scores == 0)
+    K = s["top_k"]
+    assert torch.equal(res.top_restart.cpu(), torch.arange(K, dtype=torch.int32).repeat(lib.n_ligands, 1))
+    og = oracle_lib.OGrid(zero, (0.0, 0.0, 0.0), 1.0)
+    poses = res.poses.cpu().numpy()
+    off = lg.pose_offsets(lib.rot_off, K)
+    for l in range(lib.n_ligands):
+        lig = oracle_lib.OLigand.from_library(lib, l)
+        ref = oracle_lib.dock_ligand(lig, og, s, l, range(0, K))
+        assert np.all(ref["trace"] == 0)
+        np.testing.assert_allclose(poses[off[l]:off[l + 1]].reshape(K, -1), ref["pose"], atol=1e-5)
