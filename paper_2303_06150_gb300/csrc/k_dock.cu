@@ -255,8 +255,16 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
   }
 }
 
+// Resident CTAs asked of the register allocator: 8-lane shapes fit in 64
+// registers with at most a few bytes of spill, which lets 8 CTAs (32 warps)
+// share an SM; measured on GB300, 3% faster with FP16 records and 0.6% with
+// FP32 than the 72-register build (7 CTAs). Narrower shapes keep more
+// registers, which their larger slot arrays need.
+template <int G>
+constexpr int dock_min_ctas() { return G == 8 ? 8 : 1; }
+
 template <int G, int SLOTS, int FMT>
-__global__ void __launch_bounds__(128) dock_kernel(const DockArgs a) {
+__global__ void __launch_bounds__(128, dock_min_ctas<G>()) dock_kernel(const DockArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next_item;
   SmemLayout S;

@@ -1,13 +1,18 @@
 // Top-K selection and pose compaction: one warp per ligand.
 //
-// Round k extracts the best restart that ranks after the one extracted in
-// round k-1 in the order (score descending, restart index ascending), so no
-// "taken" marks are needed: every restart ranked before the previous winner
-// compares as already taken. The winner's pose is rebuilt from its restart
-// index (random stream), its cube rotation and its torsion counts and
-// written as t[3], q[4] (w >= 0), theta[n] in [-pi, pi). A NaN score (only
-// possible from a NaN grid) ranks as -infinity, so the order stays total and
-// K <= R rounds always find a restart.
+// The ligand's R restart scores are held in registers (lane j owns restarts
+// j, j + 32, ...; up to kRegSlots per lane) with a per-lane mask of taken
+// restarts. Round k takes the best untaken restart in the order (score
+// descending, restart index ascending): each lane proposes its best untaken
+// slot (slots ascend in restart index), a shuffle argmax picks the warp's,
+// and the owning lane marks it taken. Ligands with more restarts than the
+// registers hold rank from memory instead: round k takes the best restart
+// ranked after the one taken in round k-1, so no marks are needed. The
+// winner's pose is rebuilt from its restart index (random stream), its cube
+// rotation and its torsion counts and written as t[3], q[4] (w >= 0),
+// theta[n] in [-pi, pi). A NaN score (only possible from a NaN grid) ranks as
+// -infinity, so the order stays total and K <= R rounds always find a
+// restart.
 #include <cmath>
 
 #include "../../include/ligen.h"
@@ -17,12 +22,22 @@ namespace ligen {
 namespace {
 
 constexpr int kTopkWarps = 4;
+constexpr int kRegSlots = 8;   // restarts per lane held in registers (R <= 256)
+
+// Warp argmax over (score descending, restart ascending).
+__device__ __forceinline__ void warp_best(float& bs, int& br) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+    const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+    if (os > bs || (os == bs && orr < br)) { bs = os; br = orr; }
+  }
+}
 
 __global__ void __launch_bounds__(32 * kTopkWarps) topk_kernel(const TopkArgs a) {
   const int lane = threadIdx.x & 31;
   const int l = blockIdx.x * kTopkWarps + (threadIdx.x >> 5);
   if (l >= a.L) return;
-  const unsigned full = 0xffffffffu;
   const int r0 = a.rot_off[l];
   const int n = a.rot_off[l + 1] - r0;
   const int plen = 7 + n;
@@ -37,21 +52,36 @@ __global__ void __launch_bounds__(32 * kTopkWarps) topk_kernel(const TopkArgs a)
     return;
   }
   const float* rs = a.res_score + (size_t)l * a.R;
+  const bool in_regs = a.R <= 32 * kRegSlots;
+  float v[kRegSlots];
+  unsigned taken = 0;
+#pragma unroll
+  for (int i = 0; i < kRegSlots; ++i) {
+    const int r = lane + 32 * i;
+    v[i] = -INFINITY;
+    if (in_regs && r < a.R) v[i] = isnan(rs[r]) ? -INFINITY : rs[r];   // total order
+    else taken |= 1u << i;                                             // no such restart
+  }
   float last_s = INFINITY;
   int last_r = -1;
   for (int k = 0; k < a.K; ++k) {
     float bs = -INFINITY;
     int br = 0x7fffffff;
-    for (int r = lane; r < a.R; r += 32) {
-      const float s = isnan(rs[r]) ? -INFINITY : rs[r];   // total order: always R candidates
-      const bool after = (s < last_s) || (s == last_s && r > last_r);
-      if (after && (s > bs || (s == bs && r < br))) { bs = s; br = r; }
-    }
+    if (in_regs) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float os = __shfl_xor_sync(full, bs, o);
-      const int orr = __shfl_xor_sync(full, br, o);
-      if (os > bs || (os == bs && orr < br)) { bs = os; br = orr; }
+      for (int i = 0; i < kRegSlots; ++i) {
+        const int r = lane + 32 * i;
+        if (!(taken >> i & 1u) && (v[i] > bs || (v[i] == bs && r < br))) { bs = v[i]; br = r; }
+      }
+      warp_best(bs, br);
+      if ((br & 31) == lane && br < a.R) taken |= 1u << (br >> 5);
+    } else {
+      for (int r = lane; r < a.R; r += 32) {
+        const float s = isnan(rs[r]) ? -INFINITY : rs[r];
+        const bool after = (s < last_s) || (s == last_s && r > last_r);
+        if (after && (s > bs || (s == bs && r < br))) { bs = s; br = r; }
+      }
+      warp_best(bs, br);
     }
     if (br >= a.R) br = a.R - 1;   // unreachable while K <= R; keeps every index in range
     last_s = bs;

@@ -292,14 +292,15 @@ def test_bucket_size_eq1(lg):
     assert lg.bucket_size(32)["b"] >= lg.bucket_size(256)["b"]
 
 
-@pytest.mark.parametrize("fmt", ["f32", "f16"])
-def test_zero_field_ties_take_the_lowest_index(lg, oracle_lib, small32, fmt):
+@pytest.mark.parametrize("fmt, restarts", [("f32", 8), ("f16", 8), ("f32", 300)])
+def test_zero_field_ties_take_the_lowest_index(lg, oracle_lib, small32, fmt, restarts):
     """Degenerate case: on a zero field every candidate of every stage scores
     exactly 0 on both sides, so every decision is an exact tie and the lowest
     index must win (k = 0, j = 0), the kept poses are restarts 0..K-1 in
-    order, and each pose is the restart's initial pose (the oracle's)."""
+    order, and each pose is the restart's initial pose (the oracle's).
+    300 restarts exceed what the top-K keeps in registers (256)."""
     w, lib, _ = small32
-    s = w["search"]
+    s = dict(w["search"], restarts=restarts, top_k=min(restarts, 40))
     zero = np.zeros((41, 41, 41, 4))
     L = lg.Ligands.from_arrays(lib, "cuda")
     G = lg.PocketGrid.from_array(zero, (0.0, 0.0, 0.0), 1.0, "cuda")
@@ -317,3 +318,25 @@ def test_zero_field_ties_take_the_lowest_index(lg, oracle_lib, small32, fmt):
         ref = oracle_lib.dock_ligand(lig, og, s, l, range(0, K))
         assert np.all(ref["trace"] == 0)
         np.testing.assert_allclose(poses[off[l]:off[l + 1]].reshape(K, -1), ref["pose"], atol=1e-5)
+
+
+@pytest.mark.parametrize("restarts", [200, 300])
+def test_top_k_total_order_both_paths(lg, small32, restarts):
+    """All R restarts kept (K = R): every restart once, scores non-increasing,
+    equal scores in ascending restart order; a smaller K is the prefix. 200
+    restarts rank in registers, 300 from memory."""
+    w, lib, grid = small32
+    s = w["search"]
+    L, G = _dev(lg, lib, grid)
+    kw = dict(restarts=restarts, torsion_step_deg=s["torsion_step_deg"], passes=s["passes"], seed=s["seed"],
+              top_restart=True)
+    full = lg.dock_batch(L, G, top_k=restarts, **kw)
+    part = lg.dock_batch(L, G, top_k=30, **kw)
+    torch.cuda.synchronize()
+    sc, top = full.scores.cpu().numpy(), full.top_restart.cpu().numpy()
+    for l in range(lib.n_ligands):
+        assert sorted(top[l].tolist()) == list(range(restarts))
+        assert np.all(np.diff(sc[l]) <= 0)
+        eq = np.diff(sc[l]) == 0
+        assert np.all(np.diff(top[l])[eq] > 0)
+    assert torch.equal(part.scores, full.scores[:, :30]) and torch.equal(part.top_restart, full.top_restart[:, :30])
