@@ -41,11 +41,13 @@ __global__ void grid_prep_kernel(const float* __restrict__ v, int nx, int ny, in
 }
 
 // 16-bit records: the 8 corner values of each (cell, channel), order
-// c000, c100, c010, c110, c001, c101, c011, c111, rounded to nearest.
+// c000, c100, c010, c110, c001, c101, c011, c111, rounded to nearest. The
+// record grid has rec_cells(n) cells per axis: corners past the last node
+// repeat it (the padding layers of the clamp-free sampler).
 template <int FMT>
 __global__ void grid_prep16_kernel(const float* __restrict__ v, int nx, int ny, int nz, int nc,
                                    uint4* __restrict__ out) {
-  const int cx = nx - 1, cy = ny - 1, cz = nz - 1;
+  const int cx = rec_cells(nx, FMT), cy = rec_cells(ny, FMT), cz = rec_cells(nz, FMT);
   const size_t cells = (size_t)cx * cy * cz;
   const size_t total = cells * nc;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -56,7 +58,8 @@ __global__ void grid_prep16_kernel(const float* __restrict__ v, int nx, int ny, 
     const int iy = (int)((cell / cx) % cy);
     const int iz = (int)(cell / ((size_t)cx * cy));
     auto at = [&](int dx, int dy, int dz) -> float {
-      return v[(((size_t)(iz + dz) * ny + (iy + dy)) * nx + (ix + dx)) * nc + c];
+      const int x = min(ix + dx, nx - 1), y = min(iy + dy, ny - 1), z = min(iz + dz, nz - 1);
+      return v[(((size_t)z * ny + y) * nx + x) * nc + c];
     };
     unsigned int w[4];
     const float pairs[4][2] = {{at(0, 0, 0), at(1, 0, 0)}, {at(0, 1, 0), at(1, 1, 0)},
@@ -79,7 +82,7 @@ __global__ void grid_prep16_kernel(const float* __restrict__ v, int nx, int ny, 
 cudaError_t launch_grid_prep_fmt(const float* values, int nx, int ny, int nz, int nc, int fmt, void* rec,
                                  cudaStream_t s) {
   if (fmt == kRecF32) return launch_grid_prep(values, nx, ny, nz, nc, (float*)rec, s);
-  const size_t total = (size_t)(nx - 1) * (ny - 1) * (nz - 1) * nc;
+  const size_t total = rec_count(rec_cells(nx, fmt), rec_cells(ny, fmt), rec_cells(nz, fmt), nc);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -240,13 +240,13 @@ size_t grid_values_bytes(const ligen_grid_t* g) {
   return (size_t)g->nx * g->ny * g->nz * g->nc * sizeof(float);
 }
 size_t grid_coef_bytes(const ligen_grid_t* g, int fmt = kRecF32) {
-  return rec_count(g->nx - 1, g->ny - 1, g->nz - 1, g->nc) * rec_bytes(fmt);
+  return rec_count(rec_cells(g->nx, fmt), rec_cells(g->ny, fmt), rec_cells(g->nz, fmt), g->nc) * rec_bytes(fmt);
 }
 
-GridView make_view(const ligen_grid_t* g, const float* coef, float penalty) {
+GridView make_view(const ligen_grid_t* g, const float* coef, float penalty, int fmt = kRecF32) {
   GridView v;
   v.coef = coef;
-  v.cx = g->nx - 1; v.cy = g->ny - 1; v.cz = g->nz - 1;
+  v.cx = rec_cells(g->nx, fmt); v.cy = rec_cells(g->ny, fmt); v.cz = rec_cells(g->nz, fmt);
   v.nc = g->nc;
   v.mx = (float)(g->nx - 1); v.my = (float)(g->ny - 1); v.mz = (float)(g->nz - 1);
   v.penalty = penalty;
@@ -715,7 +715,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     DockArgs da{};
     da.lig = lig;
     da.pk = pk;
-    da.grid = make_view(grid, coef, params->out_penalty);
+    da.grid = make_view(grid, coef, params->out_penalty, fmt);
     const float h = grid->spacing;
     const int np[3] = {grid->nx, grid->ny, grid->nz};
     for (int k = 0; k < 3; ++k) {
@@ -1193,7 +1193,7 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   DockArgs base{};
   base.lig = lig;
   base.pk = pk;
-  base.grid = make_view(grid, coef, params->out_penalty);
+  base.grid = make_view(grid, coef, params->out_penalty, fmt);
   const float h = grid->spacing;
   const int np[3] = {grid->nx, grid->ny, grid->nz};
   for (int k = 0; k < 3; ++k) {
