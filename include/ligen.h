@@ -330,6 +330,17 @@ int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t
 int ligen_probe_gather(const float* records, int64_t n_records, int32_t bytes_per_load, int32_t loads_per_thread,
                        float* sink, double* loads_done, float* ms_out, void* stream);
 
+/* Measurement utility (no paper counterpart): streaming read bandwidth of
+ * the L2. A full-device launch reads `buffer` (DEVICE, n_bytes, 16-byte
+ * aligned, n_bytes a multiple of 16) `passes` times with coalesced 16-byte
+ * loads that bypass L1 (ld.global.cg); after one untimed pass the buffer is
+ * L2-resident when it fits. *bytes_done receives the bytes read in the timed
+ * passes and *ms_out their device time (CUDA events on `stream`; the call
+ * synchronises). `sink` (DEVICE, 1 float) keeps the loads alive. Returns
+ * LIGEN_OK or an error code. */
+int ligen_probe_stream(const void* buffer, int64_t n_bytes, int32_t passes, float* sink, double* bytes_done,
+                       float* ms_out, void* stream);
+
 /* Release every cached workspace of the calling thread's current device. */
 int ligen_release_workspaces(void);
 

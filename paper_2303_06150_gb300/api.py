@@ -327,6 +327,19 @@ def probe_gather(records: torch.Tensor, loads_per_thread: int = 256, bytes_per_l
                 gbs=loads.value * bytes_per_load / (ms.value * 1e-3) / 1e9)
 
 
+def probe_stream(buffer: torch.Tensor, passes: int = 20) -> dict:
+    """ligen_probe_stream: L2 streaming read bandwidth over `buffer` (device)."""
+    lib = _abi.load()
+    assert buffer.is_cuda and buffer.is_contiguous()
+    nbytes = buffer.numel() * buffer.element_size() // 16 * 16
+    sink = torch.zeros(1, dtype=torch.float32, device=buffer.device)
+    ms = C.c_float()
+    done = C.c_double()
+    check(lib.ligen_probe_stream(_ptr(buffer), nbytes, int(passes), _ptr(sink), C.byref(done), C.byref(ms),
+                                 _stream_handle(buffer.device)))
+    return dict(bytes=done.value, ms=ms.value, gbs=done.value / (ms.value * 1e-3) / 1e9)
+
+
 def tune_get() -> list:
     """ligen_tune_get for every bucket: [(lanes, restarts_per_cta)] * 44."""
     lib = _abi.load()

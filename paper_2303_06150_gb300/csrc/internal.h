@@ -150,5 +150,7 @@ cudaError_t launch_probe(const float* rec, uint32_t n_rec, int bytes, int iters,
                          int blocks, cudaStream_t s);
 int probe_streams();
 int probe_threads();
+cudaError_t launch_stream_probe(const void* buf, uint64_t n_vec, int passes, float* sink, int blocks,
+                                cudaStream_t s);
 
 }  // namespace ligen

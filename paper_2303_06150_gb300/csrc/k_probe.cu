@@ -49,7 +49,32 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(const float* __res
   if (acc == 1.2345e-30f) sink[0] = acc;   // keeps the loads alive
 }
 
+// Streaming read: thread t of the grid reads 16-byte words t, t + T, ...
+// (T threads in all) once per pass, through L2 only (ld.global.cg).
+__global__ void __launch_bounds__(kProbeThreads) stream_kernel(const float4* __restrict__ buf, uint64_t n_vec,
+                                                               int passes, float* sink) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  float acc = 0.f;
+  for (int p = 0; p < passes; ++p) {
+    uint64_t i = tid;
+    for (; i + 3 * stride < n_vec; i += 4 * stride) {   // four independent loads in flight
+      const float4 a = __ldcg(buf + i), b = __ldcg(buf + i + stride);
+      const float4 c = __ldcg(buf + i + 2 * stride), d = __ldcg(buf + i + 3 * stride);
+      acc += ((a.x + b.y) + (c.z + d.w));
+    }
+    for (; i < n_vec; i += stride) acc += __ldcg(buf + i).x;
+  }
+  if (acc == 1.2345e-30f) sink[0] = acc;   // keeps the loads alive
+}
+
 }  // namespace
+
+cudaError_t launch_stream_probe(const void* buf, uint64_t n_vec, int passes, float* sink, int blocks,
+                                cudaStream_t s) {
+  stream_kernel<<<blocks, kProbeThreads, 0, s>>>(reinterpret_cast<const float4*>(buf), n_vec, passes, sink);
+  return cudaGetLastError();
+}
 
 int probe_streams() { return kProbeStreams; }
 

@@ -1300,6 +1300,34 @@ int ligen_probe_gather(const float* records, int64_t n_records, int32_t bytes_pe
   return LIGEN_OK;
 }
 
+int ligen_probe_stream(const void* buffer, int64_t n_bytes, int32_t passes, float* sink, double* bytes_done,
+                       float* ms_out, void* stream) {
+  g_err.clear();
+  if (!buffer || !sink || !bytes_done || !ms_out) return fail(LIGEN_ERR_INVALID_ARG, "NULL argument");
+  if (n_bytes < 16 || n_bytes % 16 != 0) return fail(LIGEN_ERR_INVALID_ARG, "n_bytes must be a positive multiple of 16");
+  if ((uintptr_t)buffer % 16 != 0) return fail(LIGEN_ERR_INVALID_ARG, "buffer must be 16-byte aligned");
+  if (passes < 1) return fail(LIGEN_ERR_INVALID_ARG, "passes must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, nsm = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  LG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = nsm * (2048 / probe_threads());
+  const uint64_t n_vec = (uint64_t)n_bytes / 16;
+  cudaEvent_t e0, e1;
+  LG_CUDA(cudaEventCreate(&e0));
+  LG_CUDA(cudaEventCreate(&e1));
+  LG_CUDA(launch_stream_probe(buffer, n_vec, 1, sink, blocks, s));   // brings the buffer into L2
+  LG_CUDA(cudaEventRecord(e0, s));
+  LG_CUDA(launch_stream_probe(buffer, n_vec, passes, sink, blocks, s));
+  LG_CUDA(cudaEventRecord(e1, s));
+  LG_CUDA(cudaEventSynchronize(e1));
+  LG_CUDA(cudaEventElapsedTime(ms_out, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *bytes_done = (double)n_bytes * passes;
+  return LIGEN_OK;
+}
+
 }  // extern "C"
 
 // ----------------------------------------------------------------------
