@@ -102,7 +102,14 @@ typedef struct ligen_grid {
  *   torsion_step_deg  2..360 and a divisor of 360; 360/step candidates per bond
  *   passes            >= 0 sweeps over all rotatable bonds
  *   top_k             1..R poses kept per ligand
- *   mode              0 = greedy search (the only mode)
+ *   mode              0 = greedy search; 1 = exhaustive search (small
+ *                     ligands): every restart scores every combination of
+ *                     cube rotation 0..n_rigid-1 and torsion increments and
+ *                     keeps the best (ties: the first combination in the
+ *                     order (k, j_0, .., j_{n-1})); passes and batching are
+ *                     ignored, trace must be NULL; every ligand needs at
+ *                     most 4 rotatable bonds and n_rigid * (360/step)^n <=
+ *                     2^27, else LIGEN_ERR_UNSUPPORTED
  *   seed              restart random stream (SplitMix64 counter hash)
  *   jitter            restart translation = grid centre + U[-jitter, jitter]^3 A
  *   out_penalty       energy of an atom outside the grid box

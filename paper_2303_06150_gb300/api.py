@@ -133,19 +133,21 @@ def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_ste
                top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
                status: bool = True, trace: bool = False, top_restart: bool = False,
                stage_ms: bool = False, batching: str = "plain", grid_format: str = "f32",
-               rescore_fp64: bool = False, out: DockResult | None = None) -> DockResult:
+               rescore_fp64: bool = False, mode: str = "greedy", out: DockResult | None = None) -> DockResult:
     """ligen_dock_batch: dock every ligand, keep the top_k poses of each.
 
     batching: "plain" (one launch) or "buckets" (paper §3 classes, one
     persistent launch per atom class, replayed from a CUDA graph).
     grid_format: "f32", "f16" or "bf16" grid records in the docking kernel.
     rescore_fp64: re-score and re-rank the kept poses in FP64 on the GPU;
-    the FP64 scores are returned in `scores_f64`."""
+    the FP64 scores are returned in `scores_f64`.
+    mode: "greedy" (the search) or "exhaustive" (every combination of cube
+    rotation and torsion increments per restart; small ligands only)."""
     lib = _abi.load()
     if out is None:
         out = _dock_outputs(ligands, restarts, passes, top_k, (), status, trace, top_restart, stage_ms, rescore_fp64)
     p = _dock_params(ligands.device, out, restarts, torsion_step_deg, passes, top_k, seed, n_rigid, jitter,
-                     out_penalty, batching, grid_format, rescore_fp64)
+                     out_penalty, batching, grid_format, rescore_fp64, mode)
     check(lib.ligen_dock_batch(C.byref(ligands._s), C.byref(grid._s), C.byref(p), _ptr(out.poses),
                                _ptr(out.scores)))
     return out
@@ -166,9 +168,12 @@ def _dock_outputs(ligands, restarts, passes, top_k, lead, status, trace, top_res
     )
 
 
+MODES = {"greedy": 0, "exhaustive": 1}
+
+
 def _dock_params(dev, out, restarts, torsion_step_deg, passes, top_k, seed, n_rigid, jitter, out_penalty,
-                 batching, grid_format, rescore_fp64):
-    return ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
+                 batching, grid_format, rescore_fp64, mode="greedy"):
+    return ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, MODES[mode], int(seed) & ((1 << 64) - 1),
                    float(jitter), float(out_penalty), _stream_handle(dev), _ptr(out.status), _ptr(out.trace),
                    _ptr(out.top_restart),
                    out.stage_ms.ctypes.data if out.stage_ms is not None else None, BATCHING[batching],
@@ -180,7 +185,7 @@ def dock_sites(ligands: Ligands, grids: list, *, restarts: int, torsion_step_deg
                top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
                status: bool = True, trace: bool = False, top_restart: bool = False,
                stage_ms: bool = False, batching: str = "plain", grid_format: str = "f32",
-               rescore_fp64: bool = False, out: DockResult | None = None) -> DockResult:
+               rescore_fp64: bool = False, mode: str = "greedy", out: DockResult | None = None) -> DockResult:
     """ligen_dock_sites: dock the library into every grid of `grids` (the
     docking sites). Outputs gain a leading site axis ([n_sites, L, K] scores,
     [n_sites, pose floats] poses, ...); status stays [L]. Site g's slice
@@ -194,7 +199,7 @@ def dock_sites(ligands: Ligands, grids: list, *, restarts: int, torsion_step_deg
                             rescore_fp64)
     arr = (GridT * n)(*[g._s for g in grids])
     p = _dock_params(ligands.device, out, restarts, torsion_step_deg, passes, top_k, seed, n_rigid, jitter,
-                     out_penalty, batching, grid_format, rescore_fp64)
+                     out_penalty, batching, grid_format, rescore_fp64, mode)
     check(lib.ligen_dock_sites(C.byref(ligands._s), arr, n, C.byref(p), _ptr(out.poses), _ptr(out.scores)))
     return out
 

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libligen.so")
-SOURCES = ["ligen_api.cu", "k_grid.cu", "k_pack.cu", "k_dock.cu", "k_topk.cu", "k_score.cu", "k_probe.cu", "k_grad.cu", "k_rescore.cu"]
+SOURCES = ["ligen_api.cu", "k_grid.cu", "k_pack.cu", "k_dock.cu", "k_topk.cu", "k_score.cu", "k_probe.cu", "k_grad.cu", "k_rescore.cu", "k_exhaustive.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

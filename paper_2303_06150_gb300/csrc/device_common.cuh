@@ -114,6 +114,21 @@ __device__ __forceinline__ void torsion_cs(int j, int step_deg, float* c, float*
   sincospif((float)(j * step_deg) * (1.0f / 180.0f), s, c);
 }
 
+// Rotation of point x by the angle with cosine c and sine s about the line
+// through v with unit direction k (right-handed): the component along k
+// stays, the perpendicular part turns. Same arithmetic as the docking
+// kernel's sweep.
+__device__ __forceinline__ void rodrigues_apply(float* x, const float* v, const float* k, float c, float s) {
+  const float dx = x[0] - v[0], dy = x[1] - v[1], dz = x[2] - v[2];
+  const float kd = k[0] * dx + k[1] * dy + k[2] * dz;
+  const float px = fmaf(k[0], kd, v[0]), py = fmaf(k[1], kd, v[1]), pz = fmaf(k[2], kd, v[2]);
+  const float ex = fmaf(-k[0], kd, dx), ey = fmaf(-k[1], kd, dy), ez = fmaf(-k[2], kd, dz);
+  const float qx = k[1] * dz - k[2] * dy, qy = k[2] * dx - k[0] * dz, qz = k[0] * dy - k[1] * dx;
+  x[0] = fmaf(ex, c, fmaf(qx, s, px));
+  x[1] = fmaf(ey, c, fmaf(qy, s, py));
+  x[2] = fmaf(ez, c, fmaf(qz, s, pz));
+}
+
 // --------------------------------------------------------------- sampler --
 // The grid is stored per cell and channel as the 8 coefficients of its
 // trilinear polynomial, E(f) = a0 + ax fx + ay fy + az fz + axy fx fy +

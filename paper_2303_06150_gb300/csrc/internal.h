@@ -57,6 +57,12 @@ struct DockArgs {
   int16_t* trace;     // optional
 };
 
+// Exhaustive search (mode 1): at most kExMaxRot rotatable bonds per ligand
+// and kExMaxCombos combinations (n_rigid * n_theta^n) per restart.
+constexpr int kExMaxRot = 4;
+constexpr long long kExMaxCombos = 1ll << 27;
+cudaError_t launch_exhaustive(const DockArgs& a, cudaStream_t s);
+
 struct TopkArgs {
   int L, R, K, step_deg;
   const int32_t* rot_off;

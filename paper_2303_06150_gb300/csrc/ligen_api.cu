@@ -178,7 +178,7 @@ int check_params(const ligen_params_t* p) {
     return fail(LIGEN_ERR_INVALID_ARG, "torsion_step_deg must divide 360 and be >= 2");
   if (p->passes < 0 || p->passes > 1000) return fail(LIGEN_ERR_INVALID_ARG, "passes must be 0..1000");
   if (p->top_k < 1 || p->top_k > p->restarts) return fail(LIGEN_ERR_INVALID_ARG, "top_k must be 1..restarts");
-  if (p->mode != 0) return fail(LIGEN_ERR_UNSUPPORTED, "mode %d not supported", p->mode);
+  if (p->mode != 0 && p->mode != 1) return fail(LIGEN_ERR_INVALID_ARG, "mode must be 0 (greedy) or 1 (exhaustive)");
   if (p->batching != LIGEN_BATCH_PLAIN && p->batching != LIGEN_BATCH_BUCKETS &&
       p->batching != LIGEN_BATCH_BUCKETS_STATIC)
     return fail(LIGEN_ERR_INVALID_ARG, "batching must be LIGEN_BATCH_PLAIN, _BUCKETS or _BUCKETS_STATIC");
@@ -188,6 +188,26 @@ int check_params(const ligen_params_t* p) {
   if (p->scores_f64 && !p->rescore_fp64) return fail(LIGEN_ERR_INVALID_ARG, "scores_f64 needs rescore_fp64 = 1");
   if (!std::isfinite(p->jitter) || p->jitter < 0.f) return fail(LIGEN_ERR_INVALID_ARG, "jitter must be >= 0");
   if (!std::isfinite(p->out_penalty)) return fail(LIGEN_ERR_INVALID_ARG, "out_penalty not finite");
+  return LIGEN_OK;
+}
+
+// Exhaustive mode: small ligands only (see ligen_params_t.mode).
+int check_exhaustive(const ligen_ligands_t* g, const ligen_params_t* p) {
+  if (p->trace) return fail(LIGEN_ERR_INVALID_ARG, "trace is not written in exhaustive mode (mode 1)");
+  if ((int64_t)g->n_ligands * p->restarts > INT32_MAX)
+    return fail(LIGEN_ERR_UNSUPPORTED, "exhaustive mode: ligands * restarts exceeds 2^31 - 1");
+  const int nt = 360 / p->torsion_step_deg;
+  for (int l = 0; l < g->n_ligands; ++l) {
+    const int n = g->h_rot_off[l + 1] - g->h_rot_off[l];
+    if (n > kExMaxRot)
+      return fail(LIGEN_ERR_UNSUPPORTED, "exhaustive mode: ligand %d has %d rotatable bonds (max %d)", l, n,
+                  kExMaxRot);
+    long long combos = p->n_rigid;
+    for (int b = 0; b < n; ++b) combos *= nt;
+    if (combos > kExMaxCombos)
+      return fail(LIGEN_ERR_UNSUPPORTED, "exhaustive mode: ligand %d needs %lld poses per restart (max %lld)", l,
+                  combos, kExMaxCombos);
+  }
   return LIGEN_OK;
 }
 
@@ -606,6 +626,8 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
   if (!out_poses || !out_scores) return fail(LIGEN_ERR_INVALID_ARG, "out_poses and out_scores are required");
   cudaStream_t s = (cudaStream_t)params->stream;
   const int R = params->restarts, K = params->top_k, P = params->passes;
+  const bool exhaustive = params->mode == 1;
+  if (exhaustive && (rc = check_exhaustive(ligands, params)) != LIGEN_OK) return rc;
 
   const int lhost = space_of({ligands->atom_off, ligands->xyz, ligands->type, ligands->bonds,
                               ligands->rot_off, ligands->rot_edge});
@@ -656,7 +678,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     o_s64 = ar.take(8 * (size_t)L * K);
     if (params->scores_f64 && ohost) o_out64 = ar.take(8 * (size_t)L * K);
   }
-  const bool buckets = params->batching != LIGEN_BATCH_PLAIN;
+  const bool buckets = params->batching != LIGEN_BATCH_PLAIN && !exhaustive;
   std::vector<int32_t> order;
   std::vector<Group> groups;
   size_t o_order = 0, o_queue = 0;
@@ -744,7 +766,9 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     da.res_k = ar.at<uint8_t>(o_rk);
     da.res_cnt = ar.at<uint8_t>(o_rc);
     da.trace = d_trace;
-    if (buckets) {
+    if (exhaustive) {
+      LG_CUDA(launch_exhaustive(da, s));
+    } else if (buckets) {
       int32_t* d_order = ar.at<int32_t>(o_order);
       if (!order_is_current(s, d_order, order)) {
         // pageable source: the copy is staged before the call returns
@@ -1117,6 +1141,7 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   g_err.clear();
   int rc;
   if ((rc = check_params(params)) != LIGEN_OK) return rc;
+  if (params->mode != 0) return fail(LIGEN_ERR_UNSUPPORTED, "autotuning times the greedy search (mode 0)");
   LibShape sh;
   if ((rc = check_ligands(ligands, params->passes, &sh)) != LIGEN_OK) return rc;
   if ((rc = check_grid(grid)) != LIGEN_OK) return rc;
@@ -1369,6 +1394,7 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
   g_err.clear();
   int rc;
   if ((rc = check_params(params)) != LIGEN_OK) return rc;
+  if (params->mode != 0) return fail(LIGEN_ERR_UNSUPPORTED, "ligen_dock_batch_static runs the greedy search (mode 0)");
   LibShape sh;
   if ((rc = check_ligands(ligands, params->passes, &sh)) != LIGEN_OK) return rc;
   if ((rc = check_grid(grid)) != LIGEN_OK) return rc;

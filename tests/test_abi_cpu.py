@@ -65,7 +65,7 @@ def _params(abi, **kw):
 
 @pytest.mark.parametrize("bad, code", [
     (dict(torsion_step_deg=7), -1), (dict(torsion_step_deg=1), -1), (dict(top_k=9), -1),
-    (dict(restarts=0), -1), (dict(n_rigid=25), -1), (dict(passes=-1), -1), (dict(mode=1), -2),
+    (dict(restarts=0), -1), (dict(n_rigid=25), -1), (dict(passes=-1), -1), (dict(mode=2), -1), (dict(mode=1, trace=C.c_void_p(8)), -1),
     (dict(jitter=float("nan")), -1), (dict(batching=3), -1), (dict(grid_format=3), -1),
     (dict(rescore_fp64=2), -1),
 ])
