@@ -261,9 +261,15 @@ def cpu_baseline(lib, grid, s, n_sample=96, threads=None):
     t0 = time.perf_counter()
     oracle.dock_library(lib, grid, s, ligands=idx, threads=threads)
     dt = time.perf_counter() - t0
+    one = idx[::12]                                   # every 12th of the same sample, one thread
+    t1 = time.perf_counter()
+    oracle.dock_library(lib, grid, s, ligands=one, threads=1)
+    d1 = time.perf_counter() - t1
     return {"value": n_sample / dt, "unit": "ligands/s", "cores": threads, "kind": "oracle",
             "sample": f"{n_sample} ligands evenly spaced over the {lib.n_ligands}-ligand library, all "
-                      f"{s['restarts']} restarts, FP64 C++ oracle, {dt:.1f} s wall"}
+                      f"{s['restarts']} restarts, FP64 C++ oracle, {dt:.1f} s wall",
+            "one_core": {"value": len(one) / d1, "unit": "ligands/s", "cores": 1,
+                         "sample": f"{len(one)} of those ligands on one thread, {d1:.1f} s"}}
 
 
 def run_reference(args):

@@ -56,7 +56,10 @@ typedef enum {
   LIGEN_ERR_OOM = -3,          /* workspace allocation failed */
   LIGEN_ERR_CUDA = -4,         /* a CUDA runtime call or launch failed */
   LIGEN_ERR_TIMEOUT = -5,      /* a bounded device wait expired */
-  LIGEN_ERR_BAD_LIGAND = -6    /* per-ligand status value only */
+  LIGEN_ERR_BAD_LIGAND = -6,   /* per-ligand status value only */
+  LIGEN_ERR_CHECK = -7         /* bounds-checked builds only (LIGEN_CHECKED=1): a
+                                  kernel caught a data-dependent index out of range
+                                  and skipped the access; results are invalid */
 } ligen_status;
 
 typedef enum { LIGEN_F32 = 0 } ligen_dtype;
@@ -350,6 +353,14 @@ int ligen_probe_stream(const void* buffer, int64_t n_bytes, int32_t passes, floa
 
 /* Release every cached workspace of the calling thread's current device. */
 int ligen_release_workspaces(void);
+
+/* Caps every internal workspace at `bytes` (<= 0: no cap, the default), for
+ * the whole process. A call whose workspace would exceed the cap fails with
+ * LIGEN_ERR_OOM before any device work, as it does when cudaMalloc fails;
+ * workspaces already allocated are kept. Lets a caller bound the library's
+ * device memory, and tests inject an allocation failure without exhausting
+ * the GPU. */
+int ligen_set_workspace_limit(int64_t bytes);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* ligen_last_error(void);

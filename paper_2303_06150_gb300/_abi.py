@@ -70,6 +70,7 @@ SIGNATURES = {
     "ligen_release_workspaces": (C.c_int, []),
     "ligen_last_error": (C.c_char_p, []),
     "ligen_probe_stream": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P, P]),
+    "ligen_set_workspace_limit": (C.c_int, [C.c_int64]),
     "ligen_abi_version": (C.c_int, []),
 }
 

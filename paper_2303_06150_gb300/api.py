@@ -332,6 +332,11 @@ def probe_gather(records: torch.Tensor, loads_per_thread: int = 256, bytes_per_l
                 gbs=loads.value * bytes_per_load / (ms.value * 1e-3) / 1e9)
 
 
+def set_workspace_limit(nbytes: int) -> None:
+    """ligen_set_workspace_limit: cap every internal workspace (<= 0: no cap)."""
+    check(_abi.load().ligen_set_workspace_limit(int(nbytes)))
+
+
 def probe_stream(buffer: torch.Tensor, passes: int = 20) -> dict:
     """ligen_probe_stream: L2 streaming read bandwidth over `buffer` (device)."""
     lib = _abi.load()

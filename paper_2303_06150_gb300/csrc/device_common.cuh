@@ -148,7 +148,31 @@ struct GridView {
   int nc;
   float mx, my, mz;    // points - 1 per axis, as float: upper box bound in grid units
   float penalty;
+  size_t n_rec;        // records in the buffer (checked builds compare with it)
+  unsigned* check;     // checked builds: first out-of-range code, else NULL
 };
+
+// Checked builds (compiled with -DLIGEN_CHECKED=1): every data-dependent
+// index is compared with its bound before use; a violation stores its code
+// in *check (the first one wins) and the access is skipped, so the kernel
+// carries on without touching memory out of range. Other builds compile the
+// checks away.
+#ifndef LIGEN_CHECKED
+#define LIGEN_CHECKED 0
+#endif
+enum CheckCode : unsigned {
+  kChkGridRecord = 1,   // grid record index or channel out of range
+  kChkRescoreNode = 2,  // FP64 re-score: lattice node out of range
+  kChkItemShape = 3,    // a ligand larger than the launch's shared-memory carve-up
+  kChkAtomIndex = 4,    // a bond endpoint or moving-atom index >= the ligand's atoms
+};
+__device__ __forceinline__ bool lg_check(unsigned* check, bool ok, unsigned code) {
+  if constexpr (LIGEN_CHECKED) {
+    if (!ok && check) atomicCAS(check, 0u, code);
+    return ok;
+  }
+  return true;
+}
 
 // Index (in records) of the record of channel c, cell (ix, iy, iz); the
 // grid preparation writes records at the same indices.
@@ -181,7 +205,9 @@ __device__ __forceinline__ float grid_sample(const GridView& g, float ux, float 
     float fz = fminf(floorf(uz), g.mz - 1.f);
     int ix = (int)fx, iy = (int)fy, iz = (int)fz;
     float dx = ux - fx, dy = uy - fy, dz = uz - fz;
-    const float* rec = g.coef + rec_index(g.cx, g.cy, g.cz, c, ix, iy, iz) * 8;
+    const size_t ri = rec_index(g.cx, g.cy, g.cz, c, ix, iy, iz);
+    if (!lg_check(g.check, c >= 0 && c < g.nc && ri < g.n_rec, kChkGridRecord)) return g.penalty;
+    const float* rec = g.coef + ri * 8;
     float a[8];
     ld_global_v8(rec, a);
     float t1 = fmaf(dz, a[7], a[4]);
@@ -244,7 +270,9 @@ __device__ __forceinline__ float grid_sample_fmt(const GridView& g, float ux, fl
       float fz = floorf(uz);
       int ix = (int)fx, iy = (int)fy, iz = (int)fz;
       float dx = ux - fx, dy = uy - fy, dz = uz - fz;
-      const uint4* rec = reinterpret_cast<const uint4*>(g.coef) + rec_index(g.cx, g.cy, g.cz, c, ix, iy, iz);
+      const size_t ri = rec_index(g.cx, g.cy, g.cz, c, ix, iy, iz);
+      if (!lg_check(g.check, c >= 0 && c < g.nc && ri < g.n_rec, kChkGridRecord)) return g.penalty;
+      const uint4* rec = reinterpret_cast<const uint4*>(g.coef) + ri;
       const uint4 v = __ldg(rec);
       const float2 a = unpack2<FMT>(v.x), b = unpack2<FMT>(v.y);   // (c000, c100), (c010, c110)
       const float2 d = unpack2<FMT>(v.z), f = unpack2<FMT>(v.w);   // (c001, c101), (c011, c111)
@@ -270,7 +298,9 @@ __device__ __forceinline__ float grid_sample_grad(const GridView& g, float ux, f
     float fz = fminf(floorf(uz), g.mz - 1.f);
     int ix = (int)fx, iy = (int)fy, iz = (int)fz;
     float dx = ux - fx, dy = uy - fy, dz = uz - fz;
-    const float* rec = g.coef + rec_index(g.cx, g.cy, g.cz, c, ix, iy, iz) * 8;
+    const size_t ri = rec_index(g.cx, g.cy, g.cz, c, ix, iy, iz);
+    if (!lg_check(g.check, c >= 0 && c < g.nc && ri < g.n_rec, kChkGridRecord)) return g.penalty;
+    const float* rec = g.coef + ri * 8;
     float a[8];
     ld_global_v8(rec, a);
     float t1 = fmaf(dz, a[7], a[4]);

@@ -125,6 +125,7 @@ struct RescoreArgs {
   double* s64;              // scratch [L][K]
   const float* tmp_poses;   // copy of the poses before re-ranking
   const int32_t* tmp_top;   // copy of top_restart before re-ranking, or NULL
+  unsigned* check;          // checked builds: first out-of-range code, else NULL
 };
 
 cudaError_t launch_grid_prep(const float* values, int nx, int ny, int nz, int nc, float* coef,

@@ -79,6 +79,7 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
   const int N = a.lig.atom_off[l + 1] - a0;
   const int r0 = a.lig.rot_off[l];
   const int n = a.lig.rot_off[l + 1] - r0;
+  if (!lg_check(a.grid.check, N <= a.max_atoms && n <= a.max_rot, kChkItemShape)) return;   // uniform
 
   for (int i = tid; i < N; i += blockDim.x) S.sx[i] = a.pk.xc[a0 + i];
   for (int b = tid; b < n; b += blockDim.x) S.sb[b] = a.pk.binfo[r0 + b];
@@ -89,12 +90,23 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
     for (int b = 0; b < n; ++b) { S.soff[b] = (uint16_t)o; o += S.sb[b].z; }
   }
   __syncthreads();
+  const int n_frag = n > 0 ? S.soff[n - 1] + S.sb[n - 1].z : 0;
+  if (!lg_check(a.grid.check, n_frag <= a.max_frag, kChkItemShape)) return;   // uniform
   for (int b = 0; b < n; ++b) {
     const int m = S.sb[b].z;
     for (int i = tid; i < m; i += blockDim.x)
       S.sfrag[S.soff[b] + i] = a.pk.frag[(size_t)(r0 + b) * kFragStride + i];
   }
   __syncthreads();
+  if constexpr (LIGEN_CHECKED) {   // every axis end and moving atom is an atom of the ligand
+    bool bad = false;
+    for (int b = tid; b < n; b += blockDim.x) bad |= S.sb[b].x >= N || S.sb[b].y >= N;
+    for (int t = tid; t < n_frag; t += blockDim.x) bad |= S.sfrag[t] >= N;
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) lg_check(a.grid.check, false, kChkAtomIndex);
+      return;
+    }
+  }
 
   const int rr = tid / G, sub = tid % G;
   const int r_raw = chunk * rpc + rr;

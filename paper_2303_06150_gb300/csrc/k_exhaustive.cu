@@ -36,15 +36,21 @@ __global__ void __launch_bounds__(kExThreads) exhaustive_kernel(const DockArgs a
   const int N = a.lig.atom_off[l + 1] - a0;
   const int r0 = a.lig.rot_off[l];
   const int n = a.lig.rot_off[l + 1] - r0;   // <= kExMaxRot (checked on the host)
+  if (!lg_check(a.grid.check, N <= LIGEN_MAX_ATOMS && n <= kExMaxRot, kChkItemShape)) return;   // uniform
 
   for (int i = tid; i < N; i += kExThreads) sx[i] = a.pk.xc[a0 + i];
   for (int w = tid; w < kExMaxRot * (LIGEN_MAX_ATOMS / 32); w += kExThreads) (&member[0][0])[w] = 0u;
   __syncthreads();
   for (int b = 0; b < n; ++b) {
     const uchar4 bi = a.pk.binfo[r0 + b];
-    if (tid == 0) { saxis[b][0] = bi.x; saxis[b][1] = bi.y; }
+    if (tid == 0) {
+      saxis[b][0] = bi.x;
+      saxis[b][1] = bi.y;
+      lg_check(a.grid.check, bi.x < N && bi.y < N, kChkAtomIndex);
+    }
     for (int t = tid; t < bi.z; t += kExThreads) {
       const int i = a.pk.frag[(size_t)(r0 + b) * kFragStride + t];
+      if (!lg_check(a.grid.check, i < N, kChkAtomIndex)) continue;
       atomicOr(&member[b][i >> 5], 1u << (i & 31));
     }
   }

@@ -49,6 +49,7 @@ __device__ float warp_score_grad(const GradArgs& a, int l, const float* pose, co
   __syncwarp();
   for (int b = 0; b < n; ++b) {
     const uchar4 bi = a.pk.binfo[r0 + b];
+    if (!lg_check(a.grid.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
     const float4 pv = W.y[bi.y], pu = W.y[bi.x];
     float kx = pv.x - pu.x, ky = pv.y - pu.y, kz = pv.z - pu.z;
     const float kn = rsqrtf(kx * kx + ky * ky + kz * kz);
@@ -58,6 +59,7 @@ __device__ float warp_score_grad(const GradArgs& a, int l, const float* pose, co
     const uint8_t* fr = a.pk.frag + (size_t)(r0 + b) * kFragStride;
     for (int t = lane; t < bi.z; t += 32) {
       const int i = fr[t];
+      if (!lg_check(a.grid.check, i < N, kChkAtomIndex)) continue;
       float4 v = W.y[i];
       const float dx = v.x - pv.x, dy = v.y - pv.y, dz = v.z - pv.z;
       const float kd = kx * dx + ky * dy + kz * dz;
@@ -123,6 +125,7 @@ __device__ float warp_score_grad(const GradArgs& a, int l, const float* pose, co
   }
   for (int b = 0; b < n; ++b) {
     const uchar4 bi = a.pk.binfo[r0 + b];
+    if (!lg_check(a.grid.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
     const float* xv = W.x + 3 * bi.y;
     const float* xu = W.x + 3 * bi.x;
     float ox = xv[0] - xu[0], oy = xv[1] - xu[1], oz = xv[2] - xu[2];
@@ -132,6 +135,7 @@ __device__ float warp_score_grad(const GradArgs& a, int l, const float* pose, co
     float acc = 0.f;
     for (int t = lane; t < bi.z; t += 32) {
       const int i = fr[t];
+      if (!lg_check(a.grid.check, i < N, kChkAtomIndex)) continue;
       const float dx = W.x[3 * i] - xv[0], dy = W.x[3 * i + 1] - xv[1], dz = W.x[3 * i + 2] - xv[2];
       acc += W.g[3 * i] * (oy * dz - oz * dy) + W.g[3 * i + 1] * (oz * dx - ox * dz) +
              W.g[3 * i + 2] * (ox * dy - oy * dx);
@@ -170,7 +174,8 @@ __global__ void __launch_bounds__(32 * kGradWarps) grad_kernel(const GradArgs a)
   const int r0 = a.lig.rot_off[l];
   const int n = a.lig.rot_off[l + 1] - r0;
   const size_t off = (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
-  if (a.pk.status[l] != 0) {
+  if (a.pk.status[l] != 0 ||
+      !lg_check(a.grid.check, a.lig.atom_off[l + 1] - a.lig.atom_off[l] <= a.max_atoms, kChkItemShape)) {
     if (lane == 0) a.out_scores[gp] = -INFINITY;
     for (int e = lane; e < 7 + n; e += 32) a.out_grads[off + e] = 0.f;
     return;
@@ -194,7 +199,8 @@ __global__ void __launch_bounds__(32 * kGradWarps) refine_kernel(const GradArgs 
   const int n = a.lig.rot_off[l + 1] - r0;
   const int plen = 7 + n;
   float* pose_g = a.inout_poses + (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * plen;
-  if (a.pk.status[l] != 0) {
+  if (a.pk.status[l] != 0 ||
+      !lg_check(a.grid.check, a.lig.atom_off[l + 1] - a.lig.atom_off[l] <= a.max_atoms, kChkItemShape)) {
     if (lane == 0) a.out_scores[gp] = -INFINITY;
     return;
   }

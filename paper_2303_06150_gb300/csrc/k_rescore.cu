@@ -42,6 +42,8 @@ __device__ double trilinear64(const RescoreArgs& a, double x, double y, double z
       for (int dx = 0; dx < 2; ++dx) {
         const double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
         const size_t node = (((size_t)(i[2] + dz) * a.ny + (i[1] + dy)) * a.nx + (i[0] + dx));
+        if (!lg_check(a.check, c >= 0 && c < a.nc && node < (size_t)a.nx * a.ny * a.nz, kChkRescoreNode))
+          continue;
         e += w * (double)a.values[node * a.nc + c];
       }
   return e;
@@ -53,7 +55,8 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
   const size_t gp = (size_t)blockIdx.x * kResWarps + w;
   if (gp >= (size_t)a.lig.L * a.K) return;
   const int l = (int)(gp / a.K), p = (int)(gp % a.K);
-  if (a.status[l] != 0) {
+  if (a.status[l] != 0 ||
+      !lg_check(a.check, a.lig.atom_off[l + 1] - a.lig.atom_off[l] <= LIGEN_MAX_ATOMS, kChkItemShape)) {
     if (lane == 0) a.s64[gp] = -INFINITY;
     return;
   }
@@ -72,6 +75,7 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
   __syncwarp();
   for (int b = 0; b < n; ++b) {
     const uchar4 bi = a.pk.binfo[r0 + b];
+    if (!lg_check(a.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
     const double pv[3] = {y[3 * bi.y], y[3 * bi.y + 1], y[3 * bi.y + 2]};
     double kx = pv[0] - y[3 * bi.x], ky = pv[1] - y[3 * bi.x + 1], kz = pv[2] - y[3 * bi.x + 2];
     const double kn = sqrt(kx * kx + ky * ky + kz * kz);
@@ -81,6 +85,7 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
     const uint8_t* fr = a.pk.frag + (size_t)(r0 + b) * kFragStride;
     for (int t = lane; t < bi.z; t += 32) {
       const int i = fr[t];
+      if (!lg_check(a.check, i < N, kChkAtomIndex)) continue;
       const double dx = y[3 * i] - pv[0], dy = y[3 * i + 1] - pv[1], dz = y[3 * i + 2] - pv[2];
       const double kd = kx * dx + ky * dy + kz * dz;
       y[3 * i] = pv[0] + kx * kd + (dx - kx * kd) * c + (ky * dz - kz * dy) * s;

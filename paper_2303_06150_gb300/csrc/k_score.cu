@@ -31,11 +31,16 @@ __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(const ScoreArgs
   const int r0 = a.lig.rot_off[l];
   const int n = a.lig.rot_off[l + 1] - r0;
   const float* pose = a.poses + (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
+  if (!lg_check(a.grid.check, N <= a.max_atoms, kChkItemShape)) {
+    if (lane == 0) a.out_scores[gp] = -INFINITY;
+    return;
+  }
   float4* y = ys[w];
   for (int i = lane; i < N; i += 32) y[i] = a.pk.xc[a0 + i];
   __syncwarp();
   for (int b = 0; b < n; ++b) {
     const uchar4 bi = a.pk.binfo[r0 + b];
+    if (!lg_check(a.grid.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
     const float4 pv = y[bi.y], pu = y[bi.x];
     float kx = pv.x - pu.x, ky = pv.y - pu.y, kz = pv.z - pu.z;
     const float kn = rsqrtf(kx * kx + ky * ky + kz * kz);
@@ -45,6 +50,7 @@ __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(const ScoreArgs
     const uint8_t* fr = a.pk.frag + (size_t)(r0 + b) * kFragStride;
     for (int t = lane; t < bi.z; t += 32) {
       const int i = fr[t];
+      if (!lg_check(a.grid.check, i < N, kChkAtomIndex)) continue;
       float4 v = y[i];
       const float dx = v.x - pv.x, dy = v.y - pv.y, dz = v.z - pv.z;
       const float kd = kx * dx + ky * dy + kz * dz;

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -90,9 +91,15 @@ struct Arena {
   T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
 };
 
+// Upper bound on any one workspace (0: none), ligen_set_workspace_limit.
+std::atomic<size_t> g_ws_limit{0};
+
 int get_workspace(cudaStream_t s, size_t bytes, char** out) {
   int dev = 0;
   LG_CUDA(cudaGetDevice(&dev));
+  const size_t limit = g_ws_limit.load();
+  if (limit && bytes > limit)
+    return fail(LIGEN_ERR_OOM, "workspace of %zu bytes exceeds the limit of %zu bytes", bytes, limit);
   std::lock_guard<std::mutex> lk(g_ws_mu);
   Workspace& w = g_ws[{dev, s}];
   if (w.cap < bytes) {
@@ -104,6 +111,7 @@ int get_workspace(cudaStream_t s, size_t bytes, char** out) {
       w.cap = 0;
     }
     size_t want = bytes + bytes / 8 + (1 << 20);
+    if (limit && want > limit) want = limit;
     cudaError_t e = cudaMalloc(&w.base, want);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -267,11 +275,39 @@ GridView make_view(const ligen_grid_t* g, const float* coef, float penalty, int 
   GridView v;
   v.coef = coef;
   v.cx = rec_cells(g->nx, fmt); v.cy = rec_cells(g->ny, fmt); v.cz = rec_cells(g->nz, fmt);
+  v.n_rec = rec_count(v.cx, v.cy, v.cz, g->nc);
+  v.check = nullptr;
   v.nc = g->nc;
   v.mx = (float)(g->nx - 1); v.my = (float)(g->ny - 1); v.mz = (float)(g->nz - 1);
   v.penalty = penalty;
   return v;
 }
+
+// Checked builds (LIGEN_CHECKED): one device word per call collects the
+// first out-of-range code any kernel of the call records (lg_check); the
+// call waits for its work and turns a nonzero word into LIGEN_ERR_CHECK.
+// Other builds take no word and wait for nothing.
+struct CallCheck {
+  size_t off = 0;
+  unsigned* d = nullptr;
+  void plan(Arena& ar) {
+    if (LIGEN_CHECKED) off = ar.take(16);
+  }
+  int arm(Arena& ar, cudaStream_t s) {
+    if (!LIGEN_CHECKED) return LIGEN_OK;
+    d = ar.at<unsigned>(off);
+    LG_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned), s));
+    return LIGEN_OK;
+  }
+  int verdict(cudaStream_t s) {
+    if (!LIGEN_CHECKED) return LIGEN_OK;
+    unsigned h = 0;
+    LG_CUDA(cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaStreamSynchronize(s));
+    if (h) return fail(LIGEN_ERR_CHECK, "checked build: an out-of-range index was caught and skipped (code %u)", h);
+    return LIGEN_OK;
+  }
+};
 
 struct Timer {
   float* out;
@@ -575,6 +611,11 @@ extern "C" {
 
 int ligen_abi_version(void) { return LIGEN_ABI_VERSION; }
 
+int ligen_set_workspace_limit(int64_t bytes) {
+  g_ws_limit.store(bytes > 0 ? (size_t)bytes : 0);
+  return LIGEN_OK;
+}
+
 const char* ligen_last_error(void) { return g_err.c_str(); }
 
 int ligen_release_workspaces(void) {
@@ -690,7 +731,10 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     o_order = ar.take(4 * (size_t)L);
     o_queue = ar.take(sizeof(int) * groups.size());
   }
+  CallCheck chk;
+  chk.plan(ar);
   if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+  if ((rc = chk.arm(ar, s)) != LIGEN_OK) return rc;
 
   // stage times accumulate over the sites
   float stage_acc[LIGEN_N_STAGES] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -738,6 +782,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     da.lig = lig;
     da.pk = pk;
     da.grid = make_view(grid, coef, params->out_penalty, fmt);
+    da.grid.check = chk.d;
     const float h = grid->spacing;
     const int np[3] = {grid->nx, grid->ny, grid->nz};
     for (int k = 0; k < 3; ++k) {
@@ -817,6 +862,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
       rsa.s64 = ar.at<double>(o_s64);
       rsa.tmp_poses = ar.at<float>(o_tmp_poses);
       rsa.tmp_top = ar.at<int32_t>(o_tmp_top);
+      rsa.check = chk.d;
       LG_CUDA(launch_rescore(rsa, s));
     }
 
@@ -839,7 +885,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
   if (stage_out)
     for (int k = 0; k < LIGEN_N_STAGES; ++k) stage_out[k] = stage_acc[k];
   if (ohost) LG_CUDA(cudaStreamSynchronize(s));
-  return LIGEN_OK;
+  return chk.verdict(s);
 }
 
 int ligen_dock_batch(const ligen_ligands_t* ligands, const ligen_grid_t* grid, const ligen_params_t* params,
@@ -888,7 +934,10 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
     o_poses = ar.take(4 * pose_floats);
     o_scores = ar.take(4 * nscores);
   }
+  CallCheck chk;
+  chk.plan(ar);
   if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+  if ((rc = chk.arm(ar, s)) != LIGEN_OK) return rc;
   LigandsDev lig;
   if ((rc = stage_ligands(ar, ligands, sh, lp, s, &lig)) != LIGEN_OK) return rc;
   const float* gvals = (const float*)grid->data;
@@ -913,6 +962,7 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
   sa.lig = lig;
   sa.pk = pk;
   sa.grid = make_view(grid, coef, out_penalty);
+  sa.grid.check = chk.d;
   for (int k = 0; k < 3; ++k) sa.origin[k] = grid->origin[k];
   sa.inv_h = (float)(1.0 / (double)grid->spacing);
   sa.P = poses_per_ligand;
@@ -924,7 +974,7 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
     LG_CUDA(cudaMemcpyAsync(out_scores, sa.out_scores, 4 * nscores, cudaMemcpyDeviceToHost, s));
     LG_CUDA(cudaStreamSynchronize(s));
   }
-  return LIGEN_OK;
+  return chk.verdict(s);
 }
 
 // Shared body of ligen_pose_grad and ligen_refine_poses: stage inputs, build
@@ -975,7 +1025,10 @@ static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, i
     if (!refine) o_grads = ar.take(4 * pose_floats);
     if (out_accept) o_acc = ar.take(nposes * (size_t)steps);
   }
+  CallCheck chk;
+  chk.plan(ar);
   if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+  if ((rc = chk.arm(ar, s)) != LIGEN_OK) return rc;
   LigandsDev lig;
   if ((rc = stage_ligands(ar, ligands, sh, lp, s, &lig)) != LIGEN_OK) return rc;
   const float* gvals = (const float*)grid->data;
@@ -1000,6 +1053,7 @@ static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, i
   ga.lig = lig;
   ga.pk = pk;
   ga.grid = make_view(grid, coef, out_penalty);
+  ga.grid.check = chk.d;
   for (int k = 0; k < 3; ++k) ga.origin[k] = grid->origin[k];
   ga.inv_h = (float)(1.0 / (double)grid->spacing);
   ga.P = poses_per_ligand;
@@ -1027,7 +1081,7 @@ static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, i
       LG_CUDA(cudaMemcpyAsync(out_accept, ga.out_accept, nposes * (size_t)steps, cudaMemcpyDeviceToHost, s));
     LG_CUDA(cudaStreamSynchronize(s));
   }
-  return LIGEN_OK;
+  return chk.verdict(s);
 }
 
 int ligen_pose_grad(const ligen_ligands_t* ligands, const ligen_grid_t* grid, int32_t poses_per_ligand,
@@ -1197,7 +1251,10 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   const size_t o_rk = ar.take((size_t)L * R);
   const size_t o_rc = ar.take((size_t)sh.rot * R);
   const size_t o_order = ar.take(4 * order.size());
+  CallCheck chk;
+  chk.plan(ar);
   if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+  if ((rc = chk.arm(ar, s)) != LIGEN_OK) return rc;
   forget_orders(dev);   // the order region is overwritten below
 
   LigandsDev lig;
@@ -1219,6 +1276,7 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   base.lig = lig;
   base.pk = pk;
   base.grid = make_view(grid, coef, params->out_penalty, fmt);
+  base.grid.check = chk.d;
   const float h = grid->spacing;
   const int np[3] = {grid->nx, grid->ny, grid->nz};
   for (int k = 0; k < 3; ++k) {
@@ -1292,7 +1350,8 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return result;
+  if (result != LIGEN_OK) return result;
+  return chk.verdict(s);
 }
 
 int ligen_probe_gather(const float* records, int64_t n_records, int32_t bytes_per_load, int32_t loads_per_thread,
@@ -1414,6 +1473,8 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
   const size_t o_rs = ar.take(4 * (size_t)L * R);
   const size_t o_rk = ar.take((size_t)L * R);
   const size_t o_rc = ar.take((size_t)sh.rot * R);
+  CallCheck chk;
+  chk.plan(ar);
   if (ar.used > (size_t)LIGEN_STATIC_SCRATCH_BYTES)
     return fail(LIGEN_ERR_UNSUPPORTED,
                 "this batch needs %zu bytes of scratch; ligen_dock_batch_static has %zu "
@@ -1429,6 +1490,7 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
                                        "(ligands, grid and outputs)");
   if ((rc = static_scratch_base(&ar.base)) != LIGEN_OK) return rc;
   cudaStream_t s = (cudaStream_t)params->stream;
+  if ((rc = chk.arm(ar, s)) != LIGEN_OK) return rc;
 
   // Every scratch region is written in full before it is read within this
   // call, so nothing is cleared between calls.
@@ -1449,6 +1511,7 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
   da.lig = lig;
   da.pk = pk;
   da.grid = make_view(grid, coef, params->out_penalty);
+  da.grid.check = chk.d;
   const float h = grid->spacing;
   const int np[3] = {grid->nx, grid->ny, grid->nz};
   for (int k = 0; k < 3; ++k) {
@@ -1492,5 +1555,5 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
   LG_CUDA(launch_topk(ta, s));
   if (params->status)
     LG_CUDA(cudaMemcpyAsync(params->status, pk.status, 4 * (size_t)L, cudaMemcpyDeviceToDevice, s));
-  return LIGEN_OK;
+  return chk.verdict(s);
 }

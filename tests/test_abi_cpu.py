@@ -133,6 +133,7 @@ def test_null_structs_rejected(abi):
     assert lib.ligen_tune_set(0, 8, 10) == -1 and lib.ligen_tune_set(0, 4, 64) == -1
     assert lib.ligen_autotune(None, None, None, 1, None, None, None) == -1
     assert lib.ligen_probe_stream(None, 16, 1, None, None, None, None) == -1
+    assert lib.ligen_set_workspace_limit(1 << 20) == 0 and lib.ligen_set_workspace_limit(0) == 0
 
 
 def test_package_refuses_to_load_without_library(tmp_path):

@@ -1,0 +1,50 @@
+"""The bounds-checked build (needs a GPU).
+
+libligen_checked.so compares every data-dependent device index with its
+bound (grid records and channels, lattice nodes of the FP64 re-score,
+ligand sizes against the launch's shared-memory carve-up, bond endpoints and
+moving atoms against the ligand's atoms); a violation is recorded and the
+access skipped, and the call returns LIGEN_ERR_CHECK. A child process runs
+every kernel through that build on seeded inputs (every call must succeed,
+i.e. no index was ever out of range), and its results must equal the normal
+build's: bit for bit for the packer and every docking form (the checks
+change no arithmetic there), within FP32 rounding for gradients and
+refinement, whose compiled arithmetic the extra branches may reorder."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def lg():
+    import paper_2303_06150_gb300 as lg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return lg
+
+
+def test_checked_build_runs_clean_and_matches(lg, tmp_path):
+    from paper_2303_06150_gb300 import build as b
+    checked = b.build(checked=True)
+    out = tmp_path / "checked.npz"
+    r = subprocess.run([sys.executable, os.path.join(HERE, "checked_calls.py"), checked, str(out)],
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    import checked_calls
+    ref = checked_calls.run_all(lg)
+    got = dict(np.load(out))
+    assert set(got) == set(ref)
+    for k in ref:
+        if k == "refine.accept":      # a last-bit change may flip a near-tie accept
+            assert np.mean(got[k] != ref[k]) <= 0.01, k
+        elif k.startswith(("grad.", "refine.")):
+            np.testing.assert_allclose(got[k], ref[k], rtol=1e-4, atol=1e-4, err_msg=k)
+        else:
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
