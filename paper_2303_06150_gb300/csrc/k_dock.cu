@@ -176,8 +176,20 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) torsion_cs(sub + G * s, a.step_deg, &cs[s], &sn[s]);
 
+  // Converged restarts. A decision at a state the restart already swept
+  // from repeats that sweep exactly (same positions, same arithmetic), so
+  // once n consecutive decisions kept their torsion (j = 0) every later one
+  // does too. When all restarts of the warp are there, the rest of the sweep
+  // is skipped and its decisions recorded as 0: results are unchanged.
+  int kept = 0;   // consecutive j = 0 decisions of this restart
   for (int p = 0; p < a.passes; ++p) {
     for (int b = 0; b < n; ++b) {
+      if (__all_sync(kFull, kept >= n)) {
+        if (trace && sub == 0)
+          for (int d = p * n + b; d < a.passes * n; ++d) trace[1 + d] = 0;
+        p = a.passes;   // leaves both loops
+        break;
+      }
       const uchar4 bi = S.sb[b];
       const int vi = bi.y, m = bi.z, off = S.soff[b];
       const float vx = S.cx[vi * rpc + rr], vy = S.cy[vi * rpc + rr], vz = S.cz[vi * rpc + rr];
@@ -248,6 +260,7 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
         S.scnt[b * rpc + rr] = (uint8_t)((S.scnt[b * rpc + rr] + jb) % nt);
         if (trace) trace[1 + p * n + b] = (int16_t)jb;
       }
+      kept = (jb == 0) ? kept + 1 : 0;
     }
   }
 
