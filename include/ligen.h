@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define LIGEN_ABI_VERSION 3
+#define LIGEN_ABI_VERSION 4
 #define LIGEN_MAX_ATOMS 256
 #define LIGEN_MAX_ROT 32
 #define LIGEN_MAX_CHANNELS 64
@@ -190,6 +190,14 @@ typedef struct ligen_params {
   int32_t reserved3;
   double* scores_f64;   /* optional [L][K], same memory space as out_scores:
                            the FP64 scores (needs rescore_fp64 = 1) */
+  int64_t* samples;     /* optional, HOST, 1 value: the atom samples the
+                           search needed, summed over all sites: per restart
+                           n_rigid * N for the rigid stage plus, for every
+                           torsion decision that had to be swept (not a clean
+                           bond, see the docking kernel), (360/step - 1) *
+                           (moving atoms - 1); exhaustive mode: every
+                           combination's N. Counting makes the call wait
+                           for its work. */
 } ligen_params_t;
 
 /* Dock every ligand (paper §2, the dock task; cost per §3 follows atoms and
@@ -242,7 +250,7 @@ int ligen_dock_sites(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
  *     the process exits); the call itself allocates nothing. A batch whose
  *     scratch would exceed it is rejected with LIGEN_ERR_UNSUPPORTED before
  *     any device work. Scratch bytes, each term rounded up to 256: grid
- *     cells (nx-1)(ny-1)(nz-1) * nc * 32; 16 per atom; 132 per rotatable
+ *     cells (nx-1)(ny-1)(nz-1) * nc * 32; 16 per atom; 136 per rotatable
  *     bond; 4 per ligand; restarts * (5 per ligand + 1 per rotatable bond).
  *   - Ligands, grid and every output must be device memory.
  *   - The first call on a device looks up the array's device address (with
@@ -251,7 +259,7 @@ int ligen_dock_sites(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
  *     instance on different streams without ordering) race and corrupt each
  *     other's results. Each call writes every scratch region before reading
  *     it, so the contents left by the previous call do not matter.
- *   - stage_ms is ignored. */
+ *   - stage_ms and samples are ignored; mode must be 0. */
 #define LIGEN_STATIC_SCRATCH_BYTES (32u << 20)
 int ligen_dock_batch_static(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                             const ligen_params_t* params, float* out_poses, float* out_scores);
@@ -319,6 +327,16 @@ int ligen_refine_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
  * Any output may be NULL. Outputs share one memory space. */
 int ligen_pack_ligands(const ligen_ligands_t* ligands, int32_t n_channels, uint32_t* frag_bits,
                        int32_t* axis, int32_t* bucket, int32_t* status, void* stream);
+
+/* The packer's bond interaction masks, which the docking kernel uses to
+ * skip sweeps that cannot change the pose (no counterpart in the paper).
+ *   touch [sum n]  for ligand l's bond b' (entry rot_off[l] + b'), bit b is
+ *                  set when turning b' moves an atom that bond b's sweep
+ *                  reads: an atom of b's moving side (v_b included) or b's
+ *                  fixed end u_b. Turning b' moves its moving side except
+ *                  v_b'. Bit b' is always set. 0 for an invalid ligand.
+ * `touch` may be host or device memory. */
+int ligen_pack_touch(const ligen_ligands_t* ligands, int32_t n_channels, uint32_t* touch, void* stream);
 
 /* Paper Eq. 1: ligands per bucket l = b * SM * t / ws for the docking
  * kernel instance used for ligands of up to max_atoms atoms, with b from the

@@ -49,7 +49,7 @@ class ParamsT(C.Structure):
                 ("jitter", C.c_float), ("out_penalty", C.c_float), ("stream", P), ("status", P),
                 ("trace", P), ("top_restart", P), ("stage_ms", P), ("batching", C.c_int32),
                 ("grid_format", C.c_int32), ("rescore_fp64", C.c_int32), ("reserved3", C.c_int32),
-                ("scores_f64", P)]
+                ("scores_f64", P), ("samples", P)]
 
 
 # Every function include/ligen.h declares, with its ctypes signature.
@@ -71,6 +71,7 @@ SIGNATURES = {
     "ligen_last_error": (C.c_char_p, []),
     "ligen_probe_stream": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P, P]),
     "ligen_set_workspace_limit": (C.c_int, [C.c_int64]),
+    "ligen_pack_touch": (C.c_int, [P, C.c_int32, P, P]),
     "ligen_abi_version": (C.c_int, []),
 }
 

@@ -116,6 +116,7 @@ class DockResult:
     top_restart: torch.Tensor | None
     stage_ms: np.ndarray | None
     scores_f64: torch.Tensor | None = None
+    samples: int | None = None   # atom samples the search needed (count_samples=True)
 
     def ligand_poses(self, rot_off, l: int) -> torch.Tensor:
         K = self.scores.shape[1]
@@ -133,7 +134,8 @@ def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_ste
                top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
                status: bool = True, trace: bool = False, top_restart: bool = False,
                stage_ms: bool = False, batching: str = "plain", grid_format: str = "f32",
-               rescore_fp64: bool = False, mode: str = "greedy", out: DockResult | None = None) -> DockResult:
+               rescore_fp64: bool = False, mode: str = "greedy", count_samples: bool = False,
+               out: DockResult | None = None) -> DockResult:
     """ligen_dock_batch: dock every ligand, keep the top_k poses of each.
 
     batching: "plain" (one launch) or "buckets" (paper §3 classes, one
@@ -142,14 +144,20 @@ def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_ste
     rescore_fp64: re-score and re-rank the kept poses in FP64 on the GPU;
     the FP64 scores are returned in `scores_f64`.
     mode: "greedy" (the search) or "exhaustive" (every combination of cube
-    rotation and torsion increments per restart; small ligands only)."""
+    rotation and torsion increments per restart; small ligands only).
+    count_samples: return in `samples` the atom samples the search needed
+    (the call then waits for its work)."""
     lib = _abi.load()
     if out is None:
         out = _dock_outputs(ligands, restarts, passes, top_k, (), status, trace, top_restart, stage_ms, rescore_fp64)
     p = _dock_params(ligands.device, out, restarts, torsion_step_deg, passes, top_k, seed, n_rigid, jitter,
                      out_penalty, batching, grid_format, rescore_fp64, mode)
+    n_samples = C.c_int64(0)
+    if count_samples:
+        p.samples = C.cast(C.pointer(n_samples), C.c_void_p)
     check(lib.ligen_dock_batch(C.byref(ligands._s), C.byref(grid._s), C.byref(p), _ptr(out.poses),
                                _ptr(out.scores)))
+    out.samples = int(n_samples.value) if count_samples else None
     return out
 
 
@@ -309,6 +317,15 @@ def pack_ligands(ligands: Ligands, n_channels: int):
     check(lib.ligen_pack_ligands(C.byref(ligands._s), n_channels, _ptr(bits), _ptr(axis), _ptr(bucket),
                                  _ptr(status), _stream_handle(dev)))
     return bits[:n_sum], axis[:n_sum], bucket, status
+
+
+def pack_touch(ligands: Ligands, n_channels: int) -> torch.Tensor:
+    """ligen_pack_touch: bond interaction masks [sum n] (uint32 bits as int64)."""
+    lib = _abi.load()
+    n_sum = int(ligands.h_rot_off[-1])
+    out = _empty((max(n_sum, 1),), torch.int32, ligands.device)
+    check(lib.ligen_pack_touch(C.byref(ligands._s), n_channels, _ptr(out), _stream_handle(ligands.device)))
+    return out[:n_sum].to(torch.int64) & 0xFFFFFFFF
 
 
 def bucket_size(max_atoms: int) -> dict:

@@ -30,7 +30,13 @@ struct Packed {
   int32_t* bucket;   // [L] optional
   uint32_t* fbits;   // [sum n][8] optional: full moving side as a bit mask
   int32_t* axis;     // [sum n][2] optional: (u, v)
+  uint32_t* touch;   // [sum n] optional: bit b of touch[b'] set when turning bond b'
+                     // moves an atom bond b's sweep reads (bit b' always set)
 };
+
+// Sample counters are spread over this many slots (summed on the host) so
+// that CTAs do not all add to one address.
+constexpr int kSampleSlots = 64;
 
 struct DockArgs {
   LigandsDev lig;
@@ -55,6 +61,7 @@ struct DockArgs {
   uint8_t* res_k;     // [L][R]
   uint8_t* res_cnt;   // [sum n][R] torsion increments (mod n_theta) per restart
   int16_t* trace;     // optional
+  unsigned long long* samples;   // optional [kSampleSlots]: atom samples the search needed
 };
 
 // Exhaustive search (mode 1): at most kExMaxRot rotatable bonds per ligand

@@ -38,23 +38,25 @@ struct SmemLayout {
   uint16_t* soff;   // [max_rot]
   uint8_t* scnt;    // [max_rot][rpc]
   uint8_t* sfrag;   // [max_frag]
+  uint32_t* stouch; // [max_rot] bonds whose sweep a turn of this bond affects
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 __host__ __device__ inline size_t carve(int max_atoms, int max_rot, int max_frag, int rpc,
                                         unsigned char* base, SmemLayout* L) {
-  size_t off[8];
-  const size_t bytes[8] = {(size_t)max_atoms * 16, (size_t)max_atoms * rpc * 4, (size_t)max_atoms * rpc * 4,
+  size_t off[9];
+  const size_t bytes[9] = {(size_t)max_atoms * 16, (size_t)max_atoms * rpc * 4, (size_t)max_atoms * rpc * 4,
                            (size_t)max_atoms * rpc * 4, (size_t)max_rot * 4, (size_t)max_rot * 2,
-                           (size_t)max_rot * rpc, (size_t)max_frag};
+                           (size_t)max_rot * rpc, (size_t)max_frag, (size_t)max_rot * 4};
   size_t o = 0;
-  for (int i = 0; i < 8; ++i) { off[i] = o; o = align16(o + bytes[i]); }
+  for (int i = 0; i < 9; ++i) { off[i] = o; o = align16(o + bytes[i]); }
   if (L) {
     L->sx = (float4*)(base + off[0]); L->cx = (float*)(base + off[1]);
     L->cy = (float*)(base + off[2]);  L->cz = (float*)(base + off[3]);
     L->sb = (uchar4*)(base + off[4]); L->soff = (uint16_t*)(base + off[5]);
     L->scnt = base + off[6];          L->sfrag = base + off[7];
+    L->stouch = (uint32_t*)(base + off[8]);
   }
   return o;
 }
@@ -71,7 +73,9 @@ __device__ __forceinline__ void group_argmax(float& s, int& idx) {
 }
 
 // One work item: ligand l, restarts [chunk * rpc, chunk * rpc + rpc).
-template <int G, int SLOTS, int FMT>
+// COUNT: also add the samples the item's restarts needed to a.samples (a
+// separate instantiation, so the plain kernel carries no counting).
+template <int G, int SLOTS, int FMT, bool COUNT>
 __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S, int l, int chunk) {
   const int rpc = a.rpc;
   const int tid = threadIdx.x;
@@ -82,7 +86,10 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
   if (!lg_check(a.grid.check, N <= a.max_atoms && n <= a.max_rot, kChkItemShape)) return;   // uniform
 
   for (int i = tid; i < N; i += blockDim.x) S.sx[i] = a.pk.xc[a0 + i];
-  for (int b = tid; b < n; b += blockDim.x) S.sb[b] = a.pk.binfo[r0 + b];
+  for (int b = tid; b < n; b += blockDim.x) {
+    S.sb[b] = a.pk.binfo[r0 + b];
+    S.stouch[b] = a.pk.touch[r0 + b];
+  }
   for (int i = tid; i < n * rpc; i += blockDim.x) S.scnt[i] = 0;
   __syncthreads();
   if (tid == 0) {
@@ -176,19 +183,28 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) torsion_cs(sub + G * s, a.step_deg, &cs[s], &sn[s]);
 
-  // Converged restarts. A decision at a state the restart already swept
-  // from repeats that sweep exactly (same positions, same arithmetic), so
-  // once n consecutive decisions kept their torsion (j = 0) every later one
-  // does too. When all restarts of the warp are there, the rest of the sweep
-  // is skipped and its decisions recorded as 0: results are unchanged.
-  int kept = 0;   // consecutive j = 0 decisions of this restart
+  // Clean bonds. A bond's decision reads only the positions of its moving
+  // atoms and of its axis ends. Once its sweep kept the torsion (j = 0) and
+  // no later turn moved one of those atoms (the packer's touch masks), a new
+  // sweep would repeat it exactly and keep again: the bond is clean and its
+  // decision is 0 without sampling. A clean restart in a warp that sweeps
+  // samples nothing for that bond; a bond clean for the whole warp is
+  // skipped, and so is the rest of the sweep once every bond of every
+  // restart of the warp is clean. Results are unchanged.
+  uint32_t dirty = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);   // bonds that must be swept
+  long long needed = COUNT ? (long long)a.n_rigid * N : 0;   // samples this restart needs
   for (int p = 0; p < a.passes; ++p) {
     for (int b = 0; b < n; ++b) {
-      if (__all_sync(kFull, kept >= n)) {
+      if (__all_sync(kFull, dirty == 0u)) {
         if (trace && sub == 0)
           for (int d = p * n + b; d < a.passes * n; ++d) trace[1 + d] = 0;
         p = a.passes;   // leaves both loops
         break;
+      }
+      const bool live = (dirty >> b) & 1u;
+      if (!__any_sync(kFull, live)) {
+        if (trace && sub == 0) trace[1 + p * n + b] = 0;
+        continue;
       }
       const uchar4 bi = S.sb[b];
       const int vi = bi.y, m = bi.z, off = S.soff[b];
@@ -209,7 +225,11 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
         float acc[SLOTS];
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) acc[s] = 0.f;
-        for (int t = 0; t < m; ++t) {
+        // A clean bond samples nothing: its candidates all sum to 0, so it
+        // keeps j = 0, the decision a sweep would reach.
+        const int m_live = live ? m : 0;
+        if (COUNT && ch == 0) needed += (long long)(nt - 1) * m_live;
+        for (int t = 0; t < m_live; ++t) {
           const int i = S.sfrag[off + t];
           const int c = __float_as_int(S.sx[i].w);
           const float dx = S.cx[i * rpc + rr] - vx;
@@ -260,7 +280,7 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
         S.scnt[b * rpc + rr] = (uint8_t)((S.scnt[b * rpc + rr] + jb) % nt);
         if (trace) trace[1 + p * n + b] = (int16_t)jb;
       }
-      kept = (jb == 0) ? kept + 1 : 0;
+      dirty = (jb != 0) ? (dirty | S.stouch[b]) : (dirty & ~(1u << b));
     }
   }
 
@@ -271,6 +291,12 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
                        __float_as_int(S.sx[i].w));
 #pragma unroll
   for (int off = 1; off < G; off <<= 1) acc += __shfl_xor_sync(kFull, acc, off);
+  if constexpr (COUNT) {   // one add per warp, spread over the counter slots
+    long long v = (active && sub == 0) ? needed : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((tid & 31) == 0) atomicAdd(&a.samples[blockIdx.x % kSampleSlots], (unsigned long long)v);
+  }
   if (active && sub == 0) {
     const size_t lr = (size_t)l * a.R + r;
     a.res_score[lr] = acc;
@@ -288,7 +314,7 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
 template <int G>
 constexpr int dock_min_ctas() { return G == 8 ? 8 : 1; }
 
-template <int G, int SLOTS, int FMT>
+template <int G, int SLOTS, int FMT, bool COUNT>
 __global__ void __launch_bounds__(128, dock_min_ctas<G>()) dock_kernel(const DockArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next_item;
@@ -306,7 +332,7 @@ __global__ void __launch_bounds__(128, dock_min_ctas<G>()) dock_kernel(const Doc
     const int li = item / a.chunks;
     const int l = a.list ? a.list[li] : li;
     if (a.pk.status[l] == 0)   // uniform over the CTA
-      dock_item<G, SLOTS, FMT>(a, S, l, item - li * a.chunks);
+      dock_item<G, SLOTS, FMT, COUNT>(a, S, l, item - li * a.chunks);
     if (!a.queue) break;
     __syncthreads();   // shared memory is reused by the next item
   }
@@ -326,16 +352,23 @@ using KernelFn = void (*)(DockArgs);
 // chunk of the sweep. The 16-bit record formats exist for 4 and 8 lanes.
 struct Shape {
   int G, SLOTS, FMT;
-  KernelFn fn;
+  KernelFn fn, fn_count;   // plain, and counting the samples needed
 };
 const Shape kShapes[] = {
-    {2, 6, kRecF32, dock_kernel<2, 6, kRecF32>},     {2, 18, kRecF32, dock_kernel<2, 18, kRecF32>},
-    {4, 3, kRecF32, dock_kernel<4, 3, kRecF32>},     {4, 9, kRecF32, dock_kernel<4, 9, kRecF32>},
-    {8, 2, kRecF32, dock_kernel<8, 2, kRecF32>},     {8, 5, kRecF32, dock_kernel<8, 5, kRecF32>},
-    {4, 3, kRecF16, dock_kernel<4, 3, kRecF16>},     {4, 9, kRecF16, dock_kernel<4, 9, kRecF16>},
-    {8, 2, kRecF16, dock_kernel<8, 2, kRecF16>},     {8, 5, kRecF16, dock_kernel<8, 5, kRecF16>},
-    {4, 3, kRecBF16, dock_kernel<4, 3, kRecBF16>},   {4, 9, kRecBF16, dock_kernel<4, 9, kRecBF16>},
-    {8, 2, kRecBF16, dock_kernel<8, 2, kRecBF16>},   {8, 5, kRecBF16, dock_kernel<8, 5, kRecBF16>},
+    {2, 6, kRecF32, dock_kernel<2, 6, kRecF32, false>, dock_kernel<2, 6, kRecF32, true>},
+    {2, 18, kRecF32, dock_kernel<2, 18, kRecF32, false>, dock_kernel<2, 18, kRecF32, true>},
+    {4, 3, kRecF32, dock_kernel<4, 3, kRecF32, false>, dock_kernel<4, 3, kRecF32, true>},
+    {4, 9, kRecF32, dock_kernel<4, 9, kRecF32, false>, dock_kernel<4, 9, kRecF32, true>},
+    {8, 2, kRecF32, dock_kernel<8, 2, kRecF32, false>, dock_kernel<8, 2, kRecF32, true>},
+    {8, 5, kRecF32, dock_kernel<8, 5, kRecF32, false>, dock_kernel<8, 5, kRecF32, true>},
+    {4, 3, kRecF16, dock_kernel<4, 3, kRecF16, false>, dock_kernel<4, 3, kRecF16, true>},
+    {4, 9, kRecF16, dock_kernel<4, 9, kRecF16, false>, dock_kernel<4, 9, kRecF16, true>},
+    {8, 2, kRecF16, dock_kernel<8, 2, kRecF16, false>, dock_kernel<8, 2, kRecF16, true>},
+    {8, 5, kRecF16, dock_kernel<8, 5, kRecF16, false>, dock_kernel<8, 5, kRecF16, true>},
+    {4, 3, kRecBF16, dock_kernel<4, 3, kRecBF16, false>, dock_kernel<4, 3, kRecBF16, true>},
+    {4, 9, kRecBF16, dock_kernel<4, 9, kRecBF16, false>, dock_kernel<4, 9, kRecBF16, true>},
+    {8, 2, kRecBF16, dock_kernel<8, 2, kRecBF16, false>, dock_kernel<8, 2, kRecBF16, true>},
+    {8, 5, kRecBF16, dock_kernel<8, 5, kRecBF16, false>, dock_kernel<8, 5, kRecBF16, true>},
 };
 
 // The instantiation for G lanes, n_theta increments and record format: the
@@ -365,19 +398,22 @@ cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s, bool s
   const Shape* sh = pick_shape(a.lanes, a.n_theta, a.fmt);
   if (!sh) return cudaErrorInvalidValue;
   const size_t smem = dock_smem_bytes(a.max_atoms, a.max_rot, a.max_frag, a.rpc);
+  const KernelFn fn = a.samples ? sh->fn_count : sh->fn;
   if (set_attr) {
-    cudaError_t e = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const unsigned blocks = a.queue ? (unsigned)grid_ctas : (unsigned)a.n_items;
-  sh->fn<<<blocks, a.rpc * a.lanes, smem, s>>>(a);
+  fn<<<blocks, a.rpc * a.lanes, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t dock_set_smem_limit(int lanes, int n_theta, int fmt, size_t smem) {
   const Shape* sh = pick_shape(lanes, n_theta, fmt);
   if (!sh) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sh->fn_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t dock_occupancy(int lanes, int n_theta, int fmt, int rpc, size_t smem, int* blocks_per_sm) {

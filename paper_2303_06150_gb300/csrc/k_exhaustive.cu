@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(kExThreads) exhaustive_kernel(const DockArgs a
       if (red_s[w] > best || (red_s[w] == best && red_c[w] < bestc)) { best = red_s[w]; bestc = red_c[w]; }
     if (bestc >= total) bestc = 0;   // only if every score is NaN; keeps the indices in range
     const size_t lr = (size_t)l * a.R + r;
+    if (a.samples) atomicAdd(&a.samples[blockIdx.x % kSampleSlots], (unsigned long long)(total * N));
     a.res_score[lr] = best;
     long long rem = bestc;
     uint8_t* cnt = a.res_cnt + (size_t)r0 * a.R + (size_t)r * n;

@@ -26,7 +26,17 @@ struct PackScratch {
   uint8_t tin[kMaxN];
   uint8_t order[kMaxN];
   uint8_t stack[kMaxN];
+  // per rotatable bond: moving side = atoms with preorder index in [lo, hi)
+  // (child side moves) or outside it; fixed endpoint u, moving endpoint v
+  uint16_t lo[LIGEN_MAX_ROT], hi[LIGEN_MAX_ROT];
+  uint8_t child_moves[LIGEN_MAX_ROT], u[LIGEN_MAX_ROT], v[LIGEN_MAX_ROT];
 };
+
+// Atom i (preorder index ti) is on the moving side of bond b.
+__device__ __forceinline__ bool on_moving_side(const PackScratch& S, int b, int ti) {
+  const bool in_sub = ti >= S.lo[b] && ti < S.hi[b];
+  return S.child_moves[b] ? in_sub : !in_sub;
+}
 
 __device__ __forceinline__ int rot_class(int n) {
   const int edges[11] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
@@ -174,6 +184,34 @@ __global__ void __launch_bounds__(32 * kPackWarps) pack_kernel(const LigandsDev 
       if (lane == 0) {
         out.binfo[gb] = make_uchar4((uint8_t)u, (uint8_t)v, (uint8_t)cnt, 0);
         if (out.axis) { out.axis[2 * gb] = u; out.axis[2 * gb + 1] = v; }
+        S.lo[b] = (uint16_t)lo;
+        S.hi[b] = (uint16_t)hi;
+        S.child_moves[b] = (uint8_t)child_moves;
+        S.u[b] = (uint8_t)u;
+        S.v[b] = (uint8_t)v;
+      }
+    }
+    __syncwarp();
+    // touch[b'] bit b: turning bond b' moves an atom that bond b's sweep reads
+    // (its moving side, v included, or its fixed endpoint u). Turning b'
+    // moves its moving side except v_b', which lies on its own axis.
+    if (out.touch) {
+      for (int bp = 0; bp < n; ++bp) {
+        uint32_t bits = 0u;
+        for (int b = 0; b < n; ++b) {
+          bool hit = false;
+          for (int base = 0; base < N && !hit; base += 32) {
+            const int i = base + lane;
+            bool h = false;
+            if (i < N) {
+              const int ti = S.tin[i];
+              h = on_moving_side(S, bp, ti) && i != S.v[bp] && (on_moving_side(S, b, ti) || i == S.u[b]);
+            }
+            hit = __any_sync(full, h);
+          }
+          if (hit) bits |= 1u << b;
+        }
+        if (lane == 0) out.touch[r0 + bp] = bits | (1u << bp);
       }
     }
   } else {
@@ -183,6 +221,7 @@ __global__ void __launch_bounds__(32 * kPackWarps) pack_kernel(const LigandsDev 
       if (lane == 0) {
         out.binfo[gb] = make_uchar4(0, 0, 0, 0);
         if (out.axis) { out.axis[2 * gb] = -1; out.axis[2 * gb + 1] = -1; }
+        if (out.touch) out.touch[gb] = 0u;
       }
     }
   }

@@ -498,7 +498,7 @@ std::string launch_key(const std::vector<DockArgs>& args, const std::vector<int>
     const DockArgs& a = args[i];
     const void* ptrs[] = {a.lig.atom_off, a.lig.xyz, a.lig.type, a.lig.bonds, a.lig.rot_off, a.lig.rot_edge,
                           a.pk.xc, a.pk.binfo, a.pk.frag, a.pk.status, a.grid.coef, a.res_score, a.res_k,
-                          a.res_cnt, a.trace, a.list, a.queue};
+                          a.res_cnt, a.trace, a.list, a.queue, a.samples, a.pk.touch, a.grid.check};
     append_key(k, ptrs, sizeof ptrs);
     const int ints[] = {a.lig.L, a.grid.cx, a.grid.cy, a.grid.cz, a.grid.nc, a.R, a.n_rigid, a.step_deg,
                         a.n_theta, a.passes, a.lanes, a.fmt, a.rpc, a.chunks, a.n_items, a.max_atoms,
@@ -699,6 +699,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
   const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
   const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
   const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
+  const size_t o_touch = ar.take(4 * (size_t)sh.rot);
   const size_t o_status = ar.take(4 * (size_t)L);
   const size_t o_rs = ar.take(4 * (size_t)L * R);
   const size_t o_rk = ar.take((size_t)L * R);
@@ -731,10 +732,16 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     o_order = ar.take(4 * (size_t)L);
     o_queue = ar.take(sizeof(int) * groups.size());
   }
+  const size_t o_samples = params->samples ? ar.take(8 * (size_t)kSampleSlots) : 0;
   CallCheck chk;
   chk.plan(ar);
   if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
   if ((rc = chk.arm(ar, s)) != LIGEN_OK) return rc;
+  unsigned long long* d_samples = nullptr;
+  if (params->samples) {
+    d_samples = ar.at<unsigned long long>(o_samples);
+    LG_CUDA(cudaMemsetAsync(d_samples, 0, 8 * (size_t)kSampleSlots, s));
+  }
 
   // stage times accumulate over the sites
   float stage_acc[LIGEN_N_STAGES] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -744,6 +751,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
   pk.xc = ar.at<float4>(o_xc);
   pk.binfo = ar.at<uchar4>(o_binfo);
   pk.frag = ar.at<uint8_t>(o_frag);
+  pk.touch = ar.at<uint32_t>(o_touch);
   pk.status = ar.at<int32_t>(o_status);
   const cudaMemcpyKind back = ohost ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
 
@@ -811,6 +819,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     da.res_k = ar.at<uint8_t>(o_rk);
     da.res_cnt = ar.at<uint8_t>(o_rc);
     da.trace = d_trace;
+    da.samples = d_samples;
     if (exhaustive) {
       LG_CUDA(launch_exhaustive(da, s));
     } else if (buckets) {
@@ -884,6 +893,14 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
   }
   if (stage_out)
     for (int k = 0; k < LIGEN_N_STAGES; ++k) stage_out[k] = stage_acc[k];
+  if (params->samples) {
+    unsigned long long h[kSampleSlots];
+    LG_CUDA(cudaMemcpyAsync(h, d_samples, sizeof h, cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaStreamSynchronize(s));
+    unsigned long long total = 0;
+    for (int k = 0; k < kSampleSlots; ++k) total += h[k];
+    *params->samples = (int64_t)total;
+  }
   if (ohost) LG_CUDA(cudaStreamSynchronize(s));
   return chk.verdict(s);
 }
@@ -1143,6 +1160,45 @@ int ligen_pack_ligands(const ligen_ligands_t* ligands, int32_t n_channels, uint3
   return LIGEN_OK;
 }
 
+int ligen_pack_touch(const ligen_ligands_t* ligands, int32_t n_channels, uint32_t* touch, void* stream) {
+  g_err.clear();
+  int rc;
+  LibShape sh;
+  if ((rc = check_ligands(ligands, 0, &sh)) != LIGEN_OK) return rc;
+  if (n_channels < 1 || n_channels > LIGEN_MAX_CHANNELS)
+    return fail(LIGEN_ERR_INVALID_ARG, "n_channels must be 1..%d", LIGEN_MAX_CHANNELS);
+  const int L = ligands->n_ligands;
+  if (L == 0 || sh.rot == 0) return LIGEN_OK;
+  if (!touch) return fail(LIGEN_ERR_INVALID_ARG, "touch is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int lhost = space_of({ligands->atom_off, ligands->xyz, ligands->type, ligands->bonds,
+                              ligands->rot_off, ligands->rot_edge});
+  const int ohost = space_of({touch});
+  if (lhost < 0) return fail(LIGEN_ERR_INVALID_ARG, "ligand arrays mix host and device memory");
+  Arena ar;
+  LigandPlan lp;
+  plan_ligands(ar, ligands, sh, lhost == 1, &lp);
+  const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
+  const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
+  const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
+  const size_t o_status = ar.take(4 * (size_t)L);
+  const size_t o_touch = ar.take(4 * (size_t)sh.rot);
+  if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+  LigandsDev lig;
+  if ((rc = stage_ligands(ar, ligands, sh, lp, s, &lig)) != LIGEN_OK) return rc;
+  Packed pk{};
+  pk.xc = ar.at<float4>(o_xc);
+  pk.binfo = ar.at<uchar4>(o_binfo);
+  pk.frag = ar.at<uint8_t>(o_frag);
+  pk.status = ar.at<int32_t>(o_status);
+  pk.touch = ar.at<uint32_t>(o_touch);
+  LG_CUDA(launch_pack(lig, n_channels, pk, s));
+  LG_CUDA(cudaMemcpyAsync(touch, pk.touch, 4 * (size_t)sh.rot, ohost ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          s));
+  if (ohost) LG_CUDA(cudaStreamSynchronize(s));
+  return LIGEN_OK;
+}
+
 int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t, int32_t* ws) {
   g_err.clear();
   if (max_atoms < 1 || max_atoms > LIGEN_MAX_ATOMS)
@@ -1246,6 +1302,7 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
   const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
   const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
+  const size_t o_touch = ar.take(4 * (size_t)sh.rot);
   const size_t o_status = ar.take(4 * (size_t)L);
   const size_t o_rs = ar.take(4 * (size_t)L * R);
   const size_t o_rk = ar.take((size_t)L * R);
@@ -1267,6 +1324,7 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   pk.xc = ar.at<float4>(o_xc);
   pk.binfo = ar.at<uchar4>(o_binfo);
   pk.frag = ar.at<uint8_t>(o_frag);
+  pk.touch = ar.at<uint32_t>(o_touch);
   pk.status = ar.at<int32_t>(o_status);
   LG_CUDA(launch_pack(lig, grid->nc, pk, s));
   int32_t* d_order = ar.at<int32_t>(o_order);
@@ -1469,6 +1527,7 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
   const size_t o_xc = ar.take(16 * (size_t)sh.atoms);
   const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
   const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
+  const size_t o_touch = ar.take(4 * (size_t)sh.rot);
   const size_t o_status = ar.take(4 * (size_t)L);
   const size_t o_rs = ar.take(4 * (size_t)L * R);
   const size_t o_rk = ar.take((size_t)L * R);
@@ -1504,6 +1563,7 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
   pk.xc = ar.at<float4>(o_xc);
   pk.binfo = ar.at<uchar4>(o_binfo);
   pk.frag = ar.at<uint8_t>(o_frag);
+  pk.touch = ar.at<uint32_t>(o_touch);
   pk.status = ar.at<int32_t>(o_status);
   LG_CUDA(launch_pack(lig, grid->nc, pk, s));
 

@@ -62,6 +62,7 @@ def run_all(lg) -> dict:
     bits, axis, bucket, status = lg.pack_ligands(Ls, grids.dims[3])
     out["pack.bits"], out["pack.axis"] = bits.cpu().numpy(), axis.cpu().numpy()
     out["pack.bucket"], out["pack.status"] = bucket.cpu().numpy(), status.cpu().numpy()
+    out["pack.touch"] = lg.pack_touch(Ls, grids.dims[3]).cpu().numpy()
     saved = lg.tune_get()
     try:
         tuned = lg.autotune(Ls, Gs, sample=16, **kws)

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(abi):
     for name in declared:
         assert hasattr(lib, name), name
     assert set(abi.SIGNATURES) == declared
-    assert lib.ligen_abi_version() == 3
+    assert lib.ligen_abi_version() == 4
 
 
 def _lig_struct(abi, arrays):

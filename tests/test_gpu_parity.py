@@ -65,6 +65,40 @@ def test_packer_bit_exact(lg, oracle_lib, small32, screen_sample, which):
         assert np.array_equal(axis[r0:r1], ax), l
 
 
+@pytest.mark.parametrize("which", ["small32", "screen64", "bad"])
+def test_touch_masks_bit_exact(lg, oracle_lib, small32, screen_sample, which):
+    """Bond interaction masks, against their definition on the oracle's
+    fragments: bit b of bond b' is set when b' moves (its moving side minus
+    its own v) an atom of b's moving side or b's fixed end; always for b = b'."""
+    if which == "bad":
+        ligs, _ = _bad_ligands()
+        lib, nc = gen.from_ligands(ligs), 4
+    else:
+        _, lib, _ = small32 if which == "small32" else screen_sample
+        nc = 4 if which == "small32" else 8
+    L = lg.Ligands.from_arrays(lib, "cuda")
+    touch = lg.pack_touch(L, nc).cpu().numpy()
+    for l in range(lib.n_ligands):
+        g = lib.ligand(l)
+        lig = oracle_lib.OLigand(g["xyz"], g["type"], g["bonds"], g["rot_edge"])
+        r0, n = lib.rot_off[l], lib.n_rot[l]
+        if oracle_lib.validate(lig, nc):
+            assert np.all(touch[r0:r0 + n] == 0)
+            continue
+        _, mask, axis = oracle_lib.fragments(lig)
+        mask = mask.reshape(n, -1).astype(bool)
+        for bp in range(n):
+            moved = mask[bp].copy()
+            moved[axis[bp][1]] = False
+            want = 0
+            for b in range(n):
+                reads = mask[b].copy()
+                reads[axis[b][0]] = True
+                if b == bp or np.any(moved & reads):
+                    want |= 1 << b
+            assert int(touch[r0 + bp]) == want, (l, bp)
+
+
 # ------------------------------------------------------------ scoring ---
 def _random_poses(rng, lib, grid, K):
     out = []
@@ -340,3 +374,39 @@ def test_top_k_total_order_both_paths(lg, small32, restarts):
         eq = np.diff(sc[l]) == 0
         assert np.all(np.diff(top[l])[eq] > 0)
     assert torch.equal(part.scores, full.scores[:, :30]) and torch.equal(part.top_restart, full.top_restart[:, :30])
+
+
+def test_sample_count_follows_the_clean_bond_rule(lg, small32, screen_sample):
+    """The kernel's count of needed samples equals the count replayed from
+    its own decisions: per restart n_rigid * N, plus (n_theta - 1) * (moving
+    atoms - 1) for each decision of a bond that was not clean. A bond is
+    clean after a sweep that kept its torsion, until a turn of a bond whose
+    touch mask names it."""
+    for w, lib, grid in (small32, screen_sample):
+        s = dict(w["search"], restarts=16, top_k=4)
+        L = lg.Ligands.from_arrays(lib, "cuda")
+        G = lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, "cuda")
+        res = lg.dock_batch(L, G, restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"],
+                            passes=s["passes"], top_k=s["top_k"], seed=s["seed"], trace=True, count_samples=True)
+        trace = res.trace.cpu().numpy()
+        touch = lg.pack_touch(L, grid.dims[3]).cpu().numpy()
+        nt = 360 // s["torsion_step_deg"]
+        P, R = s["passes"], s["restarts"]
+        bits, _, _, _ = lg.pack_ligands(L, grid.dims[3])
+        moving = np.unpackbits(bits.cpu().numpy().view(np.uint8), bitorder="little").reshape(len(bits), -1).sum(1)
+        want = 0
+        for l in range(lib.n_ligands):
+            n, r0 = int(lib.n_rot[l]), int(lib.rot_off[l])
+            tr = parity.ligand_trace(trace, lib.rot_off, R, P, l)
+            for r in range(R):
+                want += 24 * int(lib.n_atoms[l])
+                dirty = (1 << n) - 1
+                for d in range(P * n):
+                    b = d % n
+                    jb = int(tr[r, 1 + d])
+                    if dirty >> b & 1:
+                        want += (nt - 1) * (int(moving[r0 + b]) - 1)
+                    else:
+                        assert jb == 0
+                    dirty = dirty | int(touch[r0 + b]) if jb else dirty & ~(1 << b)
+        assert res.samples == want
