@@ -184,6 +184,30 @@ __host__ __device__ __forceinline__ size_t rec_count(int cx, int cy, int cz, int
   return (size_t)cx * cy * cz * nc;
 }
 
+// Packed FP32 pairs (sm_100 family: fma.rn.f32x2, sub.rn.f32x2): one
+// instruction for two independent operations, each element rounded exactly
+// as the scalar operation, so results are bit-identical to scalar code.
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {   // a * b + c
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a.x, a.y)), "l"(pk2(b.x, b.y)), "l"(pk2(c.x, c.y)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a.x, a.y)), "l"(pk2(b.x, b.y)));
+  return upk2(d);
+}
+
 // 256-bit read-only load (sm_100+): one 32-byte record in one instruction.
 // Not volatile: the load has no side effect, so the compiler may batch it.
 __device__ __forceinline__ void ld_global_v8(const float* p, float (&v)[8]) {
@@ -276,10 +300,16 @@ __device__ __forceinline__ float grid_sample_fmt(const GridView& g, float ux, fl
       const uint4 v = __ldg(rec);
       const float2 a = unpack2<FMT>(v.x), b = unpack2<FMT>(v.y);   // (c000, c100), (c010, c110)
       const float2 d = unpack2<FMT>(v.z), f = unpack2<FMT>(v.w);   // (c001, c101), (c011, c111)
-      const float x00 = fmaf(dx, a.y - a.x, a.x), x10 = fmaf(dx, b.y - b.x, b.x);
-      const float x01 = fmaf(dx, d.y - d.x, d.x), x11 = fmaf(dx, f.y - f.x, f.x);
-      const float y0 = fmaf(dy, x10 - x00, x00), y1 = fmaf(dy, x11 - x01, x01);
-      e = fmaf(dz, y1 - y0, y0);
+      // 7 lerps v0 + d (v1 - v0), x-lerps and y-lerps in packed pairs
+      // (measured: 1.5% faster FP16 docking; the FP32 sampler lost 1% the same way)
+      const float2 dxx = make_float2(dx, dx);
+      const float2 p0 = make_float2(a.x, b.x), q0 = make_float2(a.y, b.y);   // (c000, c010), (c100, c110)
+      const float2 p1 = make_float2(d.x, f.x), q1 = make_float2(d.y, f.y);   // (c001, c011), (c101, c111)
+      const float2 x0 = fma2(dxx, sub2(q0, p0), p0);                         // (x00, x10)
+      const float2 x1 = fma2(dxx, sub2(q1, p1), p1);                         // (x01, x11)
+      const float2 lo = make_float2(x0.x, x1.x), hi = make_float2(x0.y, x1.y);
+      const float2 y = fma2(make_float2(dy, dy), sub2(hi, lo), lo);          // (y0, y1)
+      e = fmaf(dz, y.y - y.x, y.x);
     }
     return e;
   }

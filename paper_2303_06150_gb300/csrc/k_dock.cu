@@ -239,12 +239,33 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
           const float px = fmaf(kx, kd, vx), py = fmaf(ky, kd, vy), pz = fmaf(kz, kd, vz);
           const float ex = fmaf(-kx, kd, dx), ey = fmaf(-ky, kd, dy), ez = fmaf(-kz, kd, dz);
           const float qx = ky * dz - kz * dy, qy = kz * dx - kx * dz, qz = kx * dy - ky * dx;
+          if constexpr (FMT != kRecF32) {
+            // two increments per packed instruction (measured: 0.5% faster
+            // with 16-bit records, 1% slower with FP32 records)
+            float ux[SLOTS], uy[SLOTS], uz[SLOTS];
 #pragma unroll
-          for (int s = 0; s < SLOTS; ++s) {
-            const float ux = fmaf(ex, cs[s], fmaf(qx, sn[s], px));
-            const float uy = fmaf(ey, cs[s], fmaf(qy, sn[s], py));
-            const float uz = fmaf(ez, cs[s], fmaf(qz, sn[s], pz));
-            acc[s] -= grid_sample_fmt<FMT>(grid, ux, uy, uz, c);
+            for (int s = 0; s + 1 < SLOTS; s += 2) {
+              const float2 cc = make_float2(cs[s], cs[s + 1]), ss = make_float2(sn[s], sn[s + 1]);
+              const float2 X = fma2(make_float2(ex, ex), cc, fma2(make_float2(qx, qx), ss, make_float2(px, px)));
+              const float2 Y = fma2(make_float2(ey, ey), cc, fma2(make_float2(qy, qy), ss, make_float2(py, py)));
+              const float2 Z = fma2(make_float2(ez, ez), cc, fma2(make_float2(qz, qz), ss, make_float2(pz, pz)));
+              ux[s] = X.x; ux[s + 1] = X.y; uy[s] = Y.x; uy[s + 1] = Y.y; uz[s] = Z.x; uz[s + 1] = Z.y;
+            }
+            if constexpr (SLOTS % 2 == 1) {
+              ux[SLOTS - 1] = fmaf(ex, cs[SLOTS - 1], fmaf(qx, sn[SLOTS - 1], px));
+              uy[SLOTS - 1] = fmaf(ey, cs[SLOTS - 1], fmaf(qy, sn[SLOTS - 1], py));
+              uz[SLOTS - 1] = fmaf(ez, cs[SLOTS - 1], fmaf(qz, sn[SLOTS - 1], pz));
+            }
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s) acc[s] -= grid_sample_fmt<FMT>(grid, ux[s], uy[s], uz[s], c);
+          } else {
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s) {
+              const float ux = fmaf(ex, cs[s], fmaf(qx, sn[s], px));
+              const float uy = fmaf(ey, cs[s], fmaf(qy, sn[s], py));
+              const float uz = fmaf(ez, cs[s], fmaf(qz, sn[s], pz));
+              acc[s] -= grid_sample_fmt<FMT>(grid, ux, uy, uz, c);
+            }
           }
         }
 #pragma unroll
