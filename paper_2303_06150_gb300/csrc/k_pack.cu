@@ -28,15 +28,11 @@ struct PackScratch {
   uint8_t stack[kMaxN];
   // per rotatable bond: moving side = atoms with preorder index in [lo, hi)
   // (child side moves) or outside it; fixed endpoint u, moving endpoint v
-  uint16_t lo[LIGEN_MAX_ROT], hi[LIGEN_MAX_ROT];
-  uint8_t child_moves[LIGEN_MAX_ROT], u[LIGEN_MAX_ROT], v[LIGEN_MAX_ROT];
+  // per rotatable bond, as atom bit masks: the atoms a turn moves (moving
+  // side without v) and the atoms its sweep reads (moving side and u)
+  uint32_t moved[LIGEN_MAX_ROT][kMaxN / 32];
+  uint32_t reads[LIGEN_MAX_ROT][kMaxN / 32];
 };
-
-// Atom i (preorder index ti) is on the moving side of bond b.
-__device__ __forceinline__ bool on_moving_side(const PackScratch& S, int b, int ti) {
-  const bool in_sub = ti >= S.lo[b] && ti < S.hi[b];
-  return S.child_moves[b] ? in_sub : !in_sub;
-}
 
 __device__ __forceinline__ int rot_class(int n) {
   const int edges[11] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
@@ -178,17 +174,16 @@ __global__ void __launch_bounds__(32 * kPackWarps) pack_kernel(const LigandsDev 
         if (out.fbits && lane == 0) out.fbits[(size_t)gb * 8 + (base >> 5)] = word;
         const bool mx = mv & (i != v);
         const unsigned bx = __ballot_sync(full, mx);
+        if (lane == 0) {
+          S.moved[b][base >> 5] = bx;
+          S.reads[b][base >> 5] = word | (((u >> 5) == (base >> 5)) ? 1u << (u & 31) : 0u);
+        }
         if (mx) out.frag[(size_t)gb * kFragStride + cnt + __popc(bx & ((1u << lane) - 1u))] = (uint8_t)i;
         cnt += __popc(bx);
       }
       if (lane == 0) {
         out.binfo[gb] = make_uchar4((uint8_t)u, (uint8_t)v, (uint8_t)cnt, 0);
         if (out.axis) { out.axis[2 * gb] = u; out.axis[2 * gb + 1] = v; }
-        S.lo[b] = (uint16_t)lo;
-        S.hi[b] = (uint16_t)hi;
-        S.child_moves[b] = (uint8_t)child_moves;
-        S.u[b] = (uint8_t)u;
-        S.v[b] = (uint8_t)v;
       }
     }
     __syncwarp();
@@ -196,22 +191,15 @@ __global__ void __launch_bounds__(32 * kPackWarps) pack_kernel(const LigandsDev 
     // (its moving side, v included, or its fixed endpoint u). Turning b'
     // moves its moving side except v_b', which lies on its own axis.
     if (out.touch) {
-      for (int bp = 0; bp < n; ++bp) {
-        uint32_t bits = 0u;
+      const int words = (N + 31) >> 5;
+      for (int bp = lane; bp < n; bp += 32) {   // one lane per turning bond
+        uint32_t bits = 1u << bp;
         for (int b = 0; b < n; ++b) {
-          bool hit = false;
-          for (int base = 0; base < N && !hit; base += 32) {
-            const int i = base + lane;
-            bool h = false;
-            if (i < N) {
-              const int ti = S.tin[i];
-              h = on_moving_side(S, bp, ti) && i != S.v[bp] && (on_moving_side(S, b, ti) || i == S.u[b]);
-            }
-            hit = __any_sync(full, h);
-          }
+          uint32_t hit = 0u;
+          for (int w = 0; w < words; ++w) hit |= S.moved[bp][w] & S.reads[b][w];
           if (hit) bits |= 1u << b;
         }
-        if (lane == 0) out.touch[r0 + bp] = bits | (1u << bp);
+        out.touch[r0 + bp] = bits;
       }
     }
   } else {
