@@ -327,16 +327,17 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
   }
 }
 
-// Resident CTAs asked of the register allocator: 8-lane shapes fit in 64
-// registers with at most a few bytes of spill, which lets 8 CTAs (32 warps)
-// share an SM; measured on GB300, 3% faster with FP16 records and 0.6% with
-// FP32 than the 72-register build (7 CTAs). Narrower shapes keep more
-// registers, which their larger slot arrays need.
-template <int G>
-constexpr int dock_min_ctas() { return G == 8 ? 8 : 1; }
-
-template <int G, int SLOTS, int FMT, bool COUNT>
-__global__ void __launch_bounds__(128, dock_min_ctas<G>()) dock_kernel(const DockArgs a) {
+// MINB: resident CTAs asked of the register allocator (1: no request).
+// 8-lane shapes come in four builds: 8 CTAs (64 registers, some spill to
+// local memory), 7 (72 registers), 6 (~80) and unconstrained (~100, 4 CTAs).
+// More CTAs pay only while their shared memory leaves L1 room for the
+// spills and the gathers: measured on GB300, the screening library (~20 KB
+// per CTA) docks fastest with 8 CTAs, the bimodal one (27.6 KB per CTA) with
+// 7 (8 leave under 48 KB of L1 and run 60% slower; 6 CTAs 9%, the
+// unconstrained build 42%).
+// launch_dock takes the largest count whose CTAs fit kCtaSmemBudget.
+template <int G, int SLOTS, int FMT, bool COUNT, int MINB>
+__global__ void __launch_bounds__(128, MINB) dock_kernel(const DockArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next_item;
   SmemLayout S;
@@ -369,28 +370,52 @@ namespace {
 
 using KernelFn = void (*)(DockArgs);
 
+
 // Instantiated (G, SLOTS, record format) shapes; G * SLOTS increments per
 // chunk of the sweep. The 16-bit record formats exist for 4 and 8 lanes.
 struct Shape {
   int G, SLOTS, FMT;
-  KernelFn fn, fn_count;   // plain, and counting the samples needed
+  KernelFn fn[2][4];   // [counts the samples needed][build: 8, 7, 6 CTAs, unconstrained]
 };
+#define LG_BUILDS(G, S, F, C)                                                                         \
+  {dock_kernel<G, S, F, C, G == 8 ? 8 : 1>, dock_kernel<G, S, F, C, G == 8 ? 7 : 1>,                   \
+   dock_kernel<G, S, F, C, G == 8 ? 6 : 1>, dock_kernel<G, S, F, C, 1>}
+// The counting kernel only serves untimed calls: one build for all four.
+#define LG_COUNTING(G, S, F)                                                                          \
+  {dock_kernel<G, S, F, true, 1>, dock_kernel<G, S, F, true, 1>, dock_kernel<G, S, F, true, 1>,        \
+   dock_kernel<G, S, F, true, 1>}
+#define LG_SHAPE(G, S, F) {G, S, F, {LG_BUILDS(G, S, F, false), LG_COUNTING(G, S, F)}}
 const Shape kShapes[] = {
-    {2, 6, kRecF32, dock_kernel<2, 6, kRecF32, false>, dock_kernel<2, 6, kRecF32, true>},
-    {2, 18, kRecF32, dock_kernel<2, 18, kRecF32, false>, dock_kernel<2, 18, kRecF32, true>},
-    {4, 3, kRecF32, dock_kernel<4, 3, kRecF32, false>, dock_kernel<4, 3, kRecF32, true>},
-    {4, 9, kRecF32, dock_kernel<4, 9, kRecF32, false>, dock_kernel<4, 9, kRecF32, true>},
-    {8, 2, kRecF32, dock_kernel<8, 2, kRecF32, false>, dock_kernel<8, 2, kRecF32, true>},
-    {8, 5, kRecF32, dock_kernel<8, 5, kRecF32, false>, dock_kernel<8, 5, kRecF32, true>},
-    {4, 3, kRecF16, dock_kernel<4, 3, kRecF16, false>, dock_kernel<4, 3, kRecF16, true>},
-    {4, 9, kRecF16, dock_kernel<4, 9, kRecF16, false>, dock_kernel<4, 9, kRecF16, true>},
-    {8, 2, kRecF16, dock_kernel<8, 2, kRecF16, false>, dock_kernel<8, 2, kRecF16, true>},
-    {8, 5, kRecF16, dock_kernel<8, 5, kRecF16, false>, dock_kernel<8, 5, kRecF16, true>},
-    {4, 3, kRecBF16, dock_kernel<4, 3, kRecBF16, false>, dock_kernel<4, 3, kRecBF16, true>},
-    {4, 9, kRecBF16, dock_kernel<4, 9, kRecBF16, false>, dock_kernel<4, 9, kRecBF16, true>},
-    {8, 2, kRecBF16, dock_kernel<8, 2, kRecBF16, false>, dock_kernel<8, 2, kRecBF16, true>},
-    {8, 5, kRecBF16, dock_kernel<8, 5, kRecBF16, false>, dock_kernel<8, 5, kRecBF16, true>},
+    LG_SHAPE(2, 6, kRecF32),
+    LG_SHAPE(2, 18, kRecF32),
+    LG_SHAPE(4, 3, kRecF32),
+    LG_SHAPE(4, 9, kRecF32),
+    LG_SHAPE(8, 2, kRecF32),
+    LG_SHAPE(8, 5, kRecF32),
+    LG_SHAPE(4, 3, kRecF16),
+    LG_SHAPE(4, 9, kRecF16),
+    LG_SHAPE(8, 2, kRecF16),
+    LG_SHAPE(8, 5, kRecF16),
+    LG_SHAPE(4, 3, kRecBF16),
+    LG_SHAPE(4, 9, kRecBF16),
+    LG_SHAPE(8, 2, kRecBF16),
+    LG_SHAPE(8, 5, kRecBF16),
 };
+#undef LG_SHAPE
+#undef LG_COUNTING
+#undef LG_BUILDS
+
+// Shared memory the resident CTAs may take together (of the SM's 256 KB of
+// L1 and shared memory), and the build for a CTA of `smem` bytes: the one
+// asking for as many CTAs as fit that budget. 192 KB puts the screening
+// library (~20 KB per CTA) at 8 CTAs and the bimodal one (27.6 KB, with the
+// host's upper bound on the moving lists) at 7, the best of the measured
+// builds for each.
+constexpr size_t kCtaSmemBudget = 192 * 1024;
+int build_for(size_t smem) {
+  const size_t fit = smem ? kCtaSmemBudget / smem : 8;
+  return fit >= 8 ? 0 : fit >= 7 ? 1 : fit >= 6 ? 2 : 3;
+}
 
 // The instantiation for G lanes, n_theta increments and record format: the
 // fewest slots that cover n_theta in one chunk, else the largest (several
@@ -419,7 +444,7 @@ cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s, bool s
   const Shape* sh = pick_shape(a.lanes, a.n_theta, a.fmt);
   if (!sh) return cudaErrorInvalidValue;
   const size_t smem = dock_smem_bytes(a.max_atoms, a.max_rot, a.max_frag, a.rpc);
-  const KernelFn fn = a.samples ? sh->fn_count : sh->fn;
+  const KernelFn fn = sh->fn[a.samples != nullptr][build_for(smem)];
   if (set_attr) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -432,15 +457,19 @@ cudaError_t launch_dock(const DockArgs& a, int grid_ctas, cudaStream_t s, bool s
 cudaError_t dock_set_smem_limit(int lanes, int n_theta, int fmt, size_t smem) {
   const Shape* sh = pick_shape(lanes, n_theta, fmt);
   if (!sh) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sh->fn_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  for (int c = 0; c < 2; ++c)
+    for (int o = 0; o < 4; ++o) {
+      const cudaError_t e = cudaFuncSetAttribute(sh->fn[c][o], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
 }
 
 cudaError_t dock_occupancy(int lanes, int n_theta, int fmt, int rpc, size_t smem, int* blocks_per_sm) {
   const Shape* sh = pick_shape(lanes, n_theta, fmt);
   if (!sh) return cudaErrorInvalidValue;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sh->fn, rpc * lanes, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sh->fn[0][build_for(smem)], rpc * lanes,
+                                                       smem);
 }
 
 }  // namespace ligen
