@@ -336,7 +336,7 @@ struct Timer {
 
 // Default launch shape: 8 lanes per restart, up to 16 restarts per CTA
 // (measured on GB300: faster than 2 or 4 lanes for both small and large
-// ligands; 72 registers and half the shared memory of 4 lanes per CTA).
+// ligands; fewer registers and half the shared memory of 4 lanes per CTA).
 constexpr int kDefaultLanes = 8;
 
 int dock_restarts_per_cta(int R, int lanes) {
