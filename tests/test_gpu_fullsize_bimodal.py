@@ -1,0 +1,78 @@
+"""Full-size bimodal batching workload (200,000 ligands: 70% with 15-35 atoms
+and 0-8 torsions, 30% with 60-120 atoms and 8-30 torsions; 256 restarts,
+10-degree steps, 3 passes, top 30) through the bucketed layout, checked by
+properties of every output and against the oracle on sampled small and large
+ligands (needs a GPU). Decision traces stay on the device; only the sampled
+ligands' slices are copied back."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def run():
+    import paper_2303_06150_gb300 as lg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = gen.WORKLOADS["bimodal200k"]
+    lib = gen.make_library(w["library"])
+    grid = gen.make_grid(w["grid"])
+    s = w["search"]
+    L = lg.Ligands.from_arrays(lib, "cuda")
+    G = lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, "cuda")
+    res = lg.dock_batch(L, G, restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"], passes=s["passes"],
+                        top_k=s["top_k"], seed=s["seed"], n_rigid=s["n_rigid"], jitter=s["jitter"],
+                        out_penalty=s["out_penalty"], trace=True, top_restart=True, batching="buckets")
+    torch.cuda.synchronize()
+    return lg, w, lib, grid, res
+
+
+def test_every_output_is_well_formed(run):
+    lg, w, lib, grid, res = run
+    K, R = w["search"]["top_k"], w["search"]["restarts"]
+    assert int(res.status.abs().sum()) == 0
+    sc = res.scores.cpu().numpy()
+    top = res.top_restart.cpu().numpy()
+    assert np.isfinite(sc).all() and np.all(np.diff(sc, axis=1) <= 0)
+    assert top.min() >= 0 and top.max() < R
+    assert all(len(set(row)) == K for row in top[::997])
+    poses = res.poses
+    off = lg.pose_offsets(lib.rot_off, K)
+    for l in range(0, lib.n_ligands, 1999):
+        P = poses[int(off[l]):int(off[l + 1])].reshape(K, -1).cpu().numpy()
+        assert np.all(P[:, 3] >= 0)
+        np.testing.assert_allclose(np.linalg.norm(P[:, 3:7], axis=1), 1.0, atol=1e-6)
+        assert np.all((P[:, 7:] >= -np.pi - 1e-6) & (P[:, 7:] < np.pi + 1e-6))
+
+
+def test_sampled_small_and_large_ligands_match_oracle(run, oracle_lib):
+    lg, w, lib, grid, res = run
+    s = w["search"]
+    R, K, P = s["restarts"], s["top_k"], s["passes"]
+    small = np.nonzero(lib.n_atoms <= 35)[0]
+    large = np.nonzero(lib.n_atoms >= 60)[0]
+    pick = sorted({int(x) for x in small[np.linspace(0, len(small) - 1, 6).astype(int)]} |
+                  {int(x) for x in large[np.linspace(0, len(large) - 1, 3).astype(int)]} |
+                  {int(np.argmax(lib.n_rot)), int(np.argmax(lib.n_atoms))})
+    rs = range(0, 8)
+    ref = oracle_lib.dock_library(lib, grid, s, ligands=pick, restarts=rs)
+    scores = res.scores.cpu().numpy()
+    top = res.top_restart.cpu().numpy()
+    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    for r_ in ref:
+        l = r_["ligand"]
+        D = 1 + P * int(lib.n_rot[l])
+        start = R * (l + P * int(lib.rot_off[l]))
+        gt = res.trace[start:start + R * D].cpu().numpy().reshape(R, D)
+        final = {int(top[l, k]): float(scores[l, k]) for k in range(K)}
+        st = parity.check_dock_ligand(l, r_, gt, final)
+        for k in tot:
+            tot[k] += st[k]
+    print(tot)
+    assert tot["restarts"] == len(pick) * len(rs)
+    assert tot["clean"] >= 0.85 * tot["restarts"]
