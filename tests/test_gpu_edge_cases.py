@@ -1,0 +1,98 @@
+"""Edge cases of the docking path against the oracle (needs a GPU).
+
+Maximum ligand size (256 atoms, 32 rotatable bonds), degenerate search
+settings (no sweep pass, one rigid rotation, a 360-degree step, one restart,
+restart counts that leave a partial chunk), a one-atom ligand, a rotatable
+bond whose moving side is a single atom (an empty moving list), and a grid
+of a single cell that most atoms fall outside of."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lg():
+    import paper_2303_06150_gb300 as lg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return lg
+
+
+def _dock_and_check(lg, oracle_lib, lib, grid, s, restarts=None, min_clean=0.9):
+    L = lg.Ligands.from_arrays(lib, "cuda")
+    G = lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, "cuda")
+    R, K = s["restarts"], s["top_k"]
+    res = lg.dock_batch(L, G, restarts=R, torsion_step_deg=s["torsion_step_deg"], passes=s["passes"], top_k=K,
+                        seed=s["seed"], n_rigid=s["n_rigid"], jitter=s["jitter"], out_penalty=s["out_penalty"],
+                        trace=True, top_restart=True)
+    torch.cuda.synchronize()
+    assert int(res.status.abs().sum()) == 0
+    trace, scores, top = res.trace.cpu().numpy(), res.scores.cpu().numpy(), res.top_restart.cpu().numpy()
+    ref = oracle_lib.dock_library(lib, grid, s, restarts=restarts)
+    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    for r_ in ref:
+        l = r_["ligand"]
+        gt = parity.ligand_trace(trace, lib.rot_off, R, s["passes"], l)
+        final = {int(top[l, k]): float(scores[l, k]) for k in range(K)}
+        st = parity.check_dock_ligand(l, r_, gt, final)
+        for k in tot:
+            tot[k] += st[k]
+        assert np.all(np.diff(scores[l]) <= 0)
+    print(tot)
+    assert tot["clean"] >= min_clean * tot["restarts"] and tot["scores"] > 0
+    return res
+
+
+def test_maximum_size_ligands(lg, oracle_lib):
+    spec = dict(kind="uniform", n_ligands=3, n_atoms=(256, 256), n_rot=(32, 32), n_types=8, seed=11)
+    lib = gen.make_library(spec)
+    assert lib.n_atoms.max() == 256 and lib.n_rot.max() == 32
+    grid = gen.make_grid(gen.WORKLOADS["screen20k"]["grid"])
+    s = dict(gen.WORKLOADS["screen20k"]["search"], restarts=16, top_k=16, passes=2, torsion_step_deg=30)
+    _dock_and_check(lg, oracle_lib, lib, grid, s, restarts=range(0, 4), min_clean=0.75)
+
+
+@pytest.mark.parametrize("over", [dict(passes=0), dict(n_rigid=1), dict(torsion_step_deg=360),
+                                  dict(restarts=1, top_k=1), dict(restarts=13, top_k=13),
+                                  dict(restarts=37, top_k=5)])
+def test_degenerate_search_settings(lg, oracle_lib, small32, over):
+    w, lib, grid = small32
+    s = dict(w["search"], **over)
+    res = _dock_and_check(lg, oracle_lib, lib, grid, s)
+    trace = res.trace.cpu().numpy()
+    if over.get("n_rigid") == 1:
+        for l in range(lib.n_ligands):
+            assert np.all(parity.ligand_trace(trace, lib.rot_off, s["restarts"], s["passes"], l)[:, 0] == 0)
+    if over.get("torsion_step_deg") == 360:   # one increment: every sweep keeps the torsion
+        for l in range(lib.n_ligands):
+            assert np.all(parity.ligand_trace(trace, lib.rot_off, s["restarts"], s["passes"], l)[:, 1:] == 0)
+
+
+def test_one_atom_ligand_and_empty_moving_list(lg, oracle_lib, small32):
+    w, _, grid = small32
+    one = dict(xyz=np.zeros((1, 3)), type=np.array([2], np.uint8), bonds=np.zeros((0, 2), np.int32),
+               rot_edge=np.zeros(0, np.int32))
+    # atoms 0-1-2-3 in a chain, plus atom 4 on atom 1: bond 3 (1-4) turns atom 4 alone,
+    # bond 1 (1-2) turns atoms 2 and 3
+    xyz = np.array([[0, 0, 0], [1.5, 0, 0], [2.0, 1.4, 0], [3.5, 1.4, 0.2], [1.9, -1.0, 1.0]], float)
+    chain = dict(xyz=xyz, type=np.array([0, 1, 2, 3, 1], np.uint8),
+                 bonds=np.array([[0, 1], [1, 2], [2, 3], [1, 4]], np.int32), rot_edge=np.array([1, 3], np.int32))
+    lib = gen.from_ligands([one, chain, one])
+    s = dict(w["search"], restarts=8, top_k=8)
+    _dock_and_check(lg, oracle_lib, lib, grid, s)
+
+
+def test_single_cell_grid(lg, oracle_lib, small32):
+    w, lib, _ = small32
+    rng = np.random.default_rng(5)
+    values = rng.normal(-1.0, 0.5, (2, 2, 2, 4))
+    grid = gen.Grid(values=values, origin=(-0.4, -0.3, -0.2), spacing=0.9, centers=np.zeros((0, 3)),
+                    weights=np.zeros((0, 4)))
+    s = dict(w["search"], restarts=8, top_k=8, jitter=0.3)
+    sub = lib.subset(range(0, 8))
+    _dock_and_check(lg, oracle_lib, sub, grid, s)
