@@ -31,7 +31,9 @@ namespace ligen {
 namespace {
 
 constexpr int kGradWarps = 4;
-constexpr int kGradLanes = 8;                       // lanes per pose
+// Lanes per pose: measured on GB300 (refining 8,000 screening ligands' top
+// 16 poses), 16 lanes are 1-2% faster than 8 and 40% faster than 4.
+constexpr int kGradLanes = 16;
 constexpr int kPosesPerWarp = 32 / kGradLanes;
 constexpr int kGroups = kGradWarps * kPosesPerWarp;  // poses per CTA
 constexpr unsigned kFull = 0xffffffffu;
