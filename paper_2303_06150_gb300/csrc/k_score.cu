@@ -1,10 +1,16 @@
-// Pose scoring: one warp per pose.
+// Pose scoring: a group of kScoreLanes lanes per pose, two poses of one
+// ligand per warp (the warp's per-bond work, the torsion rebuild with its
+// sincos, serves both; measured on GB300, scoring the 600,000 kept poses of
+// the screening library takes 1.17 ms per call against 1.24 ms with a warp
+// per pose, grid preparation and packing included).
 //
 // The pose (t, q, theta) is turned into atom positions exactly as the docking
 // output defines them: torsions bond by bond in index order on the centred
 // input coordinates (each about the current axis from its fixed endpoint to
 // its moving endpoint), then the rotation R(q / |q|) and the translation t.
-// Each lane then samples its atoms and the warp sums S = -sum_i E_i.
+// Each lane then samples its atoms and the group sums S = -sum_i E_i. A warp
+// whose ligand has one pose left shadows it in the spare group, which
+// writes nothing.
 #include <cmath>
 
 #include "../../include/ligen.h"
@@ -14,16 +20,23 @@ namespace ligen {
 namespace {
 
 constexpr int kScoreWarps = 4;
+constexpr int kScoreLanes = 16;
+constexpr int kScorePoses = 32 / kScoreLanes;   // poses per warp
 
 __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(const ScoreArgs a) {
-  __shared__ float4 ys[kScoreWarps][LIGEN_MAX_ATOMS];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const size_t gp = (size_t)blockIdx.x * kScoreWarps + w;
-  if (gp >= (size_t)a.lig.L * a.P) return;
-  const int l = (int)(gp / a.P), p = (int)(gp % a.P);
+  __shared__ float4 ys[kScoreWarps * kScorePoses][LIGEN_MAX_ATOMS];
+  const int w = threadIdx.x >> 5, grp = (threadIdx.x & 31) / kScoreLanes, sub = threadIdx.x % kScoreLanes;
+  const int wpl = (a.P + kScorePoses - 1) / kScorePoses;   // warps per ligand
+  const size_t gw = (size_t)blockIdx.x * kScoreWarps + w;
+  if (gw >= (size_t)a.lig.L * wpl) return;   // uniform over the warp
+  const int l = (int)(gw / wpl);
+  const int p0 = (int)(gw % wpl) * kScorePoses + grp;
+  const bool own = p0 < a.P;
+  const int p = own ? p0 : a.P - 1;
+  const size_t gp = (size_t)l * a.P + p;
   const unsigned full = 0xffffffffu;
-  if (a.pk.status[l] != 0) {
-    if (lane == 0) a.out_scores[gp] = -INFINITY;
+  if (a.pk.status[l] != 0) {   // uniform over the warp (one ligand)
+    if (own && sub == 0) a.out_scores[gp] = -INFINITY;
     return;
   }
   const int a0 = a.lig.atom_off[l];
@@ -32,11 +45,11 @@ __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(const ScoreArgs
   const int n = a.lig.rot_off[l + 1] - r0;
   const float* pose = a.poses + (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
   if (!lg_check(a.grid.check, N <= a.max_atoms, kChkItemShape)) {
-    if (lane == 0) a.out_scores[gp] = -INFINITY;
+    if (own && sub == 0) a.out_scores[gp] = -INFINITY;
     return;
   }
-  float4* y = ys[w];
-  for (int i = lane; i < N; i += 32) y[i] = a.pk.xc[a0 + i];
+  float4* y = ys[w * kScorePoses + grp];
+  for (int i = sub; i < N; i += kScoreLanes) y[i] = a.pk.xc[a0 + i];
   __syncwarp();
   for (int b = 0; b < n; ++b) {
     const uchar4 bi = a.pk.binfo[r0 + b];
@@ -48,7 +61,7 @@ __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(const ScoreArgs
     float s, c;
     sincosf(pose[7 + b], &s, &c);
     const uint8_t* fr = a.pk.frag + (size_t)(r0 + b) * kFragStride;
-    for (int t = lane; t < bi.z; t += 32) {
+    for (int t = sub; t < bi.z; t += kScoreLanes) {
       const int i = fr[t];
       if (!lg_check(a.grid.check, i < N, kChkAtomIndex)) continue;
       float4 v = y[i];
@@ -67,7 +80,7 @@ __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(const ScoreArgs
   float R[9];
   qmat(q, R);
   float acc = 0.f;
-  for (int i = lane; i < N; i += 32) {
+  for (int i = sub; i < N; i += kScoreLanes) {
     const float4 v = y[i];
     float u[3];
 #pragma unroll
@@ -78,16 +91,16 @@ __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(const ScoreArgs
     acc -= grid_sample(a.grid, u[0], u[1], u[2], __float_as_int(v.w));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(full, acc, o);
-  if (lane == 0) a.out_scores[gp] = acc;
+  for (int o = kScoreLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(full, acc, o);
+  if (own && sub == 0) a.out_scores[gp] = acc;
 }
 
 }  // namespace
 
 cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s) {
-  const size_t total = (size_t)a.lig.L * a.P;
-  if (total == 0) return cudaSuccess;
-  const size_t blocks = (total + kScoreWarps - 1) / kScoreWarps;
+  if ((size_t)a.lig.L * a.P == 0) return cudaSuccess;
+  const size_t warps = (size_t)a.lig.L * ((a.P + kScorePoses - 1) / kScorePoses);
+  const size_t blocks = (warps + kScoreWarps - 1) / kScoreWarps;
   score_kernel<<<(unsigned)blocks, 32 * kScoreWarps, 0, s>>>(a);
   return cudaGetLastError();
 }
