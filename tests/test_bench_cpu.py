@@ -6,6 +6,7 @@ import pytest
 
 import gen
 
+
 def test_algorithmic_counts_match_fragment_sums(oracle_lib):
     import bench
     w = gen.scaled("screen20k", 40)
