@@ -14,6 +14,11 @@ Tolerances:
     still on the same trajectory and the comparison goes on; when it chose
     otherwise, the rest of that restart is not compared;
   * fragment masks, axes, buckets, statuses: bit-exact.
+
+The 16-bit grid records hold each cell's corner values rounded to nearest
+(FP16 or BF16) and interpolate them in FP32, so the search over them is the
+oracle's search over a grid whose node values are those rounded values
+(`record_values`); the same tolerances then apply.
 """
 from __future__ import annotations
 
@@ -23,6 +28,32 @@ SCORE_RTOL = 1e-5
 GAP_RTOL = 1e-4
 EPS32 = 2.0 ** -24
 POS_ULPS = 16
+
+
+def record_values(values: np.ndarray, fmt: str) -> np.ndarray:
+    """Node values as a grid record of format `fmt` holds them, in FP64: the
+    FP32 values the caller passes, rounded to nearest-even in IEEE binary16
+    ("f16") or bfloat16 ("bf16", the upper half of the binary32 pattern);
+    "f32" keeps the FP32 values."""
+    v32 = np.ascontiguousarray(values, np.float32)
+    if fmt == "f32":
+        return v32.astype(np.float64)
+    if fmt == "f16":
+        return v32.astype(np.float16).astype(np.float64)
+    if fmt == "bf16":
+        bits = v32.view(np.uint32).astype(np.uint64)
+        upper = (bits + 0x7FFF + ((bits >> 16) & 1)) >> 16
+        return (upper.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+    raise ValueError(fmt)
+
+
+def oracle_grid(oracle_lib, grid, fmt: str = "f32"):
+    """The oracle's grid for a GPU run with records of format `fmt`: the
+    generator's FP64 values for FP32 records (their FP32 rounding is inside
+    the score tolerance), the rounded node values for 16-bit records."""
+    if fmt == "f32":
+        return oracle_lib.OGrid.from_grid(grid)
+    return oracle_lib.OGrid(record_values(grid.values, fmt), grid.origin, grid.spacing)
 
 
 def score_tol(D, Gs):

@@ -1,7 +1,10 @@
 """Full-size screening workload (20,000 ligands, 256 restarts, 10-degree steps,
-3 passes, top 30) in the launch configuration the benchmark times, checked
+3 passes, top 30) in the launch configurations the benchmark times (FP32
+coefficient records, and FP16 corner records, the form it reports), checked
 against the oracle on sampled ligands and restarts, and by properties that
-hold for every output (needs a GPU)."""
+hold for every output (needs a GPU). The FP16 run is compared with the
+oracle on the grid's FP16-rounded node values, the function its records
+interpolate."""
 import numpy as np
 import pytest
 import torch
@@ -28,6 +31,17 @@ def run():
                         out_penalty=s["out_penalty"], trace=True, top_restart=True)
     torch.cuda.synchronize()
     return lg, w, lib, grid, L, G, res
+
+
+@pytest.fixture(scope="module")
+def run16(run):
+    lg, w, lib, grid, L, G, _ = run
+    s = w["search"]
+    res = lg.dock_batch(L, G, restarts=s["restarts"], torsion_step_deg=s["torsion_step_deg"], passes=s["passes"],
+                        top_k=s["top_k"], seed=s["seed"], n_rigid=s["n_rigid"], jitter=s["jitter"],
+                        out_penalty=s["out_penalty"], trace=True, top_restart=True, grid_format="f16")
+    torch.cuda.synchronize()
+    return res
 
 
 def test_every_output_is_well_formed(run):
@@ -117,3 +131,41 @@ def test_full_top_k_matches_oracle_on_two_ligands(run, oracle_lib):
                 compared += 1
     print("ranks compared", compared)
     assert compared > 0
+
+
+def test_fp16_records_match_oracle_on_rounded_grid(run, run16, oracle_lib):
+    lg, w, lib, grid, L, G, _ = run
+    res = run16
+    s = w["search"]
+    R, K = s["restarts"], s["top_k"]
+    assert int(res.status.abs().sum()) == 0
+    sc = res.scores.cpu().numpy()
+    assert np.isfinite(sc).all() and np.all(np.diff(sc, axis=1) <= 0)
+    pick = set(np.linspace(0, lib.n_ligands - 1, 16).astype(int).tolist())
+    pick |= {int(np.argmax(lib.n_atoms)), int(np.argmax(lib.n_rot))}
+    rs = range(0, 24)
+    trace = res.trace.cpu().numpy()
+    top = res.top_restart.cpu().numpy()
+    ref = oracle_lib.dock_library(lib, parity.oracle_grid(oracle_lib, grid, "f16"), s, ligands=sorted(pick),
+                                  restarts=rs)
+    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    for r_ in ref:
+        l = r_["ligand"]
+        gt = parity.ligand_trace(trace, lib.rot_off, R, s["passes"], l)
+        final = {int(top[l, k]): float(sc[l, k]) for k in range(K)}
+        st = parity.check_dock_ligand(l, r_, gt, final)
+        for k in tot:
+            tot[k] += st[k]
+    print(tot)
+    assert tot["restarts"] == len(pick) * len(rs)
+    assert tot["clean"] >= 0.9 * tot["restarts"]
+    # every kept pose's score is the rounded grid's score of that pose
+    og16 = parity.oracle_grid(oracle_lib, grid, "f16")
+    poses = res.poses.cpu().numpy()
+    off = lg.pose_offsets(lib.rot_off, K)
+    for l in sorted(pick):
+        lig = oracle_lib.OLigand.from_library(lib, l)
+        P = poses[off[l]:off[l + 1]].reshape(K, -1).astype(np.float64)
+        for k in range(0, K, 3):
+            S, D, _, Gs = oracle_lib.score_pose(lig, og16, P[k], 5.0, sensitivity=True)
+            assert abs(sc[l, k] - S) <= parity.score_tol(D, Gs), (l, k, sc[l, k], S)

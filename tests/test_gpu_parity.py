@@ -133,19 +133,21 @@ def test_score_poses_within_1e5(lg, oracle_lib, small32, screen_sample, which):
 
 
 # ------------------------------------------------------------ docking ---
-def _dock_and_compare(lg, oracle_lib, w, lib, grid, restarts=None, ligands=None, device="cuda"):
+def _dock_and_compare(lg, oracle_lib, w, lib, grid, restarts=None, ligands=None, device="cuda", fmt="f32"):
     s = dict(w["search"])
     R = s["restarts"]
     Ld, Gd = _dev(lg, lib, grid, device)
     res = lg.dock_batch(Ld, Gd, restarts=R, torsion_step_deg=s["torsion_step_deg"], passes=s["passes"],
-                        top_k=R, seed=s["seed"], n_rigid=s.get("n_rigid", 24), trace=True, top_restart=True)
+                        top_k=R, seed=s["seed"], n_rigid=s.get("n_rigid", 24), trace=True, top_restart=True,
+                        grid_format=fmt)
     if device == "cuda":
         torch.cuda.synchronize()
     trace = res.trace.cpu().numpy()
     scores = res.scores.cpu().numpy()
     top = res.top_restart.cpu().numpy()
     status = res.status.cpu().numpy()
-    ref = oracle_lib.dock_library(lib, grid, s, ligands=ligands, restarts=restarts)
+    ref = oracle_lib.dock_library(lib, parity.oracle_grid(oracle_lib, grid, fmt), s, ligands=ligands,
+                                  restarts=restarts)
     tot = dict(decisions=0, restarts=0, clean=0, scores=0)
     for r_ in ref:
         l = r_["ligand"]
@@ -161,17 +163,21 @@ def _dock_and_compare(lg, oracle_lib, w, lib, grid, restarts=None, ligands=None,
     return res, ref, tot
 
 
-def test_dock_small32_matches_oracle(lg, oracle_lib, small32):
+# 16-bit records are compared with the oracle run on their rounded node
+# values (parity.oracle_grid): same decisions, scores within the FP32 bar.
+@pytest.mark.parametrize("fmt", ["f32", "f16", "bf16"])
+def test_dock_small32_matches_oracle(lg, oracle_lib, small32, fmt):
     w, lib, grid = small32
-    _, _, tot = _dock_and_compare(lg, oracle_lib, w, lib, grid)
+    _, _, tot = _dock_and_compare(lg, oracle_lib, w, lib, grid, fmt=fmt)
     print(tot)
     assert tot["clean"] >= 0.9 * tot["restarts"] and tot["scores"] > 0
 
 
-def test_dock_screen_sample_matches_oracle(lg, oracle_lib, screen_sample):
+@pytest.mark.parametrize("fmt", ["f32", "f16", "bf16"])
+def test_dock_screen_sample_matches_oracle(lg, oracle_lib, screen_sample, fmt):
     w, lib, grid = screen_sample
     _, _, tot = _dock_and_compare(lg, oracle_lib, w, lib, grid, restarts=range(0, 24),
-                                  ligands=range(0, 64, 2))
+                                  ligands=range(0, 64, 2), fmt=fmt)
     print(tot)
     assert tot["clean"] >= 0.9 * tot["restarts"] and tot["scores"] > 0
 
