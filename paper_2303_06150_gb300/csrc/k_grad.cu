@@ -13,13 +13,18 @@
 //
 // Refinement: per pose, `steps` iterations of normalised-step projected
 // ascent (t clamped to the box, q renormalised, theta wrapped); a step is
-// kept when it raises S, otherwise the step sizes are halved.
+// kept when it raises S, otherwise the step sizes are halved. Each iteration
+// evaluates the candidate once, score and gradient together, so a kept step
+// already has the gradient for the next one (measured on GB300, refining
+// 8,000 screening ligands' top 16 poses for 50 steps: 10.1 ms, against 14.1
+// ms with a score-only candidate evaluation followed by a gradient
+// re-evaluation after every kept step).
 //
 // Mapping. The poses of a warp belong to one ligand, so every group runs the
 // same atom and bond loops in lockstep and the per-bond work (the torsion
-// rebuild with its sincos, the group sums) is shared by 32 / kGradLanes
-// poses instead of occupying a whole warp for one pose, whose 32 lanes
-// mostly idle on ligands of a few dozen atoms. A warp whose ligand has fewer
+// rebuild, the group sums) is shared by 32 / kGradLanes poses instead of
+// occupying a whole warp for one pose, whose 32 lanes mostly idle on ligands
+// of a few dozen atoms. A warp whose ligand has fewer
 // poses left than groups shadows the last pose in the spare groups and
 // writes nothing for them.
 #include <cmath>
@@ -52,7 +57,15 @@ struct PoseMem {
   float* g;    // [max_atoms][3] dS/dx
 };
 
-// S of `pose` for ligand l; with `grad` (shared, 7 + n floats) also dS/dpose.
+static_assert(LIGEN_MAX_ROT <= 2 * kGradLanes, "two torsions per lane");
+
+// The record of bond b held by lane b % kGradLanes of this lane's group.
+__device__ __forceinline__ uchar4 bond_of(uchar4 mine, int b) {
+  const unsigned w = __shfl_sync(kFull, *reinterpret_cast<const unsigned*>(&mine), b % kGradLanes, kGradLanes);
+  return *reinterpret_cast<const uchar4*>(&w);
+}
+
+// S of `pose` for ligand l and dS/dpose into `grad` (shared, 7 + n floats).
 // Every lane of the group returns S. Called by all lanes of the warp.
 __device__ float group_score_grad(const GradArgs& a, int l, const float* pose, const PoseMem& W, float* grad) {
   const int sub = threadIdx.x % kGradLanes;
@@ -61,16 +74,30 @@ __device__ float group_score_grad(const GradArgs& a, int l, const float* pose, c
   const int r0 = a.lig.rot_off[l];
   const int n = a.lig.rot_off[l + 1] - r0;
   for (int i = sub; i < N; i += kGradLanes) W.y[i] = a.pk.xc[a0 + i];
+  // Per-bond values of bonds sub and sub + kGradLanes, handed to the bond
+  // loops by shuffles: sin and cos of the torsion (one sincosf per lane
+  // instead of n) and the bond record (no load in the loops' chains)
+  float s_lo = 0.f, c_lo = 1.f, s_hi = 0.f, c_hi = 1.f;
+  uchar4 bi_lo = make_uchar4(0, 0, 0, 0), bi_hi = bi_lo;
+  if (sub < n) {
+    sincosf(pose[7 + sub], &s_lo, &c_lo);
+    bi_lo = a.pk.binfo[r0 + sub];
+  }
+  if (sub + kGradLanes < n) {
+    sincosf(pose[7 + kGradLanes + sub], &s_hi, &c_hi);
+    bi_hi = a.pk.binfo[r0 + kGradLanes + sub];
+  }
   __syncwarp();
-  for (int b = 0; b < n; ++b) {
-    const uchar4 bi = a.pk.binfo[r0 + b];
+  for (int b = 0; b < n; ++b) {   // b is uniform over the warp (one ligand)
+    const bool lo = b < kGradLanes;
+    const float s = __shfl_sync(kFull, lo ? s_lo : s_hi, b % kGradLanes, kGradLanes);
+    const float c = __shfl_sync(kFull, lo ? c_lo : c_hi, b % kGradLanes, kGradLanes);
+    const uchar4 bi = bond_of(lo ? bi_lo : bi_hi, b);
     if (!lg_check(a.grid.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
     const float4 pv = W.y[bi.y], pu = W.y[bi.x];
     float kx = pv.x - pu.x, ky = pv.y - pu.y, kz = pv.z - pu.z;
     const float kn = rsqrtf(kx * kx + ky * ky + kz * kz);
     kx *= kn; ky *= kn; kz *= kn;
-    float s, c;
-    sincosf(pose[7 + b], &s, &c);
     const uint8_t* fr = a.pk.frag + (size_t)(r0 + b) * kFragStride;
     for (int t = sub; t < bi.z; t += kGradLanes) {
       const int i = fr[t];
@@ -88,7 +115,8 @@ __device__ float group_score_grad(const GradArgs& a, int l, const float* pose, c
     __syncwarp();
   }
   const float qn = sqrtf(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
-  const Quat q = {pose[3] / qn, pose[4] / qn, pose[5] / qn, pose[6] / qn};
+  const float rqn = 1.f / qn;
+  const Quat q = {pose[3] * rqn, pose[4] * rqn, pose[5] * rqn, pose[6] * rqn};
   float R[9];
   qmat(q, R);
   // dR/dq^ of the polynomial rotation matrix
@@ -97,7 +125,11 @@ __device__ float group_score_grad(const GradArgs& a, int l, const float* pose, c
       {0.f, 2.f * q.y, 2.f * q.z, 2.f * q.y, -4.f * q.x, -2.f * q.w, 2.f * q.z, 2.f * q.w, -4.f * q.x},
       {-4.f * q.y, 2.f * q.x, 2.f * q.w, 2.f * q.x, 0.f, 2.f * q.z, -2.f * q.w, 2.f * q.z, -4.f * q.y},
       {-4.f * q.z, -2.f * q.w, 2.f * q.x, 2.f * q.w, -4.f * q.z, 2.f * q.y, 2.f * q.x, 2.f * q.y, 0.f}};
-  float S = 0.f, gt[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
+  // dS/dq^_k = sum_i g_i . (dR/dq^_k) y_i = sum_rc (dR/dq^_k)_rc Gy_rc with
+  // Gy = sum_i g_i y_i^T: 9 FMAs per atom, the contraction once per pose
+  float S = 0.f, gt[3] = {0.f, 0.f, 0.f}, Gy[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) Gy[e] = 0.f;
   for (int i = sub; i < N; i += kGradLanes) {
     const float4 v = W.y[i];
     float x[3], u[3];
@@ -105,10 +137,6 @@ __device__ float group_score_grad(const GradArgs& a, int l, const float* pose, c
     for (int r = 0; r < 3; ++r) {
       x[r] = fmaf(R[3 * r], v.x, fmaf(R[3 * r + 1], v.y, fmaf(R[3 * r + 2], v.z, pose[r])));
       u[r] = (x[r] - a.origin[r]) * a.inv_h;
-    }
-    if (!grad) {
-      S -= grid_sample(a.grid, u[0], u[1], u[2], __float_as_int(v.w));
-      continue;
     }
     float gx, gy, gz;
     S -= grid_sample_grad(a.grid, u[0], u[1], u[2], __float_as_int(v.w), &gx, &gy, &gz);
@@ -118,28 +146,33 @@ __device__ float group_score_grad(const GradArgs& a, int l, const float* pose, c
       gt[r] += gi[r];
       W.x[3 * i + r] = x[r];
       W.g[3 * i + r] = gi[r];
+      Gy[3 * r] = fmaf(gi[r], v.x, Gy[3 * r]);
+      Gy[3 * r + 1] = fmaf(gi[r], v.y, Gy[3 * r + 1]);
+      Gy[3 * r + 2] = fmaf(gi[r], v.z, Gy[3 * r + 2]);
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-        dq[k] += gi[r] * fmaf(dR[k][3 * r], v.x, fmaf(dR[k][3 * r + 1], v.y, dR[k][3 * r + 2] * v.z));
   }
   S = group_sum(S);
-  if (!grad) return S;
 #pragma unroll
   for (int r = 0; r < 3; ++r) gt[r] = group_sum(gt[r]);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) dq[k] = group_sum(dq[k]);
+  for (int e = 0; e < 9; ++e) Gy[e] = group_sum(Gy[e]);
+  float dq[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float acc = 0.f;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) acc = fmaf(dR[k][e], Gy[e], acc);
+    dq[k] = acc;
+  }
   __syncwarp();
   if (sub == 0) {
     const float proj = q.w * dq[0] + q.x * dq[1] + q.y * dq[2] + q.z * dq[3];
     const float qh[4] = {q.w, q.x, q.y, q.z};
     for (int r = 0; r < 3; ++r) grad[r] = gt[r];
-    for (int k = 0; k < 4; ++k) grad[3 + k] = (dq[k] - qh[k] * proj) / qn;
+    for (int k = 0; k < 4; ++k) grad[3 + k] = (dq[k] - qh[k] * proj) * rqn;
   }
   for (int b = 0; b < n; ++b) {
-    const uchar4 bi = a.pk.binfo[r0 + b];
+    const uchar4 bi = bond_of(b < kGradLanes ? bi_lo : bi_hi, b);
     if (!lg_check(a.grid.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
     const float* xv = W.x + 3 * bi.y;
     const float* xu = W.x + 3 * bi.x;
@@ -229,9 +262,12 @@ __global__ void __launch_bounds__(32 * kGradWarps) grad_kernel(const GradArgs a)
   }
 }
 
-__global__ void __launch_bounds__(32 * kGradWarps) refine_kernel(const GradArgs a) {
+// Six resident CTAs (at most 80 registers; a few bytes spill): measured on
+// GB300, 4% faster than the unconstrained 96 registers (five CTAs) and 7%
+// faster than eight CTAs at 64 registers.
+__global__ void __launch_bounds__(32 * kGradWarps, 6) refine_kernel(const GradArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ float gbuf[kGroups][7 + LIGEN_MAX_ROT];
+  __shared__ float gbuf[2][kGroups][7 + LIGEN_MAX_ROT];
   __shared__ float pbuf[kGroups][7 + LIGEN_MAX_ROT];
   __shared__ float cbuf[kGroups][7 + LIGEN_MAX_ROT];
   const Slot sl = slot_of(a);
@@ -251,7 +287,8 @@ __global__ void __launch_bounds__(32 * kGradWarps) refine_kernel(const GradArgs 
   const PoseMem W = pose_mem(smem, a.max_atoms, sl.slot);
   float* pose = pbuf[sl.slot];
   float* cand = cbuf[sl.slot];
-  float* grad = gbuf[sl.slot];
+  float* grad = gbuf[0][sl.slot];     // gradient at `pose`
+  float* grad_c = gbuf[1][sl.slot];   // gradient at the candidate
   for (int e = sub; e < plen; e += kGradLanes) pose[e] = pose_g[e];
   __syncwarp();
   float S = group_score_grad(a, l, pose, W, grad);
@@ -265,44 +302,57 @@ __global__ void __launch_bounds__(32 * kGradWarps) refine_kernel(const GradArgs 
     nt = sqrtf(group_sum(nt));
     nq = sqrtf(group_sum(nq));
     nth = sqrtf(group_sum(nth));
-    const float qn = sqrtf(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
+    // step sizes over gradient norms: one division each, then products
+    const float kt = nt > 0.f ? st / nt : 0.f;
+    const float kq = nq > 0.f ? sq / nq : 0.f;
+    const float kth = nth > 0.f ? sth / nth : 0.f;
+    const float rqn = 1.f / sqrtf(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
     float qq[4], qm = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      qq[k] = pose[3 + k] / qn + (nq > 0.f ? sq * grad[3 + k] / nq : 0.f);
+      qq[k] = fmaf(kq, grad[3 + k], pose[3 + k] * rqn);
       qm += qq[k] * qq[k];
     }
-    qm = sqrtf(qm);
+    const float rqm = 1.f / sqrtf(qm);
     for (int e = sub; e < plen; e += kGradLanes) {
       float v;
       if (e < 3) {
-        v = pose[e] + (nt > 0.f ? st * grad[e] / nt : 0.f);
+        v = fmaf(kt, grad[e], pose[e]);
         v = fminf(fmaxf(v, a.box_lo[e]), a.box_hi[e]);
       } else if (e < 7) {
-        v = qq[e - 3] / qm;
+        v = qq[e - 3] * rqm;
       } else {
-        v = pose[e] + (nth > 0.f ? sth * grad[e] / nth : 0.f);
-        v = fmodf(v + kPiF, 2.f * kPiF);
-        if (v < 0.f) v += 2.f * kPiF;
-        v -= kPiF;
+        // wrap to [-pi, pi): a step from a wrapped angle needs at most one
+        // turn (w - 2 pi is exact there, as fmodf would give); other
+        // inputs take the general reduction
+        const float w0 = fmaf(kth, grad[e], pose[e]) + kPiF;
+        float w = w0;
+        if (w >= 2.f * kPiF) w -= 2.f * kPiF;
+        else if (w < 0.f) w += 2.f * kPiF;
+        if (!(w >= 0.f && w < 2.f * kPiF)) {
+          w = fmodf(w0, 2.f * kPiF);
+          if (w < 0.f) w += 2.f * kPiF;
+        }
+        v = w - kPiF;
       }
       cand[e] = v;
     }
     __syncwarp();
-    const float S2 = group_score_grad(a, l, cand, W, nullptr);
+    // The candidate is evaluated with its gradient: a kept step then needs
+    // no second evaluation (the buffers swap), a rejected one drops it.
+    const float S2 = group_score_grad(a, l, cand, W, grad_c);
     const bool take = S2 > S;   // identical in every lane of the group (group sums)
     if (sl.own && a.out_accept && sub == 0) a.out_accept[gp * a.steps + s] = take ? 1 : 0;
     if (take) {
       for (int e = sub; e < plen; e += kGradLanes) pose[e] = cand[e];
+      S = S2;
+      float* t = grad;
+      grad = grad_c;
+      grad_c = t;
     } else {
       st *= 0.5f; sq *= 0.5f; sth *= 0.5f;
     }
     __syncwarp();
-    // A group that moved needs the gradient at its new pose. The evaluation
-    // is warp-wide, so when any group moved every group re-evaluates at its
-    // current pose: for the others that is the pose they already had, and
-    // the same arithmetic gives the same S and gradient.
-    if (__any_sync(kFull, take)) S = group_score_grad(a, l, pose, W, grad);
   }
   if (sl.own) {
     const float sgn = pose[3] < 0.f ? -1.f : 1.f;
