@@ -59,7 +59,7 @@ struct PoseMem {
 
 static_assert(LIGEN_MAX_ROT <= 2 * kGradLanes, "two torsions per lane");
 
-// The record of bond b held by lane b % kGradLanes of this lane's group.
+// The record of bond b, held by lane b % kGradLanes of this lane's group.
 __device__ __forceinline__ uchar4 bond_of(uchar4 mine, int b) {
   const unsigned w = __shfl_sync(kFull, *reinterpret_cast<const unsigned*>(&mine), b % kGradLanes, kGradLanes);
   return *reinterpret_cast<const uchar4*>(&w);

@@ -20,20 +20,26 @@ __global__ void grid_prep_kernel(const float* __restrict__ v, int nx, int ny, in
     cell /= cx;
     const int iy = (int)(cell % cy);
     const int iz = (int)(cell / cy);
-    auto at = [&](int dx, int dy, int dz) -> double {
-      return (double)v[(((size_t)(iz + dz) * ny + (iy + dy)) * nx + (ix + dx)) * nc + c];
+    auto at = [&](int dx, int dy, int dz) -> float {
+      return v[(((size_t)(iz + dz) * ny + (iy + dy)) * nx + (ix + dx)) * nc + c];
     };
-    const double c000 = at(0, 0, 0), c100 = at(1, 0, 0), c010 = at(0, 1, 0), c110 = at(1, 1, 0);
-    const double c001 = at(0, 0, 1), c101 = at(1, 0, 1), c011 = at(0, 1, 1), c111 = at(1, 1, 1);
+    const float c000 = at(0, 0, 0), c100 = at(1, 0, 0), c010 = at(0, 1, 0), c110 = at(1, 1, 0);
+    const float c001 = at(0, 0, 1), c101 = at(1, 0, 1), c011 = at(0, 1, 1), c111 = at(1, 1, 1);
+    // FP32 differences of differences: each coefficient takes at most three
+    // roundings at the grid values' magnitude. (The same sums in FP64 ran on
+    // the chip's narrow FP64 pipe: 0.37 ms for a 96^3 x 8 grid against
+    // 0.07 ms, measured on GB300.)
+    const float dx00 = c100 - c000, dx10 = c110 - c010, dx01 = c101 - c001, dx11 = c111 - c011;
+    const float axy = dx10 - dx00, axz = dx01 - dx00;
     float4 lo, hi;
-    lo.x = (float)c000;                                   // a0
-    lo.y = (float)(c100 - c000);                          // ax
-    lo.z = (float)(c010 - c000);                          // ay
-    lo.w = (float)(c001 - c000);                          // az
-    hi.x = (float)(c110 - c100 - c010 + c000);            // axy
-    hi.y = (float)(c101 - c100 - c001 + c000);            // axz
-    hi.z = (float)(c011 - c010 - c001 + c000);            // ayz
-    hi.w = (float)(c111 - c110 - c101 - c011 + c100 + c010 + c001 - c000);  // axyz
+    lo.x = c000;                       // a0
+    lo.y = dx00;                       // ax
+    lo.z = c010 - c000;                // ay
+    lo.w = c001 - c000;                // az
+    hi.x = axy;                        // axy
+    hi.y = axz;                        // axz
+    hi.z = (c011 - c001) - lo.z;       // ayz
+    hi.w = (dx11 - dx01) - axy;        // axyz
     float4* rec = reinterpret_cast<float4*>(coef + rec_index(cx, cy, cz, c, ix, iy, iz) * 8);
     rec[0] = lo;
     rec[1] = hi;
