@@ -67,7 +67,6 @@ int space_of(std::initializer_list<const void*> ptrs) {
   return s == -2 ? 0 : s;
 }
 
-void forget_orders(int dev);   // cached ligand orders live in workspaces
 
 // ------------------------------------------------------------ workspace --
 struct Workspace {
@@ -105,7 +104,6 @@ int get_workspace(cudaStream_t s, size_t bytes, char** out) {
   if (w.cap < bytes) {
     if (w.base) {
       LG_CUDA(cudaStreamSynchronize(s));
-      forget_orders(dev);
       cudaFree(w.base);
       w.base = nullptr;
       w.cap = 0;
@@ -428,33 +426,6 @@ void plan_groups(const ligen_ligands_t* g, const ligen_params_t* p, int dev, std
   std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.cost > b.cost; });
 }
 
-// The ligand order last uploaded to each workspace region, so that docking
-// the same library again (the usual case: one library, many batches or
-// sites) skips the upload.
-std::mutex g_order_mu;
-std::map<std::tuple<int, cudaStream_t, const void*>, std::vector<int32_t>> g_order;
-
-bool order_is_current(cudaStream_t s, const void* d_order, const std::vector<int32_t>& order) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lk(g_order_mu);
-  auto it = g_order.find(std::make_tuple(dev, s, d_order));
-  return it != g_order.end() && it->second == order;
-}
-
-void remember_order(cudaStream_t s, const void* d_order, const std::vector<int32_t>& order) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lk(g_order_mu);
-  g_order[std::make_tuple(dev, s, d_order)] = order;
-}
-
-void forget_orders(int dev) {
-  std::lock_guard<std::mutex> lk(g_order_mu);
-  for (auto it = g_order.begin(); it != g_order.end();)
-    it = (std::get<0>(it->first) == dev) ? g_order.erase(it) : std::next(it);
-}
-
 // Side streams and events for the forked launches, per device.
 struct Fork {
   std::vector<cudaStream_t> streams;
@@ -632,7 +603,6 @@ int ligen_release_workspaces(void) {
       }
     }
   }
-  forget_orders(dev);
   std::lock_guard<std::mutex> lk(g_ws_mu);
   for (auto it = g_ws.begin(); it != g_ws.end();) {
     if (it->first.first == dev) {
@@ -823,12 +793,12 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     if (exhaustive) {
       LG_CUDA(launch_exhaustive(da, s));
     } else if (buckets) {
+      // Uploaded on every call: any other call on this stream may have
+      // carved the workspace differently and overwritten this region (a
+      // grid of another record format, for one). Pageable source: the copy
+      // is staged before cudaMemcpyAsync returns.
       int32_t* d_order = ar.at<int32_t>(o_order);
-      if (!order_is_current(s, d_order, order)) {
-        // pageable source: the copy is staged before the call returns
-        LG_CUDA(cudaMemcpyAsync(d_order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, s));
-        remember_order(s, d_order, order);
-      }
+      LG_CUDA(cudaMemcpyAsync(d_order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, s));
       if ((rc = run_bucketed(da, groups, d_order, ar.at<int>(o_queue),
                              params->batching == LIGEN_BATCH_BUCKETS, s)) != LIGEN_OK)
         return rc;
@@ -1312,7 +1282,6 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   chk.plan(ar);
   if ((rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
   if ((rc = chk.arm(ar, s)) != LIGEN_OK) return rc;
-  forget_orders(dev);   // the order region is overwritten below
 
   LigandsDev lig;
   lig.L = L;

@@ -47,10 +47,11 @@ def _same_decisions_close_scores(a, b):
     assert np.all(np.abs(sa - sb) <= 1e-5 * np.maximum(np.abs(sa), 1.0))
 
 
-def test_buckets_match_plain_and_replay(lg, bimodal):
+@pytest.mark.parametrize("fmt", ["f32", "f16"])
+def test_buckets_match_plain_and_replay(lg, bimodal, fmt):
     w, lib, grid = bimodal
     L, G = _dev(lg, lib, grid)
-    kw = _kw(w["search"], trace=True, top_restart=True)
+    kw = _kw(w["search"], trace=True, top_restart=True, grid_format=fmt)
     plain = lg.dock_batch(L, G, batching="plain", **kw)
     b1 = lg.dock_batch(L, G, batching="buckets", **kw)
     b2 = lg.dock_batch(L, G, batching="buckets", **kw)     # graph replay
@@ -60,10 +61,11 @@ def test_buckets_match_plain_and_replay(lg, bimodal):
     assert torch.equal(b1.trace, b2.trace)
 
 
-def test_static_bucket_launches_match_plain(lg, bimodal, small32):
+@pytest.mark.parametrize("fmt", ["f32", "f16"])
+def test_static_bucket_launches_match_plain(lg, bimodal, small32, fmt):
     for w, lib, grid in (bimodal, small32):
         L, G = _dev(lg, lib, grid)
-        kw = _kw(w["search"], trace=True, top_restart=True)
+        kw = _kw(w["search"], trace=True, top_restart=True, grid_format=fmt)
         plain = lg.dock_batch(L, G, batching="plain", **kw)
         st1 = lg.dock_batch(L, G, batching="buckets_static", **kw)
         st2 = lg.dock_batch(L, G, batching="buckets_static", **kw)     # graph replay
