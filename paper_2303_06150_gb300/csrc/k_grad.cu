@@ -31,6 +31,7 @@
 
 #include "../../include/ligen.h"
 #include "internal.h"
+#include "pose_build.cuh"
 
 namespace ligen {
 namespace {
@@ -57,14 +58,6 @@ struct PoseMem {
   float* g;    // [max_atoms][3] dS/dx
 };
 
-static_assert(LIGEN_MAX_ROT <= 2 * kGradLanes, "two torsions per lane");
-
-// The record of bond b, held by lane b % kGradLanes of this lane's group.
-__device__ __forceinline__ uchar4 bond_of(uchar4 mine, int b) {
-  const unsigned w = __shfl_sync(kFull, *reinterpret_cast<const unsigned*>(&mine), b % kGradLanes, kGradLanes);
-  return *reinterpret_cast<const uchar4*>(&w);
-}
-
 // S of `pose` for ligand l and dS/dpose into `grad` (shared, 7 + n floats).
 // Every lane of the group returns S. Called by all lanes of the warp.
 __device__ float group_score_grad(const GradArgs& a, int l, const float* pose, const PoseMem& W, float* grad) {
@@ -74,46 +67,10 @@ __device__ float group_score_grad(const GradArgs& a, int l, const float* pose, c
   const int r0 = a.lig.rot_off[l];
   const int n = a.lig.rot_off[l + 1] - r0;
   for (int i = sub; i < N; i += kGradLanes) W.y[i] = a.pk.xc[a0 + i];
-  // Per-bond values of bonds sub and sub + kGradLanes, handed to the bond
-  // loops by shuffles: sin and cos of the torsion (one sincosf per lane
-  // instead of n) and the bond record (no load in the loops' chains)
-  float s_lo = 0.f, c_lo = 1.f, s_hi = 0.f, c_hi = 1.f;
-  uchar4 bi_lo = make_uchar4(0, 0, 0, 0), bi_hi = bi_lo;
-  if (sub < n) {
-    sincosf(pose[7 + sub], &s_lo, &c_lo);
-    bi_lo = a.pk.binfo[r0 + sub];
-  }
-  if (sub + kGradLanes < n) {
-    sincosf(pose[7 + kGradLanes + sub], &s_hi, &c_hi);
-    bi_hi = a.pk.binfo[r0 + kGradLanes + sub];
-  }
+  GroupBonds<kGradLanes> bonds;   // also read by the torsion-gradient loop below
+  bonds.load(a.pk, r0, n, pose + 7, sub);
   __syncwarp();
-  for (int b = 0; b < n; ++b) {   // b is uniform over the warp (one ligand)
-    const bool lo = b < kGradLanes;
-    const float s = __shfl_sync(kFull, lo ? s_lo : s_hi, b % kGradLanes, kGradLanes);
-    const float c = __shfl_sync(kFull, lo ? c_lo : c_hi, b % kGradLanes, kGradLanes);
-    const uchar4 bi = bond_of(lo ? bi_lo : bi_hi, b);
-    if (!lg_check(a.grid.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
-    const float4 pv = W.y[bi.y], pu = W.y[bi.x];
-    float kx = pv.x - pu.x, ky = pv.y - pu.y, kz = pv.z - pu.z;
-    const float kn = rsqrtf(kx * kx + ky * ky + kz * kz);
-    kx *= kn; ky *= kn; kz *= kn;
-    const uint8_t* fr = a.pk.frag + (size_t)(r0 + b) * kFragStride;
-    for (int t = sub; t < bi.z; t += kGradLanes) {
-      const int i = fr[t];
-      if (!lg_check(a.grid.check, i < N, kChkAtomIndex)) continue;
-      float4 v = W.y[i];
-      const float dx = v.x - pv.x, dy = v.y - pv.y, dz = v.z - pv.z;
-      const float kd = kx * dx + ky * dy + kz * dz;
-      const float ex = dx - kx * kd, ey = dy - ky * kd, ez = dz - kz * kd;
-      const float qx = ky * dz - kz * dy, qy = kz * dx - kx * dz, qz = kx * dy - ky * dx;
-      v.x = pv.x + kx * kd + ex * c + qx * s;
-      v.y = pv.y + ky * kd + ey * c + qy * s;
-      v.z = pv.z + kz * kd + ez * c + qz * s;
-      W.y[i] = v;
-    }
-    __syncwarp();
-  }
+  group_torsions<kGradLanes>(a.pk, r0, n, N, bonds, W.y, a.grid.check, sub);
   const float qn = sqrtf(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
   const float rqn = 1.f / qn;
   const Quat q = {pose[3] * rqn, pose[4] * rqn, pose[5] * rqn, pose[6] * rqn};
@@ -172,7 +129,7 @@ __device__ float group_score_grad(const GradArgs& a, int l, const float* pose, c
     for (int k = 0; k < 4; ++k) grad[3 + k] = (dq[k] - qh[k] * proj) * rqn;
   }
   for (int b = 0; b < n; ++b) {
-    const uchar4 bi = bond_of(b < kGradLanes ? bi_lo : bi_hi, b);
+    const uchar4 bi = bonds.bond(b);
     if (!lg_check(a.grid.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
     const float* xv = W.x + 3 * bi.y;
     const float* xu = W.x + 3 * bi.x;

@@ -16,6 +16,7 @@
 
 #include "../../include/ligen.h"
 #include "internal.h"
+#include "pose_build.cuh"
 
 namespace ligen {
 namespace {
@@ -23,13 +24,6 @@ namespace {
 constexpr int kScoreWarps = 4;
 constexpr int kScoreLanes = 16;
 constexpr int kScorePoses = 32 / kScoreLanes;   // poses per warp
-static_assert(LIGEN_MAX_ROT <= 2 * kScoreLanes, "two torsions per lane");
-
-// The record of bond b, held by lane b % kScoreLanes of this lane's group.
-__device__ __forceinline__ uchar4 bond_of(uchar4 mine, int b) {
-  const unsigned w = __shfl_sync(0xffffffffu, *reinterpret_cast<const unsigned*>(&mine), b % kScoreLanes, kScoreLanes);
-  return *reinterpret_cast<const uchar4*>(&w);
-}
 
 __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(const ScoreArgs a) {
   __shared__ float4 ys[kScoreWarps * kScorePoses][LIGEN_MAX_ATOMS];
@@ -58,45 +52,10 @@ __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(const ScoreArgs
   }
   float4* y = ys[w * kScorePoses + grp];
   for (int i = sub; i < N; i += kScoreLanes) y[i] = a.pk.xc[a0 + i];
-  // sin and cos of torsions sub and sub + kScoreLanes and their bond records,
-  // handed to the rebuild by shuffles (one sincosf per lane instead of n)
-  float s_lo = 0.f, c_lo = 1.f, s_hi = 0.f, c_hi = 1.f;
-  uchar4 bi_lo = make_uchar4(0, 0, 0, 0), bi_hi = bi_lo;
-  if (sub < n) {
-    sincosf(pose[7 + sub], &s_lo, &c_lo);
-    bi_lo = a.pk.binfo[r0 + sub];
-  }
-  if (sub + kScoreLanes < n) {
-    sincosf(pose[7 + kScoreLanes + sub], &s_hi, &c_hi);
-    bi_hi = a.pk.binfo[r0 + kScoreLanes + sub];
-  }
+  GroupBonds<kScoreLanes> bonds;
+  bonds.load(a.pk, r0, n, pose + 7, sub);
   __syncwarp();
-  for (int b = 0; b < n; ++b) {   // b is uniform over the warp (one ligand)
-    const bool lo = b < kScoreLanes;
-    const float s = __shfl_sync(full, lo ? s_lo : s_hi, b % kScoreLanes, kScoreLanes);
-    const float c = __shfl_sync(full, lo ? c_lo : c_hi, b % kScoreLanes, kScoreLanes);
-    const uchar4 bi = bond_of(lo ? bi_lo : bi_hi, b);
-    if (!lg_check(a.grid.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
-    const float4 pv = y[bi.y], pu = y[bi.x];
-    float kx = pv.x - pu.x, ky = pv.y - pu.y, kz = pv.z - pu.z;
-    const float kn = rsqrtf(kx * kx + ky * ky + kz * kz);
-    kx *= kn; ky *= kn; kz *= kn;
-    const uint8_t* fr = a.pk.frag + (size_t)(r0 + b) * kFragStride;
-    for (int t = sub; t < bi.z; t += kScoreLanes) {
-      const int i = fr[t];
-      if (!lg_check(a.grid.check, i < N, kChkAtomIndex)) continue;
-      float4 v = y[i];
-      const float dx = v.x - pv.x, dy = v.y - pv.y, dz = v.z - pv.z;
-      const float kd = kx * dx + ky * dy + kz * dz;
-      const float ex = dx - kx * kd, ey = dy - ky * kd, ez = dz - kz * kd;
-      const float qx = ky * dz - kz * dy, qy = kz * dx - kx * dz, qz = kx * dy - ky * dx;
-      v.x = pv.x + kx * kd + ex * c + qx * s;
-      v.y = pv.y + ky * kd + ey * c + qy * s;
-      v.z = pv.z + kz * kd + ez * c + qz * s;
-      y[i] = v;
-    }
-    __syncwarp();
-  }
+  group_torsions<kScoreLanes>(a.pk, r0, n, N, bonds, y, a.grid.check, sub);
   const Quat q = qnormalize({pose[3], pose[4], pose[5], pose[6]});
   float R[9];
   qmat(q, R);
