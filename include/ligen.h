@@ -290,11 +290,11 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                       int32_t poses_per_ligand, const float* poses, float out_penalty,
                       float* out_scores, void* stream);
 
-/* Gradient of the pose score (task text: differentiation of the score with
- * respect to translation, rotation and torsions). For pose p of ligand l
- * (packing as ligen_score_poses), out_scores[l][p] = S and out_grads holds
- * dS/dpose in the pose's own slot: dS/dt[3], dS/dq[4] (through q/|q|, so
- * orthogonal to q), dS/dtheta[n_l]. E is differentiated inside the cell that
+/* Gradient of the pose score with respect to translation, rotation and
+ * torsions (the differentiable form of the score; no paper counterpart).
+ * For pose p of ligand l (packing as ligen_score_poses), out_scores[l][p] =
+ * S and out_grads holds dS/dpose in the pose's own slot: dS/dt[3], dS/dq[4]
+ * (through q/|q|, so orthogonal to q), dS/dtheta[n_l]. E is differentiated inside the cell that
  * holds the atom (one-sided at cell faces); atoms outside the box contribute
  * no gradient. Atom coordinates are rebuilt from the pose, never stored.
  * Invalid ligands: S = -INFINITY, zero gradient. `poses`, `out_scores` and

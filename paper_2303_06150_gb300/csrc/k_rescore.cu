@@ -1,6 +1,6 @@
-// FP64 re-score of kept poses and re-ranking (task text: FP64 on the GPU only
-// for the final re-score of the kept top-K, where near-ties decide the
-// ranking).
+// FP64 re-score of kept poses and re-ranking: FP64 arithmetic on the GPU is
+// spent only on the K kept poses of each ligand, where near-ties between
+// FP32 scores decide the ranking.
 //
 // Everything is recomputed in FP64 from the caller's FP32 inputs: the input
 // centroid, the torsions (bond by bond, about the current axes), the

@@ -6,8 +6,8 @@
 * FP16 / BF16 records: relative score error of every kept pose against the
   oracle's FP64 score of that pose (error / D) and best-pose agreement: the
   form's best pose scores, in the oracle, within 1e-3 * D of the best final
-  score of the oracle's own search. The task's bar is <= 1e-3 relative error
-  and >= 99% agreement."""
+  score of the oracle's own search. The bar for a precision form is <= 1e-3
+  relative error and >= 99% agreement."""
 import numpy as np
 import pytest
 import torch
