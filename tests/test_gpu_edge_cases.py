@@ -4,7 +4,9 @@ Maximum ligand size (256 atoms, 32 rotatable bonds), degenerate search
 settings (no sweep pass, one rigid rotation, a 360-degree step, one restart,
 restart counts that leave a partial chunk), a one-atom ligand, a rotatable
 bond whose moving side is a single atom (an empty moving list), and a grid
-of a single cell that most atoms fall outside of."""
+of a single cell that most atoms fall outside of; the maximum sizes and the
+single-cell grid also with 16-bit grid records (against the oracle on the
+rounded node values)."""
 import numpy as np
 import pytest
 import torch
@@ -23,17 +25,17 @@ def lg():
     return lg
 
 
-def _dock_and_check(lg, oracle_lib, lib, grid, s, restarts=None, min_clean=0.9):
+def _dock_and_check(lg, oracle_lib, lib, grid, s, restarts=None, min_clean=0.9, fmt="f32"):
     L = lg.Ligands.from_arrays(lib, "cuda")
     G = lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, "cuda")
     R, K = s["restarts"], s["top_k"]
     res = lg.dock_batch(L, G, restarts=R, torsion_step_deg=s["torsion_step_deg"], passes=s["passes"], top_k=K,
                         seed=s["seed"], n_rigid=s["n_rigid"], jitter=s["jitter"], out_penalty=s["out_penalty"],
-                        trace=True, top_restart=True)
+                        trace=True, top_restart=True, grid_format=fmt)
     torch.cuda.synchronize()
     assert int(res.status.abs().sum()) == 0
     trace, scores, top = res.trace.cpu().numpy(), res.scores.cpu().numpy(), res.top_restart.cpu().numpy()
-    ref = oracle_lib.dock_library(lib, grid, s, restarts=restarts)
+    ref = oracle_lib.dock_library(lib, parity.oracle_grid(oracle_lib, grid, fmt), s, restarts=restarts)
     tot = dict(decisions=0, restarts=0, clean=0, scores=0)
     for r_ in ref:
         l = r_["ligand"]
@@ -48,13 +50,14 @@ def _dock_and_check(lg, oracle_lib, lib, grid, s, restarts=None, min_clean=0.9):
     return res
 
 
-def test_maximum_size_ligands(lg, oracle_lib):
+@pytest.mark.parametrize("fmt", ["f32", "f16"])
+def test_maximum_size_ligands(lg, oracle_lib, fmt):
     spec = dict(kind="uniform", n_ligands=3, n_atoms=(256, 256), n_rot=(32, 32), n_types=8, seed=11)
     lib = gen.make_library(spec)
     assert lib.n_atoms.max() == 256 and lib.n_rot.max() == 32
     grid = gen.make_grid(gen.WORKLOADS["screen20k"]["grid"])
     s = dict(gen.WORKLOADS["screen20k"]["search"], restarts=16, top_k=16, passes=2, torsion_step_deg=30)
-    _dock_and_check(lg, oracle_lib, lib, grid, s, restarts=range(0, 4), min_clean=0.75)
+    _dock_and_check(lg, oracle_lib, lib, grid, s, restarts=range(0, 4), min_clean=0.75, fmt=fmt)
 
 
 @pytest.mark.parametrize("over", [dict(passes=0), dict(n_rigid=1), dict(torsion_step_deg=360),
@@ -87,7 +90,8 @@ def test_one_atom_ligand_and_empty_moving_list(lg, oracle_lib, small32):
     _dock_and_check(lg, oracle_lib, lib, grid, s)
 
 
-def test_single_cell_grid(lg, oracle_lib, small32):
+@pytest.mark.parametrize("fmt", ["f32", "f16", "bf16"])
+def test_single_cell_grid(lg, oracle_lib, small32, fmt):
     w, lib, _ = small32
     rng = np.random.default_rng(5)
     values = rng.normal(-1.0, 0.5, (2, 2, 2, 4))
@@ -95,4 +99,4 @@ def test_single_cell_grid(lg, oracle_lib, small32):
                     weights=np.zeros((0, 4)))
     s = dict(w["search"], restarts=8, top_k=8, jitter=0.3)
     sub = lib.subset(range(0, 8))
-    _dock_and_check(lg, oracle_lib, sub, grid, s)
+    _dock_and_check(lg, oracle_lib, sub, grid, s, fmt=fmt)
