@@ -196,13 +196,18 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
   for (int s = 0; s < SLOTS; ++s) torsion_cs(slot_j(sub + G * s, G * s, a.n_theta), a.step_deg, &cs[s], &sn[s]);
 
   // Clean bonds. A bond's decision reads only the positions of its moving
-  // atoms and of its axis ends. Once its sweep kept the torsion (j = 0) and
-  // no later turn moved one of those atoms (the packer's touch masks), a new
-  // sweep would repeat it exactly and keep again: the bond is clean and its
-  // decision is 0 without sampling. A clean restart in a warp that sweeps
-  // samples nothing for that bond; a bond clean for the whole warp is
-  // skipped, and so is the rest of the sweep once every bond of every
-  // restart of the warp is clean. Results are unchanged.
+  // atoms and of its axis ends, and its sweep scores the whole circle of
+  // increments. After a sweep, the bond sits at the best increment of that
+  // circle: kept (j = 0) or turned to j*, which moves none of the axis ends.
+  // Until a later turn moves one of the atoms it reads (the packer's touch
+  // masks), a new sweep would score the same circle from its maximum, so
+  // the bond is clean and its decision is 0 without sampling. After a kept
+  // torsion the new sweep would repeat the last one exactly; after a turn it
+  // scores rotated copies of the same positions, equal in exact arithmetic,
+  // so only a near-tie, where either choice is valid, could go another way
+  // in floating point. A clean restart in a warp that sweeps samples nothing
+  // for that bond; a bond clean for the whole warp is skipped, and so is the
+  // rest of the sweep once every bond of every restart of the warp is clean.
   uint32_t dirty = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);   // bonds that must be swept
   long long needed = COUNT ? (long long)a.n_rigid * N : 0;   // samples this restart needs
   for (int p = 0; p < a.passes; ++p) {
@@ -313,7 +318,8 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
         S.scnt[b * rpc + rr] = (uint8_t)((S.scnt[b * rpc + rr] + jb) % nt);
         if (trace) trace[1 + p * n + b] = (int16_t)jb;
       }
-      dirty = (jb != 0) ? (dirty | S.stouch[b]) : (dirty & ~(1u << b));
+      // a turn dirties the bonds it touches; the bond itself is clean either way
+      dirty = ((jb != 0) ? (dirty | S.stouch[b]) : dirty) & ~(1u << b);
     }
   }
 

@@ -386,8 +386,8 @@ def test_sample_count_follows_the_clean_bond_rule(lg, small32, screen_sample):
     """The kernel's count of needed samples equals the count replayed from
     its own decisions: per restart n_rigid * N, plus (n_theta - 1) * (moving
     atoms - 1) for each decision of a bond that was not clean. A bond is
-    clean after a sweep that kept its torsion, until a turn of a bond whose
-    touch mask names it."""
+    clean after its own sweep (kept or turned), until a turn of another bond
+    whose touch mask names it."""
     for w, lib, grid in (small32, screen_sample):
         s = dict(w["search"], restarts=16, top_k=4)
         L = lg.Ligands.from_arrays(lib, "cuda")
@@ -414,5 +414,5 @@ def test_sample_count_follows_the_clean_bond_rule(lg, small32, screen_sample):
                         want += (nt - 1) * (int(moving[r0 + b]) - 1)
                     else:
                         assert jb == 0
-                    dirty = dirty | int(touch[r0 + b]) if jb else dirty & ~(1 << b)
+                    dirty = (dirty | int(touch[r0 + b]) if jb else dirty) & ~(1 << b)
         assert res.samples == want
