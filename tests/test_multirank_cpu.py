@@ -1,8 +1,9 @@
 """The benchmark's multi-rank path on CPU: two gloo ranks, no GPU.
 
 Every rank docks its own shard (distinct seeds, same size) with no data
-exchange; only the timing is reduced (max over ranks) and the job throughput
-counts every rank's ligands."""
+exchange; only the timing is reduced (max over ranks), the job throughput
+counts every rank's ligands, and rank 0's choice of the reported form
+reaches every rank."""
 import os
 import socket
 import sys
@@ -29,9 +30,17 @@ def _worker(rank, world, port, out):
     w = bench.shard_spec(rank, 6)
     lib = gen.make_library(w["library"])
     local_ms = 100.0 + 50.0 * rank
+    # rank 0 measured accuracy (bf16 misses the bar); the other rank did not,
+    # and its own timings favour bf16: both must report rank 0's choice
+    forms = ["plain", "f16", "bf16"]
+    ms = {"plain": 10.0, "f16": 9.0, "bf16": 8.0 if rank == 0 else 1.0}
+    acc = {} if rank else {"plain": dict(rel_err_max=1e-5, best_pose_agreement=1.0),
+                           "f16": dict(rel_err_max=3e-4, best_pose_agreement=1.0),
+                           "bf16": dict(rel_err_max=2e-3, best_pose_agreement=1.0)}
     out[rank] = dict(lseed=w["library"]["seed"], sseed=w["search"]["seed"], xyz0=lib.xyz[:5].tolist(),
                      n=lib.n_ligands, max_ms=bench.max_over_ranks(local_ms, world),
-                     value=bench.job_throughput(lib.n_ligands, world, 3, bench.max_over_ranks(local_ms, world)))
+                     value=bench.job_throughput(lib.n_ligands, world, 3, bench.max_over_ranks(local_ms, world)),
+                     form=bench.choose_form(forms, ms, acc, world))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -48,3 +57,4 @@ def test_two_gloo_ranks_shard_and_time():
     assert not np.allclose(a["xyz0"], b["xyz0"])         # different molecules per shard
     assert a["max_ms"] == b["max_ms"] == 150.0             # slowest rank
     assert abs(a["value"] - 6 * 2 * 3 / 0.150) < 1e-9       # all ranks' ligands / slowest time
+    assert a["form"] == b["form"] == "f16"                  # rank 0's choice on every rank
