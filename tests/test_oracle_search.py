@@ -86,6 +86,71 @@ def test_greedy_decisions_are_argmaxes_screen(oracle_lib, screen_sample):
         _replay(oracle_lib, w, lib, grid, l, range(5, 6))
 
 
+def _touch_masks(frags):
+    """Bit b of entry b': turning b' moves (its moving side without v_b') an
+    atom that b's sweep reads (b's moving side or its fixed end u_b)."""
+    mask, axis = frags
+    n = len(mask)
+    touch = []
+    for bp in range(n):
+        moved = mask[bp].copy()
+        moved[axis[bp, 1]] = False
+        t = 1 << bp
+        for b in range(n):
+            reads = mask[b].copy()
+            reads[axis[b, 0]] = True
+            if (moved & reads).any():
+                t |= 1 << b
+        touch.append(t)
+    return touch
+
+
+def test_clean_bonds_would_keep_their_torsion(oracle_lib, screen_sample):
+    """The rule the docking kernel uses to skip sweeps, checked against the
+    method with an independent FP64 scorer: a bond is clean after its own
+    sweep (kept or turned) until a turn of a bond whose touch mask names it.
+    At every decision the rule calls clean, a full re-sweep from that state
+    (candidates recomputed from the accumulated torsions) has its maximum at
+    j = 0 up to rounding, so deciding 0 without sampling is the method's own
+    choice (exactly, or at a tie of rounding size)."""
+    w, lib, grid = screen_sample
+    search = w["search"]
+    og = oracle_lib.OGrid.from_grid(grid)
+    step, P = search["torsion_step_deg"], search["passes"]
+    nt = 360 // step
+    pen = search["out_penalty"]
+    ligs = [l for l in range(lib.n_ligands) if 3 <= lib.n_rot[l] <= 6 and lib.n_atoms[l] <= 40][:3]
+    assert ligs
+    checked = turned_then_clean = 0
+    for l in ligs:
+        lig, samp, frags = _setup(lib, grid, l)
+        touch = _touch_masks(frags)
+        n = lig.n_rot
+        res = oracle_lib.dock_ligand(lig, og, search, l, range(0, 2))
+        for j, r in enumerate(range(0, 2)):
+            qr, tr = oracle_lib.restart_init(og, search, l, r)
+            rot = indep.rot_from_wxyz(qr) * indep.rot_from_wxyz(oracle_lib.octahedral(int(res["trace"][j, 0])))
+            counts = np.zeros(n, int)
+            dirty, turned = (1 << n) - 1, 0
+            for d in range(P * n):
+                b = d % n
+                jb = int(res["trace"][j, 1 + d])
+                if not dirty >> b & 1:
+                    cand = []
+                    for jj in range(nt):
+                        c = counts.copy()
+                        c[b] += jj
+                        cand.append(_indep_score(lig, samp, frags, tr, rot, np.radians(c * step), pen))
+                    s = np.array([v[0] for v in cand])
+                    assert s.max() - s[0] <= 1e-9 * cand[0][1], (l, r, d, s.max() - s[0])
+                    checked += 1
+                    turned_then_clean += turned >> b & 1
+                counts[b] = (counts[b] + jb) % nt
+                turned = (turned | (1 << b)) if jb else turned & ~(1 << b)
+                dirty = ((dirty | touch[b]) if jb else dirty) & ~(1 << b)
+    assert checked > 0 and turned_then_clean > 0
+
+
 def _rigid_copy(lib, l):
     import gen
     g = dict(lib.ligand(l))
