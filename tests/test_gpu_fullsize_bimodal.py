@@ -2,8 +2,10 @@
 and 0-8 torsions, 30% with 60-120 atoms and 8-30 torsions; 256 restarts,
 10-degree steps, 3 passes, top 30) through the bucketed layout, checked by
 properties of every output and against the oracle on sampled small and large
-ligands (needs a GPU). Decision traces stay on the device; only the sampled
-ligands' slices are copied back."""
+ligands; and in the form the benchmark reports for it (FP16 records, plain
+launch) against the oracle on the FP16-rounded grid (needs a GPU). Decision
+traces stay on the device; only the sampled ligands' slices are copied
+back."""
 import numpy as np
 import pytest
 import torch
@@ -54,15 +56,51 @@ def test_sampled_small_and_large_ligands_match_oracle(run, oracle_lib):
     lg, w, lib, grid, res = run
     s = w["search"]
     R, K, P = s["restarts"], s["top_k"], s["passes"]
-    small = np.nonzero(lib.n_atoms <= 35)[0]
-    large = np.nonzero(lib.n_atoms >= 60)[0]
-    pick = sorted({int(x) for x in small[np.linspace(0, len(small) - 1, 6).astype(int)]} |
-                  {int(x) for x in large[np.linspace(0, len(large) - 1, 3).astype(int)]} |
-                  {int(np.argmax(lib.n_rot)), int(np.argmax(lib.n_atoms))})
+    pick = _sample(lib)
     rs = range(0, 8)
     ref = oracle_lib.dock_library(lib, grid, s, ligands=pick, restarts=rs)
     scores = res.scores.cpu().numpy()
     top = res.top_restart.cpu().numpy()
+    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    for r_ in ref:
+        l = r_["ligand"]
+        D = 1 + P * int(lib.n_rot[l])
+        start = R * (l + P * int(lib.rot_off[l]))
+        gt = res.trace[start:start + R * D].cpu().numpy().reshape(R, D)
+        final = {int(top[l, k]): float(scores[l, k]) for k in range(K)}
+        st = parity.check_dock_ligand(l, r_, gt, final)
+        for k in tot:
+            tot[k] += st[k]
+    print(tot)
+    assert tot["restarts"] == len(pick) * len(rs)
+    assert tot["clean"] >= 0.85 * tot["restarts"]
+
+
+def _sample(lib):
+    small = np.nonzero(lib.n_atoms <= 35)[0]
+    large = np.nonzero(lib.n_atoms >= 60)[0]
+    return sorted({int(x) for x in small[np.linspace(0, len(small) - 1, 6).astype(int)]} |
+                  {int(x) for x in large[np.linspace(0, len(large) - 1, 3).astype(int)]} |
+                  {int(np.argmax(lib.n_rot)), int(np.argmax(lib.n_atoms))})
+
+
+def test_fp16_records_plain_launch_match_oracle_on_rounded_grid(run, oracle_lib):
+    lg, w, lib, grid, _ = run
+    s = w["search"]
+    R, K, P = s["restarts"], s["top_k"], s["passes"]
+    L = lg.Ligands.from_arrays(lib, "cuda")
+    G = lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, "cuda")
+    res = lg.dock_batch(L, G, restarts=R, torsion_step_deg=s["torsion_step_deg"], passes=P, top_k=K,
+                        seed=s["seed"], n_rigid=s["n_rigid"], jitter=s["jitter"], out_penalty=s["out_penalty"],
+                        trace=True, top_restart=True, grid_format="f16")
+    torch.cuda.synchronize()
+    assert int(res.status.abs().sum()) == 0
+    scores = res.scores.cpu().numpy()
+    assert np.isfinite(scores).all() and np.all(np.diff(scores, axis=1) <= 0)
+    top = res.top_restart.cpu().numpy()
+    pick = _sample(lib)
+    rs = range(0, 8)
+    ref = oracle_lib.dock_library(lib, parity.oracle_grid(oracle_lib, grid, "f16"), s, ligands=pick, restarts=rs)
     tot = dict(decisions=0, restarts=0, clean=0, scores=0)
     for r_ in ref:
         l = r_["ligand"]
