@@ -217,6 +217,19 @@ __device__ __forceinline__ void ld_global_v8(const float* p, float (&v)[8]) {
                : "l"(p));
 }
 
+// The same load without allocating the line in L1 (L1::no_allocate): the
+// sampler's 32-byte records are rarely read twice from L1 (~3% hits), and
+// not allocating them keeps L1 for the kernel's other data. Measured on
+// GB300 (8,000 screening ligands): FP32 docking 18.97 -> 18.35 ms. The same
+// hint on the 16-byte records made FP16 docking 1.2% slower, so they keep
+// the default.
+__device__ __forceinline__ void ld_global_v8_na(const float* p, float (&v)[8]) {
+  asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+                 "=f"(v[7])
+               : "l"(p));
+}
+
 // Energy of channel `c` at grid-unit position u (u = (x - origin) / spacing).
 // Inside iff 0 <= u <= n - 1 on every axis; cell i = min(floor(u), n - 2),
 // f = u - i. Outside: the penalty.
@@ -233,7 +246,7 @@ __device__ __forceinline__ float grid_sample(const GridView& g, float ux, float 
     if (!lg_check(g.check, c >= 0 && c < g.nc && ri < g.n_rec, kChkGridRecord)) return g.penalty;
     const float* rec = g.coef + ri * 8;
     float a[8];
-    ld_global_v8(rec, a);
+    ld_global_v8_na(rec, a);
     float t1 = fmaf(dz, a[7], a[4]);
     float t2 = fmaf(dy, t1, a[1]);
     t2 = fmaf(dz, a[5], t2);
