@@ -1,6 +1,7 @@
 // Gather-ceiling probe: loads from uniformly random 32-byte records of a
-// buffer (4, 8, 16 or all 32 bytes of each), with no pose arithmetic. It measures the achievable rate of the docking kernel's
-// access pattern (one aligned 256-bit load per atom sample) on this device,
+// buffer (4, 8, 16 or all 32 bytes of each), with no pose arithmetic. It
+// measures the achievable rate of the docking kernel's access pattern (one
+// aligned load of one record per atom sample) on this device,
 // which is the denominator of the docking kernel's roofline. The paper has
 // no counterpart; this is a measurement utility.
 #include "../../include/ligen.h"
@@ -12,11 +13,14 @@ namespace {
 constexpr int kProbeThreads = 256;
 constexpr int kProbeStreams = 8;   // independent loads in flight per thread
 
+// Each width loads the way the docking kernel's sampler of that record size
+// does: 32 bytes without L1 allocation (FP32 records), 16 bytes through the
+// read-only path (FP16 / BF16 records).
 template <int BYTES>
 __device__ __forceinline__ float probe_load(const float* p) {
   if constexpr (BYTES == 32) {
     float v[8];
-    ld_global_v8(p, v);
+    ld_global_v8_na(p, v);
     return (v[0] + v[1]) + (v[2] + v[3]) + (v[4] + v[5]) + (v[6] + v[7]);
   } else if constexpr (BYTES == 16) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));
