@@ -350,7 +350,8 @@ int64_t ligen_bucket_size(int32_t max_atoms, int32_t* b, int32_t* sm, int32_t* t
  * a full-device launch makes `loads_per_thread` aligned loads of
  * `bytes_per_load` (4, 8, 16 or 32) bytes, each from the start of a uniformly
  * random 32-byte record of `records` (DEVICE, n_records * 8 floats, 32-byte
- * aligned), and discards the values (`sink`, DEVICE, 1 float, is written
+ * aligned; 32-byte loads skip L1 allocation as the FP32 sampler's do), and
+ * discards the values (`sink`, DEVICE, 1 float, is written
  * only to keep the loads alive). *loads_done receives the number of loads
  * made and *ms_out their device time (CUDA events on `stream`; the call
  * synchronises). With 32-byte loads over a buffer that fits in L2 this is
