@@ -10,37 +10,49 @@
 
 namespace ligen {
 
-// Per-bond values of the group's pose, bond b held by lane b % W (two bonds
-// per lane, so at most 2 W bonds): sin and cos of the torsion and the bond
-// record, read by shuffle inside the bond loops, so each lane computes two
+// Per-bond values of the group's pose, bond b held by lane b % W (K bonds
+// per lane, K W >= the bond limit): sin and cos of the torsion and the bond
+// record, read by shuffle inside the bond loops, so each lane computes K
 // sincosf instead of n and the loops carry no global load of their own.
 template <int W>
 struct GroupBonds {
   static_assert(W >= 1 && W <= 32 && (W & (W - 1)) == 0, "a power-of-two group width");
-  static_assert(LIGEN_MAX_ROT <= 2 * W, "two torsions per lane");
-  float s_lo = 0.f, c_lo = 1.f, s_hi = 0.f, c_hi = 1.f;
-  uchar4 b_lo = make_uchar4(0, 0, 0, 0), b_hi = make_uchar4(0, 0, 0, 0);
+  static constexpr int K = (LIGEN_MAX_ROT + W - 1) / W;   // bonds per lane
+  float s[K], c[K];
+  unsigned rec[K];   // uchar4 bond records
 
   // theta: the pose's n torsions; r0: the ligand's first bond.
   __device__ __forceinline__ void load(const Packed& pk, int r0, int n, const float* theta, int sub) {
-    if (sub < n) {
-      sincosf(theta[sub], &s_lo, &c_lo);
-      b_lo = pk.binfo[r0 + sub];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      s[k] = 0.f;
+      c[k] = 1.f;
+      rec[k] = 0u;
+      if (sub + k * W < n) {
+        sincosf(theta[k * W + sub], &s[k], &c[k]);
+        const uchar4 r = pk.binfo[r0 + k * W + sub];
+        rec[k] = *reinterpret_cast<const unsigned*>(&r);
+      }
     }
-    if (sub + W < n) {
-      sincosf(theta[W + sub], &s_hi, &c_hi);
-      b_hi = pk.binfo[r0 + W + sub];
-    }
+  }
+  // This lane's entry for bond b (b is warp-uniform, so the select is too).
+  template <typename T>
+  __device__ __forceinline__ static T mine(const T (&v)[K], int b) {
+    const int k = b / W;
+    T x = v[0];
+#pragma unroll
+    for (int kk = 1; kk < K; ++kk)
+      if (k == kk) x = v[kk];
+    return x;
   }
   // All lanes of the warp call these with the same b.
   __device__ __forceinline__ uchar4 bond(int b) const {
-    const uchar4 mine = b < W ? b_lo : b_hi;
-    const unsigned w = __shfl_sync(0xffffffffu, *reinterpret_cast<const unsigned*>(&mine), b % W, W);
+    const unsigned w = __shfl_sync(0xffffffffu, mine(rec, b), b % W, W);
     return *reinterpret_cast<const uchar4*>(&w);
   }
-  __device__ __forceinline__ void sincos(int b, float* s, float* c) const {
-    *s = __shfl_sync(0xffffffffu, b < W ? s_lo : s_hi, b % W, W);
-    *c = __shfl_sync(0xffffffffu, b < W ? c_lo : c_hi, b % W, W);
+  __device__ __forceinline__ void sincos(int b, float* sn, float* cs) const {
+    *sn = __shfl_sync(0xffffffffu, mine(s, b), b % W, W);
+    *cs = __shfl_sync(0xffffffffu, mine(c, b), b % W, W);
   }
 };
 
