@@ -38,7 +38,9 @@ namespace {
 
 constexpr int kGradWarps = 4;
 // Lanes per pose: measured on GB300 (refining 8,000 screening ligands' top
-// 16 poses), 16 lanes are 1-2% faster than 8 and 40% faster than 4.
+// 16 poses), 16 lanes are 1-2% faster than 8 and 40% faster than 4; with the
+// one-evaluation step and the shared bond values, 8 lanes (four poses per
+// warp, three CTAs per SM) come within 1% either way.
 constexpr int kGradLanes = 16;
 constexpr int kPosesPerWarp = 32 / kGradLanes;
 constexpr int kGroups = kGradWarps * kPosesPerWarp;  // poses per CTA
