@@ -208,21 +208,14 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b
   return upk2(d);
 }
 
-// 256-bit read-only load (sm_100+): one 32-byte record in one instruction.
-// Not volatile: the load has no side effect, so the compiler may batch it.
-__device__ __forceinline__ void ld_global_v8(const float* p, float (&v)[8]) {
-  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
-                 "=f"(v[7])
-               : "l"(p));
-}
-
-// The same load without allocating the line in L1 (L1::no_allocate): the
-// sampler's 32-byte records are rarely read twice from L1 (~3% hits), and
-// not allocating them keeps L1 for the kernel's other data. Measured on
-// GB300 (8,000 screening ligands): FP32 docking 18.97 -> 18.35 ms. The same
-// hint on the 16-byte records made FP16 docking 1.2% slower, so they keep
-// the default.
+// 256-bit read-only load (sm_100+): one 32-byte record in one instruction,
+// not volatile (no side effect, so the compiler may batch it), and without
+// allocating the line in L1 (L1::no_allocate): the samplers' 32-byte
+// records are rarely read twice from L1 (~3% hits), and not allocating them
+// keeps L1 for the kernels' other data. Measured on
+// GB300 (8,000 screening ligands): FP32 docking 18.97 -> 18.35 ms, gradient
+// refinement of their top 16 poses 9.27 -> 8.52 ms. The same hint on the
+// 16-byte records made FP16 docking 1.2% slower, so they keep the default.
 __device__ __forceinline__ void ld_global_v8_na(const float* p, float (&v)[8]) {
   asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
@@ -345,7 +338,7 @@ __device__ __forceinline__ float grid_sample_grad(const GridView& g, float ux, f
     if (!lg_check(g.check, c >= 0 && c < g.nc && ri < g.n_rec, kChkGridRecord)) return g.penalty;
     const float* rec = g.coef + ri * 8;
     float a[8];
-    ld_global_v8(rec, a);
+    ld_global_v8_na(rec, a);
     float t1 = fmaf(dz, a[7], a[4]);
     float t2 = fmaf(dy, t1, a[1]);
     t2 = fmaf(dz, a[5], t2);
