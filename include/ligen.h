@@ -24,7 +24,10 @@
  *   - The library owns one internal device workspace per (device, stream),
  *     grown on demand and released by ligen_release_workspaces(). Two calls
  *     in flight on different streams use different workspaces; calls on the
- *     same stream are ordered by the stream.
+ *     same stream are ordered by the stream, so several host threads that
+ *     share a stream must not call into the library at the same time (their
+ *     copies into the shared workspace could interleave). No workspace
+ *     content is assumed to survive from one call to the next.
  *   - Argument errors are detected on the host and returned immediately,
  *     before any device work (message in ligen_last_error()). Errors in a
  *     single ligand's data (not a tree, index or type out of range) do not
