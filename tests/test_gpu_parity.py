@@ -182,6 +182,47 @@ def test_dock_screen_sample_matches_oracle(lg, oracle_lib, screen_sample, fmt):
     assert tot["clean"] >= 0.9 * tot["restarts"] and tot["scores"] > 0
 
 
+def test_restart_initial_poses_match_oracle(lg, oracle_lib, small32):
+    """Restart initialisation on its own: with one rigid candidate (the
+    identity) and no sweep pass, every restart's pose is its initial one,
+    the Shoemake quaternion and jittered translation of the counter hash."""
+    w, lib, grid = small32
+    s = dict(w["search"], restarts=8, top_k=8, n_rigid=1, passes=0)
+    Ld, Gd = _dev(lg, lib, grid)
+    res = lg.dock_batch(Ld, Gd, restarts=8, torsion_step_deg=s["torsion_step_deg"], passes=0, top_k=8,
+                        seed=s["seed"], n_rigid=1, jitter=s["jitter"], top_restart=True)
+    torch.cuda.synchronize()
+    poses = res.poses.cpu().numpy()
+    top = res.top_restart.cpu().numpy()
+    og = oracle_lib.OGrid.from_grid(grid)
+    off = lg.pose_offsets(lib.rot_off, 8)
+    for l in range(lib.n_ligands):
+        P = poses[off[l]:off[l + 1]].reshape(8, -1)
+        assert np.all(P[:, 7:] == 0)                          # torsions untouched
+        for k in range(8):
+            q, t = oracle_lib.restart_init(og, s, l, int(top[l, k]))
+            q = q * (1.0 if q[0] >= 0 else -1.0)
+            np.testing.assert_allclose(P[k, :3], t, atol=4e-6, rtol=0)    # FP32 at ~10 A
+            np.testing.assert_allclose(P[k, 3:7], q, atol=1e-6, rtol=0)
+    # with the 24 cube rotations, the kept orientation is q_r (x) g_k (body
+    # frame) for the rotation k the restart chose
+    res = lg.dock_batch(Ld, Gd, restarts=8, torsion_step_deg=s["torsion_step_deg"], passes=0, top_k=8,
+                        seed=s["seed"], n_rigid=24, jitter=s["jitter"], top_restart=True, trace=True)
+    torch.cuda.synchronize()
+    poses = res.poses.cpu().numpy()
+    top = res.top_restart.cpu().numpy()
+    trace = res.trace.cpu().numpy()
+    for l in range(lib.n_ligands):
+        P = poses[off[l]:off[l + 1]].reshape(8, -1)
+        tr = parity.ligand_trace(trace, lib.rot_off, 8, 0, l)
+        for k in range(8):
+            r = int(top[l, k])
+            qr, _ = oracle_lib.restart_init(og, s, l, r)
+            q = oracle_lib.quat_mul(qr, oracle_lib.octahedral(int(tr[r, 0])))
+            q = q / np.linalg.norm(q) * (1.0 if q[0] >= 0 else -1.0)
+            np.testing.assert_allclose(P[k, 3:7], q, atol=1e-6, rtol=0)
+
+
 def test_dock_top_k_and_poses(lg, oracle_lib, small32):
     w, lib, grid = small32
     s = w["search"]
