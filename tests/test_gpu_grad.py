@@ -1,10 +1,15 @@
 """Pose gradients, autograd and gradient refinement vs the oracle (needs a GPU).
 
-Gradient tolerance: per component |g_gpu - g_ref| <= 1e-3 * (1 + max|g_ref|),
-on poses with no atom within 1e-4 cells of a cell face (the trilinear field
-has kinks there: FP32 and FP64 positions may sit on different sides). The
-FP64 central differences use h = 1e-4 on parameters whose +-h interval moves
-no atom across a cell face or the box boundary."""
+Gradient tolerance: per component |g_gpu - g_ref| <= 2e-4 * (1 + max|g_ref|)
+against the oracle's FP64 analytic gradient, and a relative error (2-norm)
+below 2e-4 against it and below 5e-4 against FP64 central differences, on
+poses with no atom within 1e-4 cells of a cell face (the trilinear field has
+kinks there: FP32 and FP64 positions may sit on different sides). These are
+about ten times the largest errors measured on GB300 over the same 248 poses
+(2.3e-5 against the analytic gradient, 3.7e-5 against central differences),
+so a wrong sign or scale in any one term fails them. The FP64 central
+differences use h = 1e-4 on parameters whose +-h interval moves no atom
+across a cell face or the box boundary."""
 import numpy as np
 import pytest
 import torch
@@ -73,7 +78,7 @@ def test_pose_grad_matches_oracle_and_central_differences(lg, oracle_lib, small3
             _, D, _, Gs = oracle_lib.score_pose(lig, og, P[k], 5.0, sensitivity=True)
             assert abs(sc[l, k] - S) <= parity.score_tol(D, Gs)
             scale = 1.0 + np.abs(g).max()
-            assert np.all(np.abs(G_gpu[k] - g) <= 1e-3 * scale), (l, k, G_gpu[k], g)
+            assert np.all(np.abs(G_gpu[k] - g) <= 2e-4 * scale), (l, k, G_gpu[k], g)
             rel_an.append(np.linalg.norm(G_gpu[k] - g) / max(np.linalg.norm(g), 1e-12))
             fd = np.full_like(g, np.nan)
             for a in range(len(g)):
@@ -89,7 +94,7 @@ def test_pose_grad_matches_oracle_and_central_differences(lg, oracle_lib, small3
     print(f"poses {used}: gradient rel. error vs analytic FP64 median {np.median(rel_an):.2e} "
           f"max {np.max(rel_an):.2e}; vs central differences median {np.median(rel_fd):.2e} "
           f"max {np.max(rel_fd):.2e}")
-    assert used >= 100 and np.max(rel_fd) < 1e-2
+    assert used >= 100 and np.max(rel_an) < 2e-4 and np.max(rel_fd) < 5e-4
 
 
 def test_autograd_backward_is_the_adjoint(lg, small32):
