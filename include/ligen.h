@@ -246,23 +246,37 @@ int ligen_dock_sites(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
  * host framework whose caching allocator already owns the device's memory,
  * or a latency-bound service that cannot take the device-wide
  * synchronisation a cudaMalloc/cudaFree implies. The paper has no
- * counterpart. Same arguments, search and outputs as ligen_dock_batch, with
+ * counterpart. Same search and outputs as ligen_dock_batch with default
+ * layout settings (bit for bit: the same kernels on the same inputs), with
  * these differences:
  *   - Its scratch is one file-scope device array of LIGEN_STATIC_SCRATCH_BYTES
  *     inside this library (every GPU that loads the library holds it until
  *     the process exits); the call itself allocates nothing. A batch whose
  *     scratch would exceed it is rejected with LIGEN_ERR_UNSUPPORTED before
- *     any device work. Scratch bytes, each term rounded up to 256: grid
- *     cells (nx-1)(ny-1)(nz-1) * nc * 32; 16 per atom; 136 per rotatable
- *     bond; 4 per ligand; restarts * (5 per ligand + 1 per rotatable bond).
- *   - Ligands, grid and every output must be device memory.
+ *     any device work. With L ligands, A atoms and B rotatable bonds in
+ *     total, R restarts and an nx x ny x nz x nc grid, the scratch is the sum
+ *     of these ten regions, EACH rounded up to a multiple of 256 bytes:
+ *       (nx-1)(ny-1)(nz-1) nc * 32   grid records
+ *       16 A                         packed coordinates
+ *       4 B, 128 B, 4 B              bond records, moving-atom lists, masks
+ *       4 L                          ligand status
+ *       4 L R, L R, B R              per-restart scores, rotations, torsions
+ *     plus, in bounds-checked builds (LIGEN_CHECKED) only, one more 256-byte
+ *     region for the error word. A batch is accepted iff that sum is at most
+ *     LIGEN_STATIC_SCRATCH_BYTES.
+ *   - Ligands, grid and every output must be device memory
+ *     (LIGEN_ERR_INVALID_ARG otherwise).
+ *   - Only the plain launch over FP32 grid records runs: grid_format other
+ *     than LIGEN_GRID_F32, batching other than LIGEN_BATCH_PLAIN,
+ *     rescore_fp64 != 0, scores_f64, stage_ms or samples not NULL, or
+ *     mode != 0 are rejected with LIGEN_ERR_UNSUPPORTED (never ignored).
+ *     status, trace and top_restart are written as by ligen_dock_batch.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
  *   - All calls share the one array: two calls that overlap on the GPU (for
  *     instance on different streams without ordering) race and corrupt each
  *     other's results. Each call writes every scratch region before reading
- *     it, so the contents left by the previous call do not matter.
- *   - stage_ms and samples are ignored; mode must be 0. */
+ *     it, so the contents left by the previous call do not matter. */
 #define LIGEN_STATIC_SCRATCH_BYTES (32u << 20)
 int ligen_dock_batch_static(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                             const ligen_params_t* params, float* out_poses, float* out_scores);
@@ -285,10 +299,14 @@ int ligen_tune_get(int32_t bucket, int32_t* lanes, int32_t* restarts_per_cta);
 int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, const ligen_params_t* params,
                    int32_t sample, int32_t* out_lanes, int32_t* out_rpc, float* out_ms_per_ligand);
 
-/* Score given poses (same pose packing as ligen_dock_batch with K =
- * poses_per_ligand): out_scores[l][p] = S of pose p of ligand l, or
- * -INFINITY for an invalid ligand. `poses` and `out_scores` share one memory
- * space. */
+/* Score given poses: the scoring half of the dock task of paper §2 (the
+ * task that estimates the ligand's placement in the docking site). The
+ * search of ligen_dock_batch keeps the candidates that maximise this score;
+ * here the caller supplies the poses. It is not §2's third task, which rates
+ * the interaction strength of an already docked ligand.
+ * Same pose packing as ligen_dock_batch with K = poses_per_ligand:
+ * out_scores[l][p] = S of pose p of ligand l, or -INFINITY for an invalid
+ * ligand. `poses` and `out_scores` share one memory space. */
 int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                       int32_t poses_per_ligand, const float* poses, float out_penalty,
                       float* out_scores, void* stream);

@@ -214,23 +214,25 @@ def dock_sites(ligands: Ligands, grids: list, *, restarts: int, torsion_step_deg
 
 def dock_batch_static(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_step_deg: int, passes: int,
                       top_k: int, seed: int, n_rigid: int = 24, jitter: float = 1.0, out_penalty: float = 5.0,
+                      status: bool = True, trace: bool = False, top_restart: bool = False,
+                      batching: str = "plain", grid_format: str = "f32", rescore_fp64: bool = False,
+                      mode: str = "greedy", stage_ms: bool = False, count_samples: bool = False,
                       out: DockResult | None = None) -> DockResult:
     """ligen_dock_batch_static: ligen_dock_batch with the library's fixed
     device scratch instead of an allocated workspace (device tensors only).
 
     Pass `out` (device tensors allocated beforehand) to make the call itself
     allocate nothing; without it the binding allocates the outputs with torch.
-    """
+    Every setting is passed to the library as given: it runs the plain launch
+    over FP32 records only and rejects the others (LigenError, code -2)."""
     lib = _abi.load()
-    L, dev = ligands.n_ligands, ligands.device
-    n_sum = int(ligands.h_rot_off[-1])
     if out is None:
-        out = DockResult(poses=_empty((top_k * (7 * L + n_sum),), torch.float32, dev),
-                         scores=_empty((L, top_k), torch.float32, dev),
-                         status=_empty((L,), torch.int32, dev), trace=None, top_restart=None, stage_ms=None)
-    p = ParamsT(restarts, n_rigid, torsion_step_deg, passes, top_k, 0, int(seed) & ((1 << 64) - 1),
-                float(jitter), float(out_penalty), _stream_handle(dev), _ptr(out.status), _ptr(out.trace),
-                _ptr(out.top_restart), None, _abi.LIGEN_BATCH_PLAIN, _abi.LIGEN_GRID_F32, 0, 0, None)
+        out = _dock_outputs(ligands, restarts, passes, top_k, (), status, trace, top_restart, stage_ms, rescore_fp64)
+    p = _dock_params(ligands.device, out, restarts, torsion_step_deg, passes, top_k, seed, n_rigid, jitter,
+                     out_penalty, batching, grid_format, rescore_fp64, mode)
+    n_samples = C.c_int64(0)
+    if count_samples:
+        p.samples = C.cast(C.pointer(n_samples), C.c_void_p)
     check(lib.ligen_dock_batch_static(C.byref(ligands._s), C.byref(grid._s), C.byref(p), _ptr(out.poses),
                                       _ptr(out.scores)))
     return out

@@ -1481,6 +1481,16 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
   int rc;
   if ((rc = check_params(params)) != LIGEN_OK) return rc;
   if (params->mode != 0) return fail(LIGEN_ERR_UNSUPPORTED, "ligen_dock_batch_static runs the greedy search (mode 0)");
+  // The call runs the plain launch over FP32 grid records and nothing else;
+  // every setting it would not honour is refused rather than ignored.
+  if (params->grid_format != LIGEN_GRID_F32)
+    return fail(LIGEN_ERR_UNSUPPORTED, "ligen_dock_batch_static samples FP32 grid records only (grid_format 0)");
+  if (params->batching != LIGEN_BATCH_PLAIN)
+    return fail(LIGEN_ERR_UNSUPPORTED, "ligen_dock_batch_static runs the plain launch only (batching 0)");
+  if (params->rescore_fp64 != 0 || params->scores_f64)
+    return fail(LIGEN_ERR_UNSUPPORTED, "ligen_dock_batch_static has no FP64 re-score (rescore_fp64 0, scores_f64 NULL)");
+  if (params->stage_ms || params->samples)
+    return fail(LIGEN_ERR_UNSUPPORTED, "ligen_dock_batch_static reports neither stage_ms nor samples (both NULL)");
   LibShape sh;
   if ((rc = check_ligands(ligands, params->passes, &sh)) != LIGEN_OK) return rc;
   if ((rc = check_grid(grid)) != LIGEN_OK) return rc;
