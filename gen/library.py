@@ -206,13 +206,30 @@ def _chunk(seed: int, chunk: int, lc: int, spec: dict) -> list[dict]:
     return out
 
 
-def make_library(spec: dict) -> Library:
-    """Generate the library described by `spec` (see gen.configs)."""
+def _chunk_args(args):
+    return _chunk(*args)
+
+
+def make_library(spec: dict, workers: int = 1) -> Library:
+    """Generate the library described by `spec` (see gen.configs).
+
+    workers > 1 grows the chunks in that many spawned processes (each chunk
+    has its own generator, so the library is the same for any worker count;
+    spawn, not fork, so a process that already holds a CUDA context may call
+    it)."""
     L = int(spec["n_ligands"])
     seed = int(spec["seed"])
+    jobs = [(seed, c, min(CHUNK, L - start), spec) for c, start in enumerate(range(0, L, CHUNK))]
     ligs: list[dict] = []
-    for c, start in enumerate(range(0, L, CHUNK)):
-        ligs.extend(_chunk(seed, c, min(CHUNK, L - start), spec))
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(min(workers, len(jobs)), mp_context=mp.get_context("spawn")) as ex:
+            for part in ex.map(_chunk_args, jobs):
+                ligs.extend(part)
+    else:
+        for job in jobs:
+            ligs.extend(_chunk(*job))
     return from_ligands(ligs)
 
 

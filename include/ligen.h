@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define LIGEN_ABI_VERSION 4
+#define LIGEN_ABI_VERSION 5
 #define LIGEN_MAX_ATOMS 256
 #define LIGEN_MAX_ROT 32
 #define LIGEN_MAX_CHANNELS 64
@@ -151,10 +151,17 @@ typedef struct ligen_grid {
  *                        but each group is a plain launch of one CTA per
  *                        work item (no device counter): the static
  *                        per-bucket launches the persistent form is
- *                        compared against. */
+ *                        compared against;
+ *   LIGEN_BATCH_QUEUE    the whole library in ONE persistent launch: one
+ *                        device work queue over every ligand in the
+ *                        buckets' largest-cost-first order, the default
+ *                        kernel shape, shared memory sized for the
+ *                        library's largest ligand, Eq. 1's b x SM CTAs,
+ *                        captured into a CUDA graph like the buckets. */
 #define LIGEN_BATCH_PLAIN 0
 #define LIGEN_BATCH_BUCKETS 1
 #define LIGEN_BATCH_BUCKETS_STATIC 2
+#define LIGEN_BATCH_QUEUE 3
 #define LIGEN_N_BUCKETS 44 /* 4 atom classes x 11 rotamer classes */
 
 /* How the docking kernel stores the grid it samples (built from the
@@ -163,7 +170,7 @@ typedef struct ligen_grid {
  *                    the cell's trilinear polynomial;
  *   LIGEN_GRID_F16   16 bytes: the 8 corner values in FP16;
  *   LIGEN_GRID_BF16  16 bytes: the 8 corner values in BF16.
- * The 16-bit formats run with 4 or 8 lanes per restart. */
+ * The 16-bit formats run with 4, 8, 16 or 32 lanes per restart. */
 #define LIGEN_GRID_F32 0
 #define LIGEN_GRID_F16 1
 #define LIGEN_GRID_BF16 2
@@ -183,7 +190,7 @@ typedef struct ligen_params {
   int16_t* trace;
   int32_t* top_restart;
   float* stage_ms;
-  int32_t batching;     /* LIGEN_BATCH_PLAIN, _BUCKETS or _BUCKETS_STATIC */
+  int32_t batching;     /* LIGEN_BATCH_PLAIN, _BUCKETS, _BUCKETS_STATIC or _QUEUE */
   int32_t grid_format;  /* LIGEN_GRID_F32, LIGEN_GRID_F16 or LIGEN_GRID_BF16 */
   int32_t rescore_fp64; /* 1: re-score the K kept poses of every ligand in
                            FP64 on the GPU (from the caller's FP32 grid
@@ -201,6 +208,13 @@ typedef struct ligen_params {
                            (moving atoms - 1); exhaustive mode: every
                            combination's N. Counting makes the call wait
                            for its work. */
+  float* coords;        /* optional debug output, same memory space as
+                           out_scores: the final FP32 atom positions of every
+                           restart as the docking kernel holds them, in grid
+                           units u = (x - origin) / spacing, ligand l's block
+                           at 3 * R * atom_off[l], restart r at + 3 * r * N_l,
+                           atom i at + 3 * i (x, y, z); [n_sites][...] for
+                           ligen_dock_sites. Greedy mode only. */
 } ligen_params_t;
 
 /* Dock every ligand (paper §2, the dock task; cost per §3 follows atoms and
@@ -283,14 +297,18 @@ int ligen_dock_batch_static(const ligen_ligands_t* ligands, const ligen_grid_t* 
 
 /* Tuning table of the bucketed layout, one per device (the current one):
  * for bucket b (atom_class * 11 + rotamer_class, 0 .. LIGEN_N_BUCKETS-1) the
- * lanes per restart (2, 4 or 8) and restarts per CTA (a multiple of 32/lanes,
- * lanes * restarts <= 128). Defaults: 8 lanes, 16 restarts. */
+ * lanes per restart (2, 4, 8, 16 or 32) and restarts per CTA (a multiple of
+ * 32/lanes, lanes * restarts <= 128). Defaults: 8 lanes, 16 restarts. The
+ * 16-bit grid formats run with 4 to 32 lanes; other shapes fall back to the
+ * default. */
 int ligen_tune_set(int32_t bucket, int32_t lanes, int32_t restarts_per_cta);
 int ligen_tune_get(int32_t bucket, int32_t* lanes, int32_t* restarts_per_cta);
 
 /* Autotuner: for every bucket present in `ligands` (at most `sample`
- * ligands of each), dock with every candidate shape (lanes 4 or 8, 8 to 32
- * restarts per CTA), time the docking kernel with CUDA events on
+ * ligands of each), dock with every candidate shape (lanes per restart x
+ * restarts per CTA: 2 x 64, 4 x 16, 4 x 32, 8 x 8, 8 x 16, 16 x 8, 32 x 4;
+ * those the record format does not run are skipped), time the docking
+ * kernel with CUDA events on
  * params->stream, and store the fastest shape per ligand in the tuning table.
  * Writes the chosen shapes to out_lanes / out_rpc ([LIGEN_N_BUCKETS], HOST,
  * 0 for absent buckets) and each bucket's best time per ligand in
@@ -310,6 +328,34 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
 int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                       int32_t poses_per_ligand, const float* poses, float out_penalty,
                       float* out_scores, void* stream);
+
+/* Scoring inputs prepared once for many ligen_score_prepared calls: a
+ * caller that scores batch after batch of poses of one library against one
+ * grid (a refinement loop, a rescoring service) pays the grid records and
+ * the ligand packer once instead of on every call. The paper has no
+ * counterpart; it is the scoring of ligen_score_poses split into its
+ * per-input and per-pose parts.
+ *   ligen_prepare_scoring  builds, on `stream`, the FP32 grid records, the
+ *          packed library and the scoring plan in one device allocation
+ *          owned by the returned handle (*out; NULL on error). Ligands and
+ *          grid may be host or device memory; the handle keeps no pointer
+ *          to them (host inputs: the call waits for their copies).
+ *          LIGEN_ERR_OOM when the allocation fails or exceeds the
+ *          ligen_set_workspace_limit cap.
+ *   ligen_score_prepared   ligen_score_poses on the prepared inputs (same
+ *          poses packing, outputs and results); `poses` and `out_scores`
+ *          in one memory space. Stream-ordered after the preparation when
+ *          on the same stream; otherwise the caller orders the streams.
+ *          Must run on the device the handle was prepared on.
+ *   ligen_release_prepared frees the handle (NULL: no-op). Its cudaFree
+ *          waits for the device, so release after the last call that uses
+ *          it, and never during a stream capture. */
+typedef struct ligen_prepared ligen_prepared_t;
+int ligen_prepare_scoring(const ligen_ligands_t* ligands, const ligen_grid_t* grid, void* stream,
+                          ligen_prepared_t** out);
+int ligen_score_prepared(const ligen_prepared_t* prep, int32_t poses_per_ligand, const float* poses,
+                         float out_penalty, float* out_scores, void* stream);
+int ligen_release_prepared(ligen_prepared_t* prep);
 
 /* Gradient of the pose score with respect to translation, rotation and
  * torsions (the differentiable form of the score; no paper counterpart).

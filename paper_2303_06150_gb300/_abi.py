@@ -23,6 +23,7 @@ LIGEN_N_STAGES = 5
 LIGEN_BATCH_PLAIN = 0
 LIGEN_BATCH_BUCKETS = 1
 LIGEN_BATCH_BUCKETS_STATIC = 2
+LIGEN_BATCH_QUEUE = 3
 LIGEN_N_BUCKETS = 44
 LIGEN_GRID_F32 = 0
 LIGEN_GRID_F16 = 1
@@ -49,7 +50,7 @@ class ParamsT(C.Structure):
                 ("jitter", C.c_float), ("out_penalty", C.c_float), ("stream", P), ("status", P),
                 ("trace", P), ("top_restart", P), ("stage_ms", P), ("batching", C.c_int32),
                 ("grid_format", C.c_int32), ("rescore_fp64", C.c_int32), ("reserved3", C.c_int32),
-                ("scores_f64", P), ("samples", P)]
+                ("scores_f64", P), ("samples", P), ("coords", P)]
 
 
 # Every function include/ligen.h declares, with its ctypes signature.
@@ -73,6 +74,9 @@ SIGNATURES = {
     "ligen_set_workspace_limit": (C.c_int, [C.c_int64]),
     "ligen_pack_touch": (C.c_int, [P, C.c_int32, P, P]),
     "ligen_abi_version": (C.c_int, []),
+    "ligen_prepare_scoring": (C.c_int, [P, P, P, P]),
+    "ligen_score_prepared": (C.c_int, [P, C.c_int32, P, C.c_float, P, P]),
+    "ligen_release_prepared": (C.c_int, [P]),
 }
 
 _lock = threading.Lock()

@@ -117,6 +117,7 @@ class DockResult:
     stage_ms: np.ndarray | None
     scores_f64: torch.Tensor | None = None
     samples: int | None = None   # atom samples the search needed (count_samples=True)
+    coords: torch.Tensor | None = None   # debug: final grid-unit positions per restart (coords=True)
 
     def ligand_poses(self, rot_off, l: int) -> torch.Tensor:
         K = self.scores.shape[1]
@@ -126,7 +127,7 @@ class DockResult:
 
 
 BATCHING = {"plain": _abi.LIGEN_BATCH_PLAIN, "buckets": _abi.LIGEN_BATCH_BUCKETS,
-            "buckets_static": _abi.LIGEN_BATCH_BUCKETS_STATIC}
+            "buckets_static": _abi.LIGEN_BATCH_BUCKETS_STATIC, "queue": _abi.LIGEN_BATCH_QUEUE}
 GRID_FORMATS = {"f32": _abi.LIGEN_GRID_F32, "f16": _abi.LIGEN_GRID_F16, "bf16": _abi.LIGEN_GRID_BF16}
 
 
@@ -135,23 +136,31 @@ def dock_batch(ligands: Ligands, grid: PocketGrid, *, restarts: int, torsion_ste
                status: bool = True, trace: bool = False, top_restart: bool = False,
                stage_ms: bool = False, batching: str = "plain", grid_format: str = "f32",
                rescore_fp64: bool = False, mode: str = "greedy", count_samples: bool = False,
-               out: DockResult | None = None) -> DockResult:
+               coords: bool = False, out: DockResult | None = None) -> DockResult:
     """ligen_dock_batch: dock every ligand, keep the top_k poses of each.
 
-    batching: "plain" (one launch) or "buckets" (paper §3 classes, one
-    persistent launch per atom class, replayed from a CUDA graph).
+    batching: "plain" (one launch), "buckets" (paper §3 classes, one
+    persistent launch per atom class, replayed from a CUDA graph),
+    "buckets_static" (the same groups, one CTA per work item) or "queue"
+    (one persistent launch over the whole library in bucket order).
     grid_format: "f32", "f16" or "bf16" grid records in the docking kernel.
     rescore_fp64: re-score and re-rank the kept poses in FP64 on the GPU;
     the FP64 scores are returned in `scores_f64`.
     mode: "greedy" (the search) or "exhaustive" (every combination of cube
     rotation and torsion increments per restart; small ligands only).
     count_samples: return in `samples` the atom samples the search needed
-    (the call then waits for its work)."""
+    (the call then waits for its work).
+    coords: return in `coords` (debug) the docking kernel's final FP32 atom
+    positions of every restart, in grid units, [3 * R * sum N] flat."""
     lib = _abi.load()
     if out is None:
         out = _dock_outputs(ligands, restarts, passes, top_k, (), status, trace, top_restart, stage_ms, rescore_fp64)
+        if coords:
+            out.coords = _empty((3 * restarts * int(ligands.h_atom_off[-1]),), torch.float32, ligands.device)
     p = _dock_params(ligands.device, out, restarts, torsion_step_deg, passes, top_k, seed, n_rigid, jitter,
                      out_penalty, batching, grid_format, rescore_fp64, mode)
+    if out.coords is not None:
+        p.coords = _ptr(out.coords)
     n_samples = C.c_int64(0)
     if count_samples:
         p.samples = C.cast(C.pointer(n_samples), C.c_void_p)
@@ -248,6 +257,46 @@ def score_poses(ligands: Ligands, grid: PocketGrid, poses: torch.Tensor, poses_p
     check(lib.ligen_score_poses(C.byref(ligands._s), C.byref(grid._s), poses_per_ligand, _ptr(poses),
                                 float(out_penalty), _ptr(out), _stream_handle(poses.device)))
     return out
+
+
+class PreparedScoring:
+    """ligen_prepare_scoring: grid records and packed library built once for
+    many score() calls (ligen_score_prepared); release() (or garbage
+    collection) frees them with ligen_release_prepared."""
+
+    def __init__(self, ligands: Ligands, grid: PocketGrid):
+        lib = _abi.load()
+        h = C.c_void_p()
+        check(lib.ligen_prepare_scoring(C.byref(ligands._s), C.byref(grid._s), _stream_handle(ligands.device),
+                                        C.byref(h)))
+        self._h = h
+        self.n_ligands = ligands.n_ligands
+
+    def score(self, poses: torch.Tensor, poses_per_ligand: int, out_penalty: float = 5.0,
+              out: torch.Tensor | None = None) -> torch.Tensor:
+        if self._h is None:
+            raise ValueError("released")
+        if out is None:
+            out = _empty((self.n_ligands, poses_per_ligand), torch.float32, poses.device)
+        check(_abi.load().ligen_score_prepared(self._h, poses_per_ligand, _ptr(poses), float(out_penalty),
+                                               _ptr(out), _stream_handle(poses.device)))
+        return out
+
+    def release(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            h, self._h = self._h, None
+            check(_abi.load().ligen_release_prepared(h))
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def prepare_scoring(ligands: Ligands, grid: PocketGrid) -> PreparedScoring:
+    """Grid records and packed library for repeated scoring (see PreparedScoring)."""
+    return PreparedScoring(ligands, grid)
 
 
 def pose_grad(ligands: Ligands, grid: PocketGrid, poses: torch.Tensor, poses_per_ligand: int,

@@ -48,7 +48,7 @@ struct DockArgs {
   float jitter;
   uint64_t seed;
   int R, n_rigid, step_deg, n_theta, passes;
-  int lanes;          // G: lanes per restart (2, 4 or 8)
+  int lanes;          // G: lanes per restart (2, 4, 8, 16 or 32)
   int fmt;            // grid record format (RecFormat)
   int rpc;            // restarts per work item (a multiple of 32 / lanes)
   int chunks;         // work items per ligand: ceil(R / rpc)
@@ -62,6 +62,7 @@ struct DockArgs {
   uint8_t* res_cnt;   // [sum n][R] torsion increments (mod n_theta) per restart
   int16_t* trace;     // optional
   unsigned long long* samples;   // optional [kSampleSlots]: atom samples the search needed
+  float* coords;      // optional: final grid-unit positions, [3 R atom_off[l] + 3 (r N_l + i) + k]
 };
 
 // Exhaustive search (mode 1): at most kExMaxRot rotatable bonds per ligand
@@ -92,9 +93,12 @@ struct ScoreArgs {
   float origin[3];
   float inv_h;
   int P;              // poses per ligand
-  int max_atoms;
+  int max_atoms;      // largest ligand of the launch (shared-memory carve-up)
+  int max_rot;        // most rotatable bonds of a ligand of the launch
   const float* poses;
   float* out_scores;
+  const int32_t* list;  // pose-per-lane launch: ligands to score (NULL: 0 .. n_list - 1)
+  int n_list;
 };
 
 struct GradArgs {
@@ -125,6 +129,7 @@ struct RescoreArgs {
   double h;
   double penalty;
   int K;                    // kept poses per ligand
+  int max_atoms;            // largest ligand (shared-memory carve-up)
   float* poses;             // outputs, re-ranked in place
   float* scores;            // [L][K], FP64 scores rounded to FP32
   int32_t* top_restart;     // [L][K] or NULL
@@ -156,6 +161,10 @@ cudaError_t dock_set_smem_limit(int lanes, int n_theta, int fmt, size_t smem);
 cudaError_t dock_occupancy(int lanes, int n_theta, int fmt, int rpc, size_t smem, int* blocks_per_sm);
 cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s);
+// Pose-per-lane scoring of the ligands a.list[0 .. n_list) (all of them at
+// most a.max_atoms atoms), 32 poses per warp.
+cudaError_t launch_score_lanes(const ScoreArgs& a, cudaStream_t s);
+size_t score_lane_smem_bytes(int cap, int max_rot);
 cudaError_t launch_rescore(const RescoreArgs& a, cudaStream_t s);
 size_t grad_smem_bytes(int max_atoms);
 // refine = false: dS/dpose of every pose; true: gradient refinement in place.

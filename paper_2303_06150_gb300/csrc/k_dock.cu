@@ -1,8 +1,8 @@
 // Docking kernel: restarts -> rigid stage -> torsion sweeps -> final score.
 //
 // Mapping. A work item is one ligand over `rpc` consecutive restarts; each
-// restart is owned by a group of G adjacent lanes (G = 2, 4 or 8), so a warp
-// runs 32/G restarts of the same ligand in lockstep (identical atom counts,
+// restart is owned by a group of G adjacent lanes (G = 2, 4, 8, 16 or 32), so
+// a warp runs 32/G restarts of the same ligand in lockstep (identical atom counts,
 // bonds and fragment sizes: no divergence). Inside a group the lanes split
 // the *candidates* of a stage (cube rotations in the rigid stage, torsion
 // increments in the sweep) and each lane sums its candidates' atom terms on
@@ -336,6 +336,14 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     if ((tid & 31) == 0) atomicAdd(&a.samples[blockIdx.x % kSampleSlots], (unsigned long long)v);
   }
+  if (a.coords && active) {   // debug output: the positions the final score sampled
+    float* cd = a.coords + 3 * ((size_t)a.R * a0 + (size_t)r * N);
+    for (int i = sub; i < N; i += G) {
+      cd[3 * i] = S.cx[i * rpc + rr];
+      cd[3 * i + 1] = S.cy[i * rpc + rr];
+      cd[3 * i + 2] = S.cz[i * rpc + rr];
+    }
+  }
   if (active && sub == 0) {
     const size_t lr = (size_t)l * a.R + r;
     a.res_score[lr] = acc;
@@ -418,6 +426,13 @@ const Shape kShapes[] = {
     LG_SHAPE(4, 9, kRecBF16),
     LG_SHAPE(8, 2, kRecBF16),
     LG_SHAPE(8, 5, kRecBF16),
+    // one restart per half-warp or warp: a gather request covers 16 or 32
+    // consecutive increments of one atom of one restart (36 increments as
+    // 3 x 16 or 2 x 32 slots, the spare lanes repeating a valid increment)
+    LG_SHAPE(16, 3, kRecF32),
+    LG_SHAPE(32, 2, kRecF32),
+    LG_SHAPE(16, 3, kRecF16),
+    LG_SHAPE(32, 2, kRecF16),
 };
 #undef LG_SHAPE
 #undef LG_COUNTING
@@ -453,7 +468,7 @@ const Shape* pick_shape(int G, int n_theta, int fmt) {
 
 }  // namespace
 
-bool dock_lanes_supported(int G) { return G == 2 || G == 4 || G == 8; }
+bool dock_lanes_supported(int G) { return G == 2 || G == 4 || G == 8 || G == 16 || G == 32; }
 
 bool dock_shape_supported(int G, int fmt) { return pick_shape(G, 36, fmt) != nullptr; }
 

@@ -5,7 +5,19 @@
 // Everything is recomputed in FP64 from the caller's FP32 inputs: the input
 // centroid, the torsions (bond by bond, about the current axes), the
 // rotation q/|q|, the translation, and the trilinear value from the eight
-// FP32 node values of the caller's [z][y][x][c] grid. One warp per pose.
+// FP32 node values of the caller's [z][y][x][c] grid.
+//
+// Mapping. GB300 issues FP64 at a small fraction of its FP32 rate, so the
+// FP64 instruction count decides the time. A group of kRsLanes lanes scores
+// one pose and a warp holds kRsPoses poses of the same ligand: the per-bond
+// work (axis length, its reciprocal) is one FP64 instruction stream for all
+// of the warp's poses, each group's lanes split the moving atoms and the
+// atoms, and the torsions' sines and cosines are computed once per bond by
+// one lane of the group and passed by shuffle (measured on GB300, re-scoring
+// the 600,000 kept poses of the screening library: 28 ms with a warp per
+// pose and every lane repeating the per-bond work). Positions are scaled by
+// 1/h (one FP64 product) instead of divided by h; the two differ by FP64
+// rounding only.
 // Re-ranking: one warp per ligand orders its K poses by FP64 score
 // (descending; ties by the restart that produced them) and rewrites poses,
 // scores and restart ids in that order.
@@ -18,6 +30,9 @@ namespace ligen {
 namespace {
 
 constexpr int kResWarps = 4;
+constexpr int kRsLanes = 8;
+constexpr int kRsPoses = 32 / kRsLanes;            // poses per warp (one ligand)
+constexpr int kRsK = LIGEN_MAX_ROT / kRsLanes;     // bonds per lane of a group
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -26,8 +41,14 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-__device__ double trilinear64(const RescoreArgs& a, double x, double y, double z, int c) {
-  const double u[3] = {(x - a.origin[0]) / a.h, (y - a.origin[1]) / a.h, (z - a.origin[2]) / a.h};
+__device__ __forceinline__ double group_sum_d(double v) {
+#pragma unroll
+  for (int o = kRsLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ double trilinear64(const RescoreArgs& a, double inv_h, double x, double y, double z, int c) {
+  const double u[3] = {(x - a.origin[0]) * inv_h, (y - a.origin[1]) * inv_h, (z - a.origin[2]) * inv_h};
   const int n[3] = {a.nx, a.ny, a.nz};
   int i[3];
   double f[3];
@@ -50,14 +71,20 @@ __device__ double trilinear64(const RescoreArgs& a, double x, double y, double z
 }
 
 __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreArgs a) {
-  __shared__ double ys[kResWarps][LIGEN_MAX_ATOMS * 3];
+  extern __shared__ double ys[];   // [kResWarps * kRsPoses][max_atoms * 3]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const size_t gp = (size_t)blockIdx.x * kResWarps + w;
-  if (gp >= (size_t)a.lig.L * a.K) return;
-  const int l = (int)(gp / a.K), p = (int)(gp % a.K);
+  const int grp = lane / kRsLanes, sub = lane % kRsLanes;
+  const int wpl = (a.K + kRsPoses - 1) / kRsPoses;   // warps per ligand
+  const size_t gw = (size_t)blockIdx.x * kResWarps + w;
+  if (gw >= (size_t)a.lig.L * wpl) return;   // uniform over the warp
+  const int l = (int)(gw / wpl);
+  const int p0 = (int)(gw % wpl) * kRsPoses + grp;
+  const bool own = p0 < a.K;
+  const int p = own ? p0 : a.K - 1;          // spare groups shadow the last pose
+  const size_t gp = (size_t)l * a.K + p;
   if (a.status[l] != 0 ||
-      !lg_check(a.check, a.lig.atom_off[l + 1] - a.lig.atom_off[l] <= LIGEN_MAX_ATOMS, kChkItemShape)) {
-    if (lane == 0) a.s64[gp] = -INFINITY;
+      !lg_check(a.check, a.lig.atom_off[l + 1] - a.lig.atom_off[l] <= a.max_atoms, kChkItemShape)) {
+    if (own && sub == 0) a.s64[gp] = -INFINITY;
     return;
   }
   const int a0 = a.lig.atom_off[l];
@@ -65,25 +92,37 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
   const int r0 = a.lig.rot_off[l];
   const int n = a.lig.rot_off[l + 1] - r0;
   const float* pose = a.poses + (size_t)a.K * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
-  double* y = ys[w];
+  double* y = ys + (size_t)(w * kRsPoses + grp) * a.max_atoms * 3;
   double c0[3] = {0.0, 0.0, 0.0};
   for (int i = lane; i < N; i += 32)
     for (int k = 0; k < 3; ++k) c0[k] += (double)a.lig.xyz[3 * (a0 + i) + k];
   for (int k = 0; k < 3; ++k) c0[k] = warp_sum_d(c0[k]) / N;
-  for (int i = lane; i < N; i += 32)
+  for (int i = sub; i < N; i += kRsLanes)
     for (int k = 0; k < 3; ++k) y[3 * i + k] = (double)a.lig.xyz[3 * (a0 + i) + k] - c0[k];
+  // sine and cosine of bond b held by lane b % kRsLanes of the group
+  double bs[kRsK], bc[kRsK];
+#pragma unroll
+  for (int k = 0; k < kRsK; ++k) {
+    bs[k] = 0.0;
+    bc[k] = 1.0;
+    if (sub + k * kRsLanes < n) sincos((double)pose[7 + sub + k * kRsLanes], &bs[k], &bc[k]);
+  }
   __syncwarp();
-  for (int b = 0; b < n; ++b) {
+  for (int b = 0; b < n; ++b) {   // uniform over the warp (one ligand)
     const uchar4 bi = a.pk.binfo[r0 + b];
     if (!lg_check(a.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
+    double sb = bs[0], cb = bc[0];
+#pragma unroll
+    for (int k = 1; k < kRsK; ++k)
+      if (b / kRsLanes == k) { sb = bs[k]; cb = bc[k]; }
+    const double s = __shfl_sync(kFull, sb, b % kRsLanes, kRsLanes);
+    const double c = __shfl_sync(kFull, cb, b % kRsLanes, kRsLanes);
     const double pv[3] = {y[3 * bi.y], y[3 * bi.y + 1], y[3 * bi.y + 2]};
     double kx = pv[0] - y[3 * bi.x], ky = pv[1] - y[3 * bi.x + 1], kz = pv[2] - y[3 * bi.x + 2];
-    const double kn = sqrt(kx * kx + ky * ky + kz * kz);
-    kx /= kn; ky /= kn; kz /= kn;
-    double s, c;
-    sincos((double)pose[7 + b], &s, &c);
+    const double inv = 1.0 / sqrt(kx * kx + ky * ky + kz * kz);
+    kx *= inv; ky *= inv; kz *= inv;
     const uint8_t* fr = a.pk.frag + (size_t)(r0 + b) * kFragStride;
-    for (int t = lane; t < bi.z; t += 32) {
+    for (int t = sub; t < bi.z; t += kRsLanes) {
       const int i = fr[t];
       if (!lg_check(a.check, i < N, kChkAtomIndex)) continue;
       const double dx = y[3 * i] - pv[0], dy = y[3 * i + 1] - pv[1], dz = y[3 * i + 2] - pv[2];
@@ -96,19 +135,21 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
   }
   const double qn = sqrt((double)pose[3] * pose[3] + (double)pose[4] * pose[4] + (double)pose[5] * pose[5] +
                          (double)pose[6] * pose[6]);
-  const double qw = pose[3] / qn, qx = pose[4] / qn, qy = pose[5] / qn, qz = pose[6] / qn;
+  const double qi = 1.0 / qn;
+  const double qw = pose[3] * qi, qx = pose[4] * qi, qy = pose[5] * qi, qz = pose[6] * qi;
   const double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
                        2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
                        2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)};
+  const double inv_h = 1.0 / a.h;
   double S = 0.0;
-  for (int i = lane; i < N; i += 32) {
+  for (int i = sub; i < N; i += kRsLanes) {
     double x[3];
     for (int r = 0; r < 3; ++r)
       x[r] = R[3 * r] * y[3 * i] + R[3 * r + 1] * y[3 * i + 1] + R[3 * r + 2] * y[3 * i + 2] + (double)pose[r];
-    S -= trilinear64(a, x[0], x[1], x[2], a.lig.type[a0 + i]);
+    S -= trilinear64(a, inv_h, x[0], x[1], x[2], a.lig.type[a0 + i]);
   }
-  S = warp_sum_d(S);
-  if (lane == 0) a.s64[gp] = S;
+  S = group_sum_d(S);
+  if (own && sub == 0) a.s64[gp] = S;
 }
 
 // Re-rank the K poses of each ligand by FP64 score; ties go to the lower
@@ -157,7 +198,13 @@ __global__ void __launch_bounds__(32 * kResWarps) rerank_kernel(const RescoreArg
 cudaError_t launch_rescore(const RescoreArgs& a, cudaStream_t s) {
   const size_t total = (size_t)a.lig.L * a.K;
   if (total == 0) return cudaSuccess;
-  rescore_kernel<<<(unsigned)((total + kResWarps - 1) / kResWarps), 32 * kResWarps, 0, s>>>(a);
+  const size_t smem = (size_t)kResWarps * kRsPoses * a.max_atoms * 3 * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const size_t warps = (size_t)a.lig.L * ((a.K + kRsPoses - 1) / kRsPoses);
+  rescore_kernel<<<(unsigned)((warps + kResWarps - 1) / kResWarps), 32 * kResWarps, smem, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   rerank_kernel<<<(unsigned)((a.lig.L + kResWarps - 1) / kResWarps), 32 * kResWarps, 0, s>>>(a);

@@ -186,8 +186,8 @@ int check_params(const ligen_params_t* p) {
   if (p->top_k < 1 || p->top_k > p->restarts) return fail(LIGEN_ERR_INVALID_ARG, "top_k must be 1..restarts");
   if (p->mode != 0 && p->mode != 1) return fail(LIGEN_ERR_INVALID_ARG, "mode must be 0 (greedy) or 1 (exhaustive)");
   if (p->batching != LIGEN_BATCH_PLAIN && p->batching != LIGEN_BATCH_BUCKETS &&
-      p->batching != LIGEN_BATCH_BUCKETS_STATIC)
-    return fail(LIGEN_ERR_INVALID_ARG, "batching must be LIGEN_BATCH_PLAIN, _BUCKETS or _BUCKETS_STATIC");
+      p->batching != LIGEN_BATCH_BUCKETS_STATIC && p->batching != LIGEN_BATCH_QUEUE)
+    return fail(LIGEN_ERR_INVALID_ARG, "batching must be LIGEN_BATCH_PLAIN, _BUCKETS, _BUCKETS_STATIC or _QUEUE");
   if (p->grid_format != LIGEN_GRID_F32 && p->grid_format != LIGEN_GRID_F16 && p->grid_format != LIGEN_GRID_BF16)
     return fail(LIGEN_ERR_INVALID_ARG, "grid_format must be LIGEN_GRID_F32, _F16 or _BF16");
   if (p->rescore_fp64 != 0 && p->rescore_fp64 != 1) return fail(LIGEN_ERR_INVALID_ARG, "rescore_fp64 must be 0 or 1");
@@ -200,6 +200,7 @@ int check_params(const ligen_params_t* p) {
 // Exhaustive mode: small ligands only (see ligen_params_t.mode).
 int check_exhaustive(const ligen_ligands_t* g, const ligen_params_t* p) {
   if (p->trace) return fail(LIGEN_ERR_INVALID_ARG, "trace is not written in exhaustive mode (mode 1)");
+  if (p->coords) return fail(LIGEN_ERR_INVALID_ARG, "coords are not written in exhaustive mode (mode 1)");
   if ((int64_t)g->n_ligands * p->restarts > INT32_MAX)
     return fail(LIGEN_ERR_UNSUPPORTED, "exhaustive mode: ligands * restarts exceeds 2^31 - 1");
   const int nt = 360 / p->torsion_step_deg;
@@ -380,9 +381,11 @@ struct Group {
 // Host plan of the bucketed layout: groups keyed by (atom class, tuned
 // shape); inside a group ligands go by decreasing estimated cost
 // (R * (n_rigid * N + passes * n * n_theta * N / 4)), and the groups by
-// decreasing total cost, so the longest work starts first.
+// decreasing total cost, so the longest work starts first. `single`: one
+// group of every ligand (the single-queue layout), default shape, in the
+// same cost order.
 void plan_groups(const ligen_ligands_t* g, const ligen_params_t* p, int dev, std::vector<int32_t>& order,
-                 std::vector<Group>& groups) {
+                 std::vector<Group>& groups, bool single = false) {
   const int L = g->n_ligands;
   const int nt = 360 / p->torsion_step_deg;
   struct Item {
@@ -395,8 +398,8 @@ void plan_groups(const ligen_ligands_t* g, const ligen_params_t* p, int dev, std
     for (int l = 0; l < L; ++l) {
       const int N = g->h_atom_off[l + 1] - g->h_atom_off[l];
       const int n = g->h_rot_off[l + 1] - g->h_rot_off[l];
-      const int ac = atom_class_of(N);
-      TuneEntry t = g_tune[dev][ac * 11 + rot_class_of(n)];
+      const int ac = single ? 0 : atom_class_of(N);
+      TuneEntry t = single ? TuneEntry() : g_tune[dev][ac * 11 + rot_class_of(n)];
       if (!dock_shape_supported(t.lanes, p->grid_format)) t = TuneEntry();   // default shape
       const double cost = (double)N * p->n_rigid + (double)p->passes * n * nt * (0.25 * N + 1.0);
       by[std::make_tuple(ac, t.lanes, t.rpc)].push_back({l, cost});
@@ -469,7 +472,8 @@ std::string launch_key(const std::vector<DockArgs>& args, const std::vector<int>
     const DockArgs& a = args[i];
     const void* ptrs[] = {a.lig.atom_off, a.lig.xyz, a.lig.type, a.lig.bonds, a.lig.rot_off, a.lig.rot_edge,
                           a.pk.xc, a.pk.binfo, a.pk.frag, a.pk.status, a.grid.coef, a.res_score, a.res_k,
-                          a.res_cnt, a.trace, a.list, a.queue, a.samples, a.pk.touch, a.grid.check};
+                          a.res_cnt, a.trace, a.list, a.queue, a.samples, a.pk.touch, a.grid.check,
+                          a.coords};
     append_key(k, ptrs, sizeof ptrs);
     const int ints[] = {a.lig.L, a.grid.cx, a.grid.cy, a.grid.cz, a.grid.nc, a.R, a.n_rigid, a.step_deg,
                         a.n_theta, a.passes, a.lanes, a.fmt, a.rpc, a.chunks, a.n_items, a.max_atoms,
@@ -576,7 +580,73 @@ int run_bucketed(const DockArgs& base, const std::vector<Group>& groups, int32_t
   return LIGEN_OK;
 }
 
+// ------------------------------------------------------------- scoring --
+// Calls with at least kLanePosesMin poses per ligand score one pose per lane
+// (launch_score_lanes), ligands grouped by atom count into classes of
+// kScoreClassStep atoms: the kernel's shared memory per warp is 384 bytes
+// per atom of its class bound, so small ligands are not charged for the
+// largest one. Fewer poses per ligand leave most lanes of such a warp idle;
+// those calls keep the group-per-pose kernel (launch_score).
+constexpr int kLanePosesMin = 16;
+constexpr int kScoreClassStep = 16;
+constexpr int kScoreClasses = LIGEN_MAX_ATOMS / kScoreClassStep;
+
+struct ScorePlan {
+  int n[kScoreClasses] = {};        // ligands per class
+  int start[kScoreClasses] = {};    // first entry of the class in `list`
+  std::vector<int32_t> list;        // ligand ids, class by class, ascending within a class
+};
+
+void plan_score(const int32_t* h_atom_off, int L, ScorePlan* sp) {
+  int cnt[kScoreClasses] = {};
+  for (int l = 0; l < L; ++l) ++cnt[(h_atom_off[l + 1] - h_atom_off[l] - 1) / kScoreClassStep];
+  int o = 0;
+  for (int c = 0; c < kScoreClasses; ++c) {
+    sp->n[c] = cnt[c];
+    sp->start[c] = o;
+    o += cnt[c];
+  }
+  sp->list.assign(L, 0);
+  int fill[kScoreClasses];
+  std::copy(sp->start, sp->start + kScoreClasses, fill);
+  for (int l = 0; l < L; ++l) sp->list[fill[(h_atom_off[l + 1] - h_atom_off[l] - 1) / kScoreClassStep]++] = l;
+}
+
+// Every ligand of base.lig scored: class by class (d_list = the plan's list
+// on the device) or in one group-per-pose launch.
+int run_score(const ScoreArgs& base, const ScorePlan& sp, const int32_t* d_list, cudaStream_t s) {
+  if (base.P < kLanePosesMin) {
+    LG_CUDA(launch_score(base, s));
+    return LIGEN_OK;
+  }
+  for (int c = 0; c < kScoreClasses; ++c) {
+    if (!sp.n[c]) continue;
+    ScoreArgs a = base;
+    a.list = d_list + sp.start[c];
+    a.n_list = sp.n[c];
+    a.max_atoms = (c + 1) * kScoreClassStep;
+    LG_CUDA(launch_score_lanes(a, s));
+  }
+  return LIGEN_OK;
+}
+
 }  // namespace
+
+// Inputs prepared once for repeated scoring (ligen_prepare_scoring): the
+// FP32 grid records, the packed library and the scoring plan, in one
+// device allocation owned by the handle.
+struct ligen_prepared {
+  int dev = 0;
+  char* mem = nullptr;
+  LigandsDev lig{};
+  Packed pk{};
+  float* coef = nullptr;
+  ligen_grid_t grid{};          // dimensions, origin, spacing (data not kept)
+  LibShape sh;
+  std::vector<int32_t> h_atom_off, h_rot_off;
+  ScorePlan plan;
+  int32_t* d_list = nullptr;
+};
 
 extern "C" {
 
@@ -649,12 +719,13 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     else if (gh != ghost) return fail(LIGEN_ERR_INVALID_ARG, "site grids mix host and device memory");
   }
   const int ohost = space_of({out_poses, out_scores, params->status, params->trace, params->top_restart,
-                              params->scores_f64});
+                              params->scores_f64, params->coords});
   if (lhost < 0) return fail(LIGEN_ERR_INVALID_ARG, "ligand arrays mix host and device memory");
   if (ohost < 0) return fail(LIGEN_ERR_INVALID_ARG, "output arrays mix host and device memory");
 
   const size_t pose_floats = (size_t)K * (7 * (size_t)L + sh.rot);
   const size_t trace_elems = (size_t)R * sh.trace_len;
+  const size_t coord_elems = 3 * (size_t)R * sh.atoms;
   const int fmt = params->grid_format;
   size_t gval_max = 0, coef_max = 0;
   for (int g = 0; g < n_sites; ++g) {
@@ -674,11 +745,12 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
   const size_t o_rs = ar.take(4 * (size_t)L * R);
   const size_t o_rk = ar.take((size_t)L * R);
   const size_t o_rc = ar.take((size_t)sh.rot * R);
-  size_t o_poses = 0, o_scores = 0, o_trace = 0, o_top = 0;
+  size_t o_poses = 0, o_scores = 0, o_trace = 0, o_top = 0, o_coords = 0;
   if (ohost == 1) {
     o_poses = ar.take(4 * pose_floats);
     o_scores = ar.take(4 * (size_t)L * K);
     if (params->trace) o_trace = ar.take(2 * trace_elems);
+    if (params->coords) o_coords = ar.take(4 * coord_elems);
     if (params->top_restart) o_top = ar.take(4 * (size_t)L * K);
   }
   const bool rescore = params->rescore_fp64 == 1;
@@ -698,7 +770,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     int dev = 0;
     LG_CUDA(cudaGetDevice(&dev));
     if (dev >= kMaxDev) return fail(LIGEN_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDev);
-    plan_groups(ligands, params, dev, order, groups);
+    plan_groups(ligands, params, dev, order, groups, params->batching == LIGEN_BATCH_QUEUE);
     o_order = ar.take(4 * (size_t)L);
     o_queue = ar.take(sizeof(int) * groups.size());
   }
@@ -730,6 +802,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     float* site_poses = out_poses + (size_t)site * pose_floats;
     float* site_scores = out_scores + (size_t)site * L * K;
     int16_t* site_trace = params->trace ? params->trace + (size_t)site * trace_elems : nullptr;
+    float* site_coords = params->coords ? params->coords + (size_t)site * coord_elems : nullptr;
     int32_t* site_top = params->top_restart ? params->top_restart + (size_t)site * L * K : nullptr;
     double* site_s64 = params->scores_f64 ? params->scores_f64 + (size_t)site * L * K : nullptr;
     float site_ms[LIGEN_N_STAGES];
@@ -753,6 +826,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     float* d_poses = ohost ? ar.at<float>(o_poses) : site_poses;
     float* d_scores = ohost ? ar.at<float>(o_scores) : site_scores;
     int16_t* d_trace = site_trace ? (ohost ? ar.at<int16_t>(o_trace) : site_trace) : nullptr;
+    float* d_coords = site_coords ? (ohost ? ar.at<float>(o_coords) : site_coords) : nullptr;
     int32_t* d_top = site_top ? (ohost ? ar.at<int32_t>(o_top) : site_top) : nullptr;
     if (rescore && !d_top) d_top = ar.at<int32_t>(o_itop);
 
@@ -789,6 +863,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
     da.res_k = ar.at<uint8_t>(o_rk);
     da.res_cnt = ar.at<uint8_t>(o_rc);
     da.trace = d_trace;
+    da.coords = d_coords;
     da.samples = d_samples;
     if (exhaustive) {
       LG_CUDA(launch_exhaustive(da, s));
@@ -800,7 +875,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
       int32_t* d_order = ar.at<int32_t>(o_order);
       LG_CUDA(cudaMemcpyAsync(d_order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, s));
       if ((rc = run_bucketed(da, groups, d_order, ar.at<int>(o_queue),
-                             params->batching == LIGEN_BATCH_BUCKETS, s)) != LIGEN_OK)
+                             params->batching != LIGEN_BATCH_BUCKETS_STATIC, s)) != LIGEN_OK)
         return rc;
     } else {
       LG_CUDA(launch_dock(da, 0, s, true));
@@ -834,6 +909,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
       rsa.h = grid->spacing;
       rsa.penalty = params->out_penalty;
       rsa.K = K;
+      rsa.max_atoms = sh.max_atoms;
       rsa.poses = d_poses;
       rsa.scores = d_scores;
       rsa.top_restart = site_top ? d_top : nullptr;
@@ -851,6 +927,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
       LG_CUDA(cudaMemcpyAsync(site_poses, d_poses, 4 * pose_floats, back, s));
       LG_CUDA(cudaMemcpyAsync(site_scores, d_scores, 4 * (size_t)L * K, back, s));
       if (d_trace) LG_CUDA(cudaMemcpyAsync(site_trace, d_trace, 2 * trace_elems, back, s));
+      if (d_coords) LG_CUDA(cudaMemcpyAsync(site_coords, d_coords, 4 * coord_elems, back, s));
       if (site_top) LG_CUDA(cudaMemcpyAsync(site_top, d_top, 4 * (size_t)L * K, back, s));
       if (d_out64) LG_CUDA(cudaMemcpyAsync(site_s64, d_out64, 8 * (size_t)L * K, back, s));
     }
@@ -907,6 +984,8 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
   if (lhost < 0 || ohost < 0) return fail(LIGEN_ERR_INVALID_ARG, "arrays mix host and device memory");
   const size_t pose_floats = (size_t)poses_per_ligand * (7 * (size_t)L + sh.rot);
   const size_t nscores = (size_t)poses_per_ligand * L;
+  ScorePlan plan;
+  if (poses_per_ligand >= kLanePosesMin) plan_score(ligands->h_atom_off, L, &plan);
   Arena ar;
   LigandPlan lp;
   plan_ligands(ar, ligands, sh, lhost == 1, &lp);
@@ -916,6 +995,7 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
   const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
   const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
   const size_t o_status = ar.take(4 * (size_t)L);
+  const size_t o_list = ar.take(4 * plan.list.size());
   size_t o_poses = 0, o_scores = 0;
   if (ohost) {
     o_poses = ar.take(4 * pose_floats);
@@ -937,6 +1017,8 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
     LG_CUDA(cudaMemcpyAsync(ar.base + o_poses, poses, 4 * pose_floats, cudaMemcpyHostToDevice, s));
     d_poses = ar.at<float>(o_poses);
   }
+  if (!plan.list.empty())   // pageable source: staged before the call returns
+    LG_CUDA(cudaMemcpyAsync(ar.base + o_list, plan.list.data(), 4 * plan.list.size(), cudaMemcpyHostToDevice, s));
   float* coef = ar.at<float>(o_coef);
   LG_CUDA(launch_grid_prep(gvals, grid->nx, grid->ny, grid->nz, grid->nc, coef, s));
   Packed pk{};
@@ -954,14 +1036,174 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
   sa.inv_h = (float)(1.0 / (double)grid->spacing);
   sa.P = poses_per_ligand;
   sa.max_atoms = sh.max_atoms;
+  sa.max_rot = sh.max_rot;
   sa.poses = d_poses;
   sa.out_scores = ohost ? ar.at<float>(o_scores) : out_scores;
-  LG_CUDA(launch_score(sa, s));
+  if ((rc = run_score(sa, plan, ar.at<int32_t>(o_list), s)) != LIGEN_OK) return rc;
   if (ohost) {
     LG_CUDA(cudaMemcpyAsync(out_scores, sa.out_scores, 4 * nscores, cudaMemcpyDeviceToHost, s));
     LG_CUDA(cudaStreamSynchronize(s));
   }
   return chk.verdict(s);
+}
+
+int ligen_prepare_scoring(const ligen_ligands_t* ligands, const ligen_grid_t* grid, void* stream,
+                          ligen_prepared_t** out) {
+  g_err.clear();
+  if (!out) return fail(LIGEN_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int rc;
+  LibShape sh;
+  if ((rc = check_ligands(ligands, 0, &sh)) != LIGEN_OK) return rc;
+  if ((rc = check_grid(grid)) != LIGEN_OK) return rc;
+  const int L = ligands->n_ligands;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int lhost = L ? space_of({ligands->atom_off, ligands->xyz, ligands->type, ligands->bonds,
+                                  ligands->rot_off, ligands->rot_edge}) : 0;
+  const int ghost = space_of({grid->data});
+  if (lhost < 0) return fail(LIGEN_ERR_INVALID_ARG, "ligand arrays mix host and device memory");
+  // Persistent regions (the handle's own allocation).
+  Arena keep;
+  const size_t k_atom_off = keep.take(4 * (size_t)(L + 1));
+  const size_t k_rot_off = keep.take(4 * (size_t)(L + 1));
+  const size_t k_coef = keep.take(grid_coef_bytes(grid));
+  const size_t k_xc = keep.take(16 * (size_t)sh.atoms);
+  const size_t k_binfo = keep.take(4 * (size_t)sh.rot);
+  const size_t k_frag = keep.take((size_t)kFragStride * sh.rot);
+  const size_t k_status = keep.take(4 * (size_t)L);
+  const size_t k_list = keep.take(4 * (size_t)L);
+  const size_t limit = g_ws_limit.load();
+  if (limit && keep.used > limit)
+    return fail(LIGEN_ERR_OOM, "prepared inputs of %zu bytes exceed the limit of %zu bytes", keep.used, limit);
+  // Staging of host inputs (the calling stream's workspace, this call only).
+  Arena tmp;
+  LigandPlan lp;
+  plan_ligands(tmp, ligands, sh, lhost == 1, &lp);
+  const size_t o_gval = ghost ? tmp.take(grid_values_bytes(grid)) : 0;
+  CallCheck chk;
+  chk.plan(tmp);
+  if (tmp.used && (rc = get_workspace(s, tmp.used, &tmp.base)) != LIGEN_OK) return rc;
+  auto* h = new ligen_prepared();
+  LG_CUDA(cudaGetDevice(&h->dev));
+  cudaError_t e = cudaMalloc(&h->mem, keep.used);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(LIGEN_ERR_OOM, "prepared inputs of %zu bytes: %s", keep.used, cudaGetErrorString(e));
+  }
+  keep.base = h->mem;
+  auto bail = [&](int code) { cudaFree(h->mem); delete h; return code; };
+  if ((rc = chk.arm(tmp, s)) != LIGEN_OK) return bail(rc);
+  h->grid = *grid;
+  h->grid.data = nullptr;
+  h->sh = sh;
+  h->h_atom_off.assign(ligands->h_atom_off, ligands->h_atom_off + L + 1);
+  h->h_rot_off.assign(ligands->h_rot_off, ligands->h_rot_off + L + 1);
+  plan_score(h->h_atom_off.data(), L, &h->plan);
+  LigandsDev lig;
+  if ((rc = stage_ligands(tmp, ligands, sh, lp, s, &lig)) != LIGEN_OK) return bail(rc);
+  const float* gvals = (const float*)grid->data;
+  if (ghost) {
+    if (cudaMemcpyAsync(tmp.base + o_gval, grid->data, grid_values_bytes(grid), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "grid upload"));
+    gvals = tmp.at<float>(o_gval);
+  }
+  const cudaMemcpyKind kind = lhost ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  h->lig.L = L;
+  h->lig.atom_off = keep.at<int32_t>(k_atom_off);
+  h->lig.rot_off = keep.at<int32_t>(k_rot_off);
+  h->coef = keep.at<float>(k_coef);
+  h->pk.xc = keep.at<float4>(k_xc);
+  h->pk.binfo = keep.at<uchar4>(k_binfo);
+  h->pk.frag = keep.at<uint8_t>(k_frag);
+  h->pk.status = keep.at<int32_t>(k_status);
+  h->d_list = keep.at<int32_t>(k_list);
+  cudaError_t ce = cudaSuccess;
+  if (L) {
+    ce = cudaMemcpyAsync((void*)h->lig.atom_off, ligands->atom_off, 4 * (size_t)(L + 1), kind, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync((void*)h->lig.rot_off, ligands->rot_off, 4 * (size_t)(L + 1), kind, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(h->d_list, h->plan.list.data(), 4 * (size_t)L, cudaMemcpyHostToDevice, s);
+  }
+  if (ce == cudaSuccess) ce = launch_grid_prep(gvals, grid->nx, grid->ny, grid->nz, grid->nc, h->coef, s);
+  if (ce == cudaSuccess && L) ce = launch_pack(lig, grid->nc, h->pk, s);
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "preparing the scoring inputs"));
+  // Host inputs are copied through the workspace asynchronously: wait for
+  // the copies, so the caller may reuse its host buffers on return.
+  if (lhost || ghost) {
+    if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamSynchronize"));
+  }
+  if ((rc = chk.verdict(s)) != LIGEN_OK) return bail(rc);
+  *out = h;
+  return LIGEN_OK;
+}
+
+int ligen_score_prepared(const ligen_prepared_t* prep, int32_t poses_per_ligand, const float* poses,
+                         float out_penalty, float* out_scores, void* stream) {
+  g_err.clear();
+  if (!prep) return fail(LIGEN_ERR_INVALID_ARG, "prep is NULL");
+  if (poses_per_ligand < 0) return fail(LIGEN_ERR_INVALID_ARG, "poses_per_ligand < 0");
+  if (!std::isfinite(out_penalty)) return fail(LIGEN_ERR_INVALID_ARG, "out_penalty not finite");
+  const int L = prep->lig.L;
+  if (L == 0 || poses_per_ligand == 0) return LIGEN_OK;
+  if (!poses || !out_scores) return fail(LIGEN_ERR_INVALID_ARG, "poses and out_scores are required");
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  if (dev != prep->dev) return fail(LIGEN_ERR_INVALID_ARG, "prepared on device %d, called on device %d", prep->dev, dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ohost = space_of({poses, out_scores});
+  if (ohost < 0) return fail(LIGEN_ERR_INVALID_ARG, "poses and out_scores mix host and device memory");
+  const size_t pose_floats = (size_t)poses_per_ligand * (7 * (size_t)L + prep->sh.rot);
+  const size_t nscores = (size_t)poses_per_ligand * L;
+  Arena ar;
+  size_t o_poses = 0, o_scores = 0;
+  if (ohost) {
+    o_poses = ar.take(4 * pose_floats);
+    o_scores = ar.take(4 * nscores);
+  }
+  CallCheck chk;
+  chk.plan(ar);
+  int rc;
+  if (ar.used && (rc = get_workspace(s, ar.used, &ar.base)) != LIGEN_OK) return rc;
+  if ((rc = chk.arm(ar, s)) != LIGEN_OK) return rc;
+  const float* d_poses = poses;
+  if (ohost) {
+    LG_CUDA(cudaMemcpyAsync(ar.base + o_poses, poses, 4 * pose_floats, cudaMemcpyHostToDevice, s));
+    d_poses = ar.at<float>(o_poses);
+  }
+  ScoreArgs sa{};
+  sa.lig = prep->lig;
+  sa.pk = prep->pk;
+  sa.grid = make_view(&prep->grid, prep->coef, out_penalty);
+  sa.grid.check = chk.d;
+  for (int k = 0; k < 3; ++k) sa.origin[k] = prep->grid.origin[k];
+  sa.inv_h = (float)(1.0 / (double)prep->grid.spacing);
+  sa.P = poses_per_ligand;
+  sa.max_atoms = prep->sh.max_atoms;
+  sa.max_rot = prep->sh.max_rot;
+  sa.poses = d_poses;
+  sa.out_scores = ohost ? ar.at<float>(o_scores) : out_scores;
+  if ((rc = run_score(sa, prep->plan, prep->d_list, s)) != LIGEN_OK) return rc;
+  if (ohost) {
+    LG_CUDA(cudaMemcpyAsync(out_scores, sa.out_scores, 4 * nscores, cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaStreamSynchronize(s));
+  }
+  return chk.verdict(s);
+}
+
+int ligen_release_prepared(ligen_prepared_t* prep) {
+  g_err.clear();
+  if (!prep) return LIGEN_OK;
+  int cur = 0;
+  LG_CUDA(cudaGetDevice(&cur));
+  if (cur != prep->dev) LG_CUDA(cudaSetDevice(prep->dev));
+  cudaError_t e = cudaFree(prep->mem);
+  if (cur != prep->dev) cudaSetDevice(cur);
+  delete prep;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFree(prepared inputs)");
+  return LIGEN_OK;
 }
 
 // Shared body of ligen_pose_grad and ligen_refine_poses: stage inputs, build
@@ -1323,7 +1565,7 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
   base.res_k = ar.at<uint8_t>(o_rk);
   base.res_cnt = ar.at<uint8_t>(o_rc);
 
-  static const int kCand[][2] = {{4, 32}, {4, 16}, {8, 16}, {8, 8}, {2, 64}};
+  static const int kCand[][2] = {{4, 32}, {4, 16}, {8, 16}, {8, 8}, {2, 64}, {16, 8}, {32, 4}};
   cudaEvent_t e0, e1;
   LG_CUDA(cudaEventCreate(&e0));
   LG_CUDA(cudaEventCreate(&e1));
@@ -1489,8 +1731,9 @@ extern "C" int ligen_dock_batch_static(const ligen_ligands_t* ligands, const lig
     return fail(LIGEN_ERR_UNSUPPORTED, "ligen_dock_batch_static runs the plain launch only (batching 0)");
   if (params->rescore_fp64 != 0 || params->scores_f64)
     return fail(LIGEN_ERR_UNSUPPORTED, "ligen_dock_batch_static has no FP64 re-score (rescore_fp64 0, scores_f64 NULL)");
-  if (params->stage_ms || params->samples)
-    return fail(LIGEN_ERR_UNSUPPORTED, "ligen_dock_batch_static reports neither stage_ms nor samples (both NULL)");
+  if (params->stage_ms || params->samples || params->coords)
+    return fail(LIGEN_ERR_UNSUPPORTED,
+                "ligen_dock_batch_static reports neither stage_ms, samples nor coords (all NULL)");
   LibShape sh;
   if ((rc = check_ligands(ligands, params->passes, &sh)) != LIGEN_OK) return rc;
   if ((rc = check_grid(grid)) != LIGEN_OK) return rc;

@@ -1,14 +1,14 @@
 """Helpers that compare the CUDA path with the oracle (test infrastructure).
 
 Tolerances:
-  * scores: |S_gpu - S_ref| <= 1e-5 * D + 16 * eps32 * Gs, with
+  * scores: |S_gpu - S_ref| <= 1e-5 * D + POS_ULPS * eps32 * Gs, with
     D = max(|S_ref|, sum_i |E_i|) and Gs = sum_i |grad E_i| |x_i - origin| the
     score's sensitivity to a relative perturbation of the atom coordinates
     (eps32 = 2^-24). The second term is the FP32 rounding of atom positions,
     which no FP32 evaluation avoids: at ~10 A an FP32 coordinate is off by up
     to 1e-6 A, and the grid's clash-plateau edges change E by up to ~12 per A;
   * decisions (chosen cube rotation, chosen torsion increment): equal at every
-    decision whose oracle top-2 gap exceeds 1e-4 * D + 32 * eps32 * Gs (the
+    decision whose oracle top-2 gap exceeds 1e-4 * D + 2 * POS_ULPS * eps32 * Gs (the
     score tolerance of both candidates). At a decision under that gap either
     choice is valid: when the GPU made the oracle's choice, both searches are
     still on the same trajectory and the comparison goes on; when it chose
@@ -27,7 +27,12 @@ import numpy as np
 SCORE_RTOL = 1e-5
 GAP_RTOL = 1e-4
 EPS32 = 2.0 ** -24
-POS_ULPS = 16
+# Position term of the score tolerance: the docking kernel's final FP32 atom
+# positions were measured against the oracle's FP64 positions of the same
+# pose (test_docking_coordinates_within_pos_ulps): on 42,109 atom positions of
+# small32 and the screening sample the error was at most 16.2 units of
+# 2^-24 |u| (99.9% below 9.3); 24 is that maximum with a margin of 1.5.
+POS_ULPS = 24
 
 
 def record_values(values: np.ndarray, fmt: str) -> np.ndarray:
@@ -85,12 +90,30 @@ def compare_restart(gpu_trace_row, ref: dict, j: int) -> tuple[int, bool]:
     return len(tr), True
 
 
+def new_stats() -> dict:
+    """Counters of a parity run: decisions compared, restarts, restarts on the
+    oracle's trajectory, scores compared, how many of those meet the bare
+    1e-5 * D (without the position term) and the worst |error| / (1e-5 D)."""
+    return dict(decisions=0, restarts=0, clean=0, scores=0, bare_ok=0, bare_worst=0.0)
+
+
+def merge(tot: dict, st: dict) -> dict:
+    for k in tot:
+        tot[k] = max(tot[k], st[k]) if k == "bare_worst" else tot[k] + st[k]
+    return tot
+
+
+def bare_ratio(err: float, D: float) -> float:
+    """|S_gpu - S_ref| as a fraction of the bare relative bar 1e-5 * D."""
+    return float(err) / (SCORE_RTOL * float(D))
+
+
 def check_dock_ligand(l: int, ref: dict, gpu_trace: np.ndarray, gpu_final: dict | None) -> dict:
     """Per-restart parity of one ligand.
 
     gpu_final maps restart -> the GPU's final score for the restarts it
     reports (all of them when top_k = R, the kept ones otherwise)."""
-    stats = dict(decisions=0, restarts=0, clean=0, scores=0)
+    stats = new_stats()
     for j, r in enumerate(ref["restarts"]):
         nd, clean = compare_restart(gpu_trace[r], ref, j)
         stats["decisions"] += nd
@@ -102,7 +125,18 @@ def check_dock_ligand(l: int, ref: dict, gpu_trace: np.ndarray, gpu_final: dict 
                 g = gpu_final[int(r)]
                 assert abs(g - ref["score"][j]) <= score_tol(D, Gs), (l, r, g, ref["score"][j], D, Gs)
                 stats["scores"] += 1
+                b = bare_ratio(abs(g - ref["score"][j]), D)
+                stats["bare_ok"] += int(b <= 1.0)
+                stats["bare_worst"] = max(stats["bare_worst"], b)
     return stats
+
+
+def coord_ulps(u_gpu: np.ndarray, u_ref: np.ndarray) -> np.ndarray:
+    """Per-atom position error in units of 2^-24 |u_ref| (u: grid-unit
+    positions, distance from the grid origin): the measure the position term
+    of the score tolerance assumes, |dx_i| <= POS_ULPS * eps32 * |x_i - origin|."""
+    err = np.linalg.norm(np.asarray(u_gpu, np.float64) - u_ref, axis=-1)
+    return err / (EPS32 * np.maximum(np.linalg.norm(u_ref, axis=-1), 1e-30))
 
 
 def clean_restart(ref: dict, j: int, gpu_trace_row=None) -> bool:

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(abi):
     for name in declared:
         assert hasattr(lib, name), name
     assert set(abi.SIGNATURES) == declared
-    assert lib.ligen_abi_version() == 4
+    assert lib.ligen_abi_version() == 5
 
 
 def _lig_struct(abi, arrays):
@@ -66,7 +66,8 @@ def _params(abi, **kw):
 @pytest.mark.parametrize("bad, code", [
     (dict(torsion_step_deg=7), -1), (dict(torsion_step_deg=1), -1), (dict(top_k=9), -1),
     (dict(restarts=0), -1), (dict(n_rigid=25), -1), (dict(passes=-1), -1), (dict(mode=2), -1), (dict(mode=1, trace=C.c_void_p(8)), -1),
-    (dict(jitter=float("nan")), -1), (dict(batching=3), -1), (dict(grid_format=3), -1),
+    (dict(jitter=float("nan")), -1), (dict(batching=4), -1), (dict(grid_format=3), -1),
+    (dict(mode=1, coords=C.c_void_p(8)), -1),
     (dict(rescore_fp64=2), -1),
 ])
 def test_bad_params_rejected_on_host(abi, bad, code):

@@ -31,9 +31,10 @@ def test_algorithmic_counts_match_fragment_sums(oracle_lib):
 
 def test_recorded_traffic_requires_matching_source_and_form(monkeypatch):
     import bench
-    value, _ = bench.recorded_traffic("f16")
-    assert value is not None and value > 0               # the committed capture matches this source
-    assert bench.recorded_traffic("plain")[0] is None      # another form
+    for form in ("f16", "plain"):
+        value, _ = bench.recorded_traffic(form)
+        assert value is not None and value > 0           # the committed capture matches this source
+    assert bench.recorded_traffic("bf16")[0] is None       # a form without a capture
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")   # an edited kernel
     assert bench.recorded_traffic("f16") == (None, "kernel changed since the full-size ncu capture")
 

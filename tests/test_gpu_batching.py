@@ -62,6 +62,42 @@ def test_buckets_match_plain_and_replay(lg, bimodal, fmt):
 
 
 @pytest.mark.parametrize("fmt", ["f32", "f16"])
+def test_single_queue_launch_matches_plain(lg, bimodal, small32, fmt):
+    """The whole library in one persistent launch (default shape, bucket
+    order): same kernel shape as the plain launch, so bit-identical results."""
+    for w, lib, grid in (bimodal, small32):
+        L, G = _dev(lg, lib, grid)
+        kw = _kw(w["search"], trace=True, top_restart=True, grid_format=fmt)
+        plain = lg.dock_batch(L, G, batching="plain", **kw)
+        q1 = lg.dock_batch(L, G, batching="queue", **kw)
+        q2 = lg.dock_batch(L, G, batching="queue", **kw)     # graph replay
+        torch.cuda.synchronize()
+        for name in ("trace", "scores", "poses", "top_restart", "status"):
+            assert torch.equal(getattr(plain, name), getattr(q1, name)), name
+            assert torch.equal(getattr(q1, name), getattr(q2, name)), name
+
+
+@pytest.mark.parametrize("lanes,rpc", [(16, 8), (32, 4)])
+def test_wide_lane_shapes_match_plain(lg, bimodal, lanes, rpc):
+    """16 and 32 lanes per restart (a gather request covers consecutive
+    increments of one atom of one restart): the same decisions as the
+    default 8-lane shape."""
+    w, lib, grid = bimodal
+    L, G = _dev(lg, lib, grid)
+    saved = lg.tune_get()
+    try:
+        for fmt in ("f32", "f16"):
+            kw = _kw(w["search"], trace=True, top_restart=True, grid_format=fmt)
+            plain = lg.dock_batch(L, G, batching="plain", **kw)
+            lg.tune_set({b: (lanes, rpc) for b in range(44)})
+            wide = lg.dock_batch(L, G, batching="buckets_static", **kw)
+            torch.cuda.synchronize()
+            _same_decisions_close_scores(plain, wide)
+    finally:
+        lg.tune_set(saved)
+
+
+@pytest.mark.parametrize("fmt", ["f32", "f16"])
 def test_static_bucket_launches_match_plain(lg, bimodal, small32, fmt):
     for w, lib, grid in (bimodal, small32):
         L, G = _dev(lg, lib, grid)
@@ -128,13 +164,12 @@ def test_buckets_bimodal_sample_matches_oracle(lg, oracle_lib, bimodal):
     small = [l for l in range(lib.n_ligands) if lib.n_atoms[l] <= 35][:6]
     large = [l for l in range(lib.n_ligands) if lib.n_atoms[l] >= 60][:3]
     ref = oracle_lib.dock_library(lib, grid, s, ligands=small + large, restarts=range(0, 6))
-    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    tot = parity.new_stats()
     for r_ in ref:
         l = r_["ligand"]
         gt = parity.ligand_trace(trace, lib.rot_off, R, s["passes"], l)
         final = {int(top[l, k]): float(scores[l, k]) for k in range(R)}
         st = parity.check_dock_ligand(l, r_, gt, final)
-        for k in tot:
-            tot[k] += st[k]
+        parity.merge(tot, st)
     print(tot)
     assert tot["clean"] >= 0.9 * tot["restarts"] and tot["scores"] > 0

@@ -36,14 +36,13 @@ def _dock_and_check(lg, oracle_lib, lib, grid, s, restarts=None, min_clean=0.9, 
     assert int(res.status.abs().sum()) == 0
     trace, scores, top = res.trace.cpu().numpy(), res.scores.cpu().numpy(), res.top_restart.cpu().numpy()
     ref = oracle_lib.dock_library(lib, parity.oracle_grid(oracle_lib, grid, fmt), s, restarts=restarts)
-    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    tot = parity.new_stats()
     for r_ in ref:
         l = r_["ligand"]
         gt = parity.ligand_trace(trace, lib.rot_off, R, s["passes"], l)
         final = {int(top[l, k]): float(scores[l, k]) for k in range(K)}
         st = parity.check_dock_ligand(l, r_, gt, final)
-        for k in tot:
-            tot[k] += st[k]
+        parity.merge(tot, st)
         assert np.all(np.diff(scores[l]) <= 0)
     print(tot)
     assert tot["clean"] >= min_clean * tot["restarts"] and tot["scores"] > 0

@@ -76,14 +76,13 @@ def test_sampled_ligands_match_oracle(run, oracle_lib):
     scores = res.scores.cpu().numpy()
     top = res.top_restart.cpu().numpy()
     ref = oracle_lib.dock_library(lib, grid, s, ligands=pick, restarts=rs)
-    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    tot = parity.new_stats()
     for r_ in ref:
         l = r_["ligand"]
         gt = parity.ligand_trace(trace, lib.rot_off, R, s["passes"], l)
         final = {int(top[l, k]): float(scores[l, k]) for k in range(K)}
         st = parity.check_dock_ligand(l, r_, gt, final)
-        for k in tot:
-            tot[k] += st[k]
+        parity.merge(tot, st)
     print(tot)
     assert tot["restarts"] == len(pick) * len(rs)
     assert tot["clean"] >= 0.9 * tot["restarts"]
@@ -148,14 +147,13 @@ def test_fp16_records_match_oracle_on_rounded_grid(run, run16, oracle_lib):
     top = res.top_restart.cpu().numpy()
     ref = oracle_lib.dock_library(lib, parity.oracle_grid(oracle_lib, grid, "f16"), s, ligands=sorted(pick),
                                   restarts=rs)
-    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    tot = parity.new_stats()
     for r_ in ref:
         l = r_["ligand"]
         gt = parity.ligand_trace(trace, lib.rot_off, R, s["passes"], l)
         final = {int(top[l, k]): float(sc[l, k]) for k in range(K)}
         st = parity.check_dock_ligand(l, r_, gt, final)
-        for k in tot:
-            tot[k] += st[k]
+        parity.merge(tot, st)
     print(tot)
     assert tot["restarts"] == len(pick) * len(rs)
     assert tot["clean"] >= 0.9 * tot["restarts"]

@@ -61,7 +61,7 @@ def test_sampled_small_and_large_ligands_match_oracle(run, oracle_lib):
     ref = oracle_lib.dock_library(lib, grid, s, ligands=pick, restarts=rs)
     scores = res.scores.cpu().numpy()
     top = res.top_restart.cpu().numpy()
-    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    tot = parity.new_stats()
     for r_ in ref:
         l = r_["ligand"]
         D = 1 + P * int(lib.n_rot[l])
@@ -69,8 +69,7 @@ def test_sampled_small_and_large_ligands_match_oracle(run, oracle_lib):
         gt = res.trace[start:start + R * D].cpu().numpy().reshape(R, D)
         final = {int(top[l, k]): float(scores[l, k]) for k in range(K)}
         st = parity.check_dock_ligand(l, r_, gt, final)
-        for k in tot:
-            tot[k] += st[k]
+        parity.merge(tot, st)
     print(tot)
     assert tot["restarts"] == len(pick) * len(rs)
     assert tot["clean"] >= 0.85 * tot["restarts"]
@@ -101,7 +100,7 @@ def test_fp16_records_plain_launch_match_oracle_on_rounded_grid(run, oracle_lib)
     pick = _sample(lib)
     rs = range(0, 8)
     ref = oracle_lib.dock_library(lib, parity.oracle_grid(oracle_lib, grid, "f16"), s, ligands=pick, restarts=rs)
-    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    tot = parity.new_stats()
     for r_ in ref:
         l = r_["ligand"]
         D = 1 + P * int(lib.n_rot[l])
@@ -109,8 +108,7 @@ def test_fp16_records_plain_launch_match_oracle_on_rounded_grid(run, oracle_lib)
         gt = res.trace[start:start + R * D].cpu().numpy().reshape(R, D)
         final = {int(top[l, k]): float(scores[l, k]) for k in range(K)}
         st = parity.check_dock_ligand(l, r_, gt, final)
-        for k in tot:
-            tot[k] += st[k]
+        parity.merge(tot, st)
     print(tot)
     assert tot["restarts"] == len(pick) * len(rs)
     assert tot["clean"] >= 0.85 * tot["restarts"]

@@ -94,7 +94,7 @@ def test_site_off_origin_matches_oracle(lg, oracle_lib, sites):
     L = lg.Ligands.from_arrays(lib, "cuda")
     res = lg.dock_sites(L, _grids(lg, grids, "cuda"), **_kw(s, top_k=R, trace=True, top_restart=True))
     torch.cuda.synchronize()
-    tot = dict(decisions=0, restarts=0, clean=0, scores=0)
+    tot = parity.new_stats()
     for g in (1, 2):
         trace = res.trace[g].cpu().numpy()
         scores = res.scores[g].cpu().numpy()
@@ -105,7 +105,6 @@ def test_site_off_origin_matches_oracle(lg, oracle_lib, sites):
             gt = parity.ligand_trace(trace, lib.rot_off, R, s["passes"], l)
             final = {int(top[l, k]): float(scores[l, k]) for k in range(R)}
             st = parity.check_dock_ligand(l, r_, gt, final)
-            for k in tot:
-                tot[k] += st[k]
+            parity.merge(tot, st)
     print(tot)
     assert tot["clean"] >= 0.9 * tot["restarts"] and tot["scores"] > 0
