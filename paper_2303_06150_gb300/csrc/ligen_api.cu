@@ -582,14 +582,20 @@ int run_bucketed(const DockArgs& base, const std::vector<Group>& groups, int32_t
 
 // ------------------------------------------------------------- scoring --
 // Calls with at least kLanePosesMin poses per ligand score one pose per lane
-// (launch_score_lanes), ligands grouped by atom count into classes of
-// kScoreClassStep atoms: the kernel's shared memory per warp is 384 bytes
-// per atom of its class bound, so small ligands are not charged for the
-// largest one. Fewer poses per ligand leave most lanes of such a warp idle;
-// those calls keep the group-per-pose kernel (launch_score).
+// (launch_score_lanes), ligands grouped by rotatable-bond count: that
+// kernel keeps n + 1 rigid transforms per lane (1.5 KB per warp each) in
+// shared memory, so ligands with few bonds are not charged for the most
+// flexible one. Fewer poses per ligand leave most lanes of such a warp
+// idle; those calls keep the group-per-pose kernel (launch_score).
 constexpr int kLanePosesMin = 16;
-constexpr int kScoreClassStep = 16;
-constexpr int kScoreClasses = LIGEN_MAX_ATOMS / kScoreClassStep;
+constexpr int kScoreClasses = 9;
+constexpr int kScoreRotCap[kScoreClasses] = {0, 2, 4, 6, 8, 12, 16, 24, 32};
+
+int score_class_of(int n) {
+  int c = 0;
+  while (c + 1 < kScoreClasses && n > kScoreRotCap[c]) ++c;
+  return c;
+}
 
 struct ScorePlan {
   int n[kScoreClasses] = {};        // ligands per class
@@ -597,9 +603,9 @@ struct ScorePlan {
   std::vector<int32_t> list;        // ligand ids, class by class, ascending within a class
 };
 
-void plan_score(const int32_t* h_atom_off, int L, ScorePlan* sp) {
+void plan_score(const int32_t* h_rot_off, int L, ScorePlan* sp) {
   int cnt[kScoreClasses] = {};
-  for (int l = 0; l < L; ++l) ++cnt[(h_atom_off[l + 1] - h_atom_off[l] - 1) / kScoreClassStep];
+  for (int l = 0; l < L; ++l) ++cnt[score_class_of(h_rot_off[l + 1] - h_rot_off[l])];
   int o = 0;
   for (int c = 0; c < kScoreClasses; ++c) {
     sp->n[c] = cnt[c];
@@ -609,11 +615,12 @@ void plan_score(const int32_t* h_atom_off, int L, ScorePlan* sp) {
   sp->list.assign(L, 0);
   int fill[kScoreClasses];
   std::copy(sp->start, sp->start + kScoreClasses, fill);
-  for (int l = 0; l < L; ++l) sp->list[fill[(h_atom_off[l + 1] - h_atom_off[l] - 1) / kScoreClassStep]++] = l;
+  for (int l = 0; l < L; ++l) sp->list[fill[score_class_of(h_rot_off[l + 1] - h_rot_off[l])]++] = l;
 }
 
 // Every ligand of base.lig scored: class by class (d_list = the plan's list
-// on the device) or in one group-per-pose launch.
+// on the device; base.max_atoms the call's largest ligand) or in one
+// group-per-pose launch.
 int run_score(const ScoreArgs& base, const ScorePlan& sp, const int32_t* d_list, cudaStream_t s) {
   if (base.P < kLanePosesMin) {
     LG_CUDA(launch_score(base, s));
@@ -624,7 +631,7 @@ int run_score(const ScoreArgs& base, const ScorePlan& sp, const int32_t* d_list,
     ScoreArgs a = base;
     a.list = d_list + sp.start[c];
     a.n_list = sp.n[c];
-    a.max_atoms = (c + 1) * kScoreClassStep;
+    a.max_rot = kScoreRotCap[c];
     LG_CUDA(launch_score_lanes(a, s));
   }
   return LIGEN_OK;
@@ -985,7 +992,7 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
   const size_t pose_floats = (size_t)poses_per_ligand * (7 * (size_t)L + sh.rot);
   const size_t nscores = (size_t)poses_per_ligand * L;
   ScorePlan plan;
-  if (poses_per_ligand >= kLanePosesMin) plan_score(ligands->h_atom_off, L, &plan);
+  if (poses_per_ligand >= kLanePosesMin) plan_score(ligands->h_rot_off, L, &plan);
   Arena ar;
   LigandPlan lp;
   plan_ligands(ar, ligands, sh, lhost == 1, &lp);
@@ -1099,7 +1106,7 @@ int ligen_prepare_scoring(const ligen_ligands_t* ligands, const ligen_grid_t* gr
   h->sh = sh;
   h->h_atom_off.assign(ligands->h_atom_off, ligands->h_atom_off + L + 1);
   h->h_rot_off.assign(ligands->h_rot_off, ligands->h_rot_off + L + 1);
-  plan_score(h->h_atom_off.data(), L, &h->plan);
+  plan_score(h->h_rot_off.data(), L, &h->plan);
   LigandsDev lig;
   if ((rc = stage_ligands(tmp, ligands, sh, lp, s, &lig)) != LIGEN_OK) return bail(rc);
   const float* gvals = (const float*)grid->data;
