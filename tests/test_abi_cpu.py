@@ -135,6 +135,14 @@ def test_null_structs_rejected(abi):
     assert lib.ligen_autotune(None, None, None, 1, None, None, None) == -1
     assert lib.ligen_probe_stream(None, 16, 1, None, None, None, None) == -1
     assert lib.ligen_set_workspace_limit(1 << 20) == 0 and lib.ligen_set_workspace_limit(0) == 0
+    h = C.c_void_p()
+    assert lib.ligen_prepare_scoring(None, None, None, None) == -1           # no output handle
+    assert lib.ligen_prepare_scoring(None, None, None, C.byref(h)) == -1 and h.value is None
+    assert lib.ligen_score_prepared(None, 30, None, 5.0, None, None) == -1
+    assert lib.ligen_release_prepared(None) == 0
+    # shapes beyond 128 threads, off the warp's restart multiple or of an unsupported width
+    assert lib.ligen_tune_set(0, 32, 8) == -1 and lib.ligen_tune_set(0, 16, 9) == -1
+    assert lib.ligen_tune_set(0, 64, 2) == -1
 
 
 def test_package_refuses_to_load_without_library(tmp_path):

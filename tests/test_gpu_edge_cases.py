@@ -99,3 +99,59 @@ def test_single_cell_grid(lg, oracle_lib, small32, fmt):
     s = dict(w["search"], restarts=8, top_k=8, jitter=0.3)
     sub = lib.subset(range(0, 8))
     _dock_and_check(lg, oracle_lib, sub, grid, s, fmt=fmt)
+
+
+@pytest.mark.parametrize("P", [15, 16, 33])    # group-per-pose kernel, then one pose per lane (1 and 2 warps)
+def test_scoring_at_maximum_sizes(lg, oracle_lib, P):
+    """ligen_score_poses and the prepared form on 256-atom, 32-bond ligands
+    (the largest shared-memory carve-ups of both scoring kernels) plus a
+    rigid and a one-atom ligand, against the oracle; the FP64 re-score of
+    docked poses of the same ligands (its largest carve-up) against the
+    oracle's FP64 score of the same poses."""
+    spec = dict(kind="uniform", n_ligands=2, n_atoms=(256, 256), n_rot=(32, 32), n_types=8, seed=12)
+    big = gen.make_library(spec)
+    one = dict(xyz=np.zeros((1, 3)), type=np.array([1], np.uint8), bonds=np.zeros((0, 2), np.int32),
+               rot_edge=np.zeros(0, np.int32))
+    rigid = dict(big.ligand(0), rot_edge=np.zeros(0, np.int32))
+    lib = gen.from_ligands([big.ligand(0), one, rigid, big.ligand(1)])
+    grid = gen.make_grid(gen.WORKLOADS["screen20k"]["grid"])
+    rng = np.random.default_rng(13)
+    poses = []
+    for l in range(lib.n_ligands):
+        for _ in range(P):
+            poses.append(np.concatenate([grid.center + rng.uniform(-3, 3, 3), rng.normal(size=4),
+                                         rng.uniform(-np.pi, np.pi, lib.n_rot[l])]))
+    poses = np.concatenate(poses).astype(np.float32)
+    L = lg.Ligands.from_arrays(lib, "cuda")
+    G = lg.PocketGrid.from_array(grid.values, grid.origin, grid.spacing, "cuda")
+    pt = torch.tensor(poses, device="cuda")
+    out = lg.score_poses(L, G, pt, P).cpu().numpy()
+    prep = lg.prepare_scoring(L, G)
+    assert np.array_equal(prep.score(pt, P).cpu().numpy(), out)
+    prep.release()
+    og = oracle_lib.OGrid.from_grid(grid)
+    off = lg.pose_offsets(lib.rot_off, P)
+    for l in range(lib.n_ligands):
+        lig = oracle_lib.OLigand.from_library(lib, l)
+        Pl = poses[off[l]:off[l + 1]].astype(np.float64).reshape(P, -1)
+        for p in range(0, P, 4):
+            S, D, _, Gs = oracle_lib.score_pose(lig, og, Pl[p], 5.0, sensitivity=True)
+            assert abs(out[l, p] - S) <= parity.score_tol(D, Gs), (l, p, out[l, p], S)
+    if P == 16:   # FP64 re-score of docked poses of the same ligands
+        s = dict(gen.WORKLOADS["screen20k"]["search"], restarts=16, top_k=16, passes=1, torsion_step_deg=60)
+        res = lg.dock_batch(L, G, restarts=16, torsion_step_deg=60, passes=1, top_k=16, seed=s["seed"],
+                            rescore_fp64=True)
+        s64 = res.scores_f64.cpu().numpy()
+        dp = res.poses.cpu().numpy()
+        o32 = oracle_lib.OGrid(np.asarray(grid.values, np.float32).astype(np.float64), grid.origin, grid.spacing)
+        offk = lg.pose_offsets(lib.rot_off, 16)
+        xyz32 = np.asarray(lib.xyz, np.float32).astype(np.float64)
+        for l in range(lib.n_ligands):
+            g = lib.ligand(l)
+            lig32 = oracle_lib.OLigand(xyz32[lib.atom_off[l]:lib.atom_off[l + 1]], g["type"], g["bonds"],
+                                       g["rot_edge"])
+            Pl = dp[offk[l]:offk[l + 1]].astype(np.float64).reshape(16, -1)
+            for k in range(0, 16, 5):
+                S, D, _ = oracle_lib.score_pose(lig32, o32, Pl[k], 5.0)
+                assert abs(s64[l, k] - S) <= 1e-9 * D, (l, k, s64[l, k], S)
+            assert np.all(np.diff(s64[l]) <= 0)
