@@ -117,6 +117,10 @@ struct GradArgs {
   float step_t, step_q, step_theta;
   float box_lo[3], box_hi[3];
   int8_t* out_accept;       // refinement: [L * P][steps], optional
+  const int32_t* list;      // pose-group launch: ligands (NULL: 0 .. n_list - 1)
+  int n_list;
+  int max_rot;              // pose-group launch: most rotatable bonds of a ligand of the launch
+  float h;                  // grid spacing (Angstrom)
 };
 
 struct RescoreArgs {
@@ -169,6 +173,11 @@ cudaError_t launch_rescore(const RescoreArgs& a, cudaStream_t s);
 size_t grad_smem_bytes(int max_atoms);
 // refine = false: dS/dpose of every pose; true: gradient refinement in place.
 cudaError_t launch_grad(const GradArgs& a, bool refine, cudaStream_t s);
+// The same on forward kinematics, a group of lanes per pose, for the ligands
+// a.list[0 .. n_list) (at most a.max_atoms atoms and a.max_rot bonds each);
+// calls with at least kGradLanePosesMin poses per ligand.
+constexpr int kGradLanePosesMin = 4;
+cudaError_t launch_grad_lanes(const GradArgs& a, bool refine, cudaStream_t s);
 cudaError_t launch_probe(const float* rec, uint32_t n_rec, int bytes, int iters, uint64_t seed, float* sink,
                          int blocks, cudaStream_t s);
 int probe_streams();

@@ -30,6 +30,7 @@
 #include <cmath>
 
 #include "../../include/ligen.h"
+#include "fk_pose.cuh"
 #include "internal.h"
 #include "pose_build.cuh"
 
@@ -320,7 +321,305 @@ __global__ void __launch_bounds__(32 * kGradWarps, 6) refine_kernel(const GradAr
   }
 }
 
+// --------------------------------------------------------------------------
+// Pose-group gradients and refinement on forward kinematics (fk_pose.cuh).
+//
+// One warp per (ligand, PW poses), a group of G = 32 / PW lanes per pose. A
+// pose's n + 1 transforms are built once, by the group's first lane, into
+// shared memory [slot][pose][12]; each lane of the group then takes atoms
+// sub, sub + G, ... : position u = T_owner x (grid units), value and
+// gradient of the cell polynomial, du = dS/du. Per lane it accumulates
+//   dS/dt contribution  sum du,
+//   the rotation term   Gp = sum du (x - t)^T   (x the position in A),
+//   per owner bond b    F_b = sum du,  tau_b = sum u x du.
+// The bond sums become subtree sums (children added into parents, in
+// reverse bond order), so F_b and tau_b cover b's whole moving side, and
+//   dS/dtheta_b = w_b . (tau_b - u_v x F_b)
+// with w_b the unit axis and u_v the axis point of bond b in the pose, from
+// the parent's transform (torsions commute, so theta_b may be taken as the
+// last rotation); dS/dq through q/|q| from Gy = Gp R (y = R^T (x - t) the
+// body coordinates), as in the group kernel above. Nothing is stored between
+// evaluations but the pose, its gradient and the transforms.
+//
+// Refinement runs the group kernel's steps (normalised-step projected
+// ascent, keep if S rises, else halve) per pose, the group's first lane
+// doing the per-pose scalar work.
+
+template <int G>
+struct GL {
+  static constexpr int PW = 32 / G;   // poses per warp
+};
+
+// Shared memory of one warp: transforms [ncap + 1][PW][12]; per-lane bond
+// sums [ncap][32][6]; pose state [4][PW][7 + ncap] (pose, candidate, two
+// gradients); then the staged ligand.
+template <int G>
+__host__ __device__ inline size_t gl_carve(int acap, int ncap, unsigned char* base, FkLigand* S, float** T,
+                                           float** acc, float** st) {
+  constexpr int PW = GL<G>::PW;
+  const size_t tb = (size_t)(ncap + 1) * PW * 12 * sizeof(float);
+  const size_t ab = (size_t)ncap * 32 * 6 * sizeof(float);
+  const size_t sb = ((size_t)4 * PW * (7 + ncap) * sizeof(float) + 15) & ~(size_t)15;
+  if (base) {
+    *T = (float*)base;
+    *acc = (float*)(base + tb);
+    *st = (float*)(base + tb + ab);
+  }
+  return tb + ab + sb + fk_ligand_carve(acap, ncap, base ? base + tb + ab + sb : nullptr, S);
+}
+
+__device__ __forceinline__ float gl_sum(float v, int G) {
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// S of `pose` (7 + n floats, shared by the group) and dS/dpose into `grad`
+// (written by the group's first lane). Every lane of the group returns S.
+// All lanes of the warp call it.
+template <int G>
+__device__ float gl_eval(const GradArgs& a, const FkLigand& S, int N, int n, const float* pose, float* grad,
+                         float* T, float* acc, int grp, int sub, int lane) {
+  constexpr int PW = GL<G>::PW;
+  const float rqn = rsqrtf(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
+  const Quat q = {pose[3] * rqn, pose[4] * rqn, pose[5] * rqn, pose[6] * rqn};
+  if (sub == 0) fk_transforms(S, n, pose, q, pose + 7, a.origin, a.inv_h, T + 12 * grp, (size_t)PW * 12);
+  for (int b = 0; b < n; ++b)
+#pragma unroll
+    for (int e = 0; e < 6; ++e) acc[((size_t)b * 32 + lane) * 6 + e] = 0.f;
+  __syncwarp();
+  const float d0[3] = {a.origin[0] - pose[0], a.origin[1] - pose[1], a.origin[2] - pose[2]};
+  float Sl = 0.f, gs[3] = {0.f, 0.f, 0.f}, Gp[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) Gp[e] = 0.f;
+  for (int i = sub; i < N; i += G) {
+    const float4 X = S.sx[i];
+    const int o = S.own[i];
+    float4 m0, m1, m2;
+    fk_get(T + ((size_t)o * PW + grp) * 12, m0, m1, m2);
+    const float u[3] = {fmaf(m0.x, X.x, fmaf(m0.y, X.y, fmaf(m0.z, X.z, m0.w))),
+                        fmaf(m1.x, X.x, fmaf(m1.y, X.y, fmaf(m1.z, X.z, m1.w))),
+                        fmaf(m2.x, X.x, fmaf(m2.y, X.y, fmaf(m2.z, X.z, m2.w)))};
+    float gx, gy, gz;
+    Sl -= grid_sample_grad(a.grid, u[0], u[1], u[2], __float_as_int(X.w), &gx, &gy, &gz);
+    const float du[3] = {-gx, -gy, -gz};   // dS/du, per grid unit
+#pragma unroll
+    for (int r = 0; r < 3; ++r) gs[r] += du[r];
+    const float dv[3] = {fmaf(a.h, u[0], d0[0]), fmaf(a.h, u[1], d0[1]), fmaf(a.h, u[2], d0[2])};   // x - t, A
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Gp[3 * r + c] = fmaf(du[r], dv[c], Gp[3 * r + c]);
+    if (o < n) {   // uniform over the warp: every group samples atom i of the same ligand
+      float* ac = acc + ((size_t)o * 32 + lane) * 6;
+      ac[0] += du[0];
+      ac[1] += du[1];
+      ac[2] += du[2];
+      ac[3] += u[1] * du[2] - u[2] * du[1];
+      ac[4] += u[2] * du[0] - u[0] * du[2];
+      ac[5] += u[0] * du[1] - u[1] * du[0];
+    }
+  }
+  // subtree sums, children first (this lane's own sums)
+  for (int r = n - 1; r >= 0; --r) {
+    const int b = S.ord[r], pb = S.par[b];
+    if (pb < n) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) acc[((size_t)pb * 32 + lane) * 6 + e] += acc[((size_t)b * 32 + lane) * 6 + e];
+    }
+  }
+  Sl = gl_sum(Sl, G);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) gs[r] = gl_sum(gs[r], G);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) Gp[e] = gl_sum(Gp[e], G);
+  __syncwarp();
+  if (sub == 0) {
+    float R[9];
+    qmat(q, R);
+    // Gy = Gp R: sum du y^T with y = R^T (x - t)
+    float Gy[9];
+    mat3mul(Gp, R, Gy);
+    const float dR[4][9] = {
+        {0.f, -2.f * q.z, 2.f * q.y, 2.f * q.z, 0.f, -2.f * q.x, -2.f * q.y, 2.f * q.x, 0.f},
+        {0.f, 2.f * q.y, 2.f * q.z, 2.f * q.y, -4.f * q.x, -2.f * q.w, 2.f * q.z, 2.f * q.w, -4.f * q.x},
+        {-4.f * q.y, 2.f * q.x, 2.f * q.w, 2.f * q.x, 0.f, 2.f * q.z, -2.f * q.w, 2.f * q.z, -4.f * q.y},
+        {-4.f * q.z, -2.f * q.w, 2.f * q.x, 2.f * q.w, -4.f * q.z, 2.f * q.y, 2.f * q.x, 2.f * q.y, 0.f}};
+    float dq[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float s = 0.f;
+#pragma unroll
+      for (int e = 0; e < 9; ++e) s = fmaf(dR[k][e], Gy[e], s);
+      dq[k] = s * a.inv_h;
+    }
+    const float proj = q.w * dq[0] + q.x * dq[1] + q.y * dq[2] + q.z * dq[3];
+    const float qh[4] = {q.w, q.x, q.y, q.z};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) grad[r] = gs[r] * a.inv_h;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) grad[3 + k] = (dq[k] - qh[k] * proj) * rqn;
+    for (int b = 0; b < n; ++b) {
+      float F[3] = {0.f, 0.f, 0.f}, tau[3] = {0.f, 0.f, 0.f};
+      for (int j = 0; j < G; ++j) {   // the group's lanes, in lane order
+        const float* ac = acc + ((size_t)b * 32 + grp * G + j) * 6;
+        F[0] += ac[0]; F[1] += ac[1]; F[2] += ac[2];
+        tau[0] += ac[3]; tau[1] += ac[4]; tau[2] += ac[5];
+      }
+      float4 p0, p1, p2;
+      fk_get(T + ((size_t)S.par[b] * PW + grp) * 12, p0, p1, p2);
+      const float4 xv = S.sx[S.sb[b].y], k = S.ax[b];
+      const float uv[3] = {fmaf(p0.x, xv.x, fmaf(p0.y, xv.y, fmaf(p0.z, xv.z, p0.w))),
+                           fmaf(p1.x, xv.x, fmaf(p1.y, xv.y, fmaf(p1.z, xv.z, p1.w))),
+                           fmaf(p2.x, xv.x, fmaf(p2.y, xv.y, fmaf(p2.z, xv.z, p2.w)))};
+      float w[3] = {p0.x * k.x + p0.y * k.y + p0.z * k.z, p1.x * k.x + p1.y * k.y + p1.z * k.z,
+                    p2.x * k.x + p2.y * k.y + p2.z * k.z};
+      const float wn = rsqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+      const float c0 = tau[0] - (uv[1] * F[2] - uv[2] * F[1]);
+      const float c1 = tau[1] - (uv[2] * F[0] - uv[0] * F[2]);
+      const float c2 = tau[2] - (uv[0] * F[1] - uv[1] * F[0]);
+      grad[7 + b] = (w[0] * c0 + w[1] * c1 + w[2] * c2) * wn;
+    }
+  }
+  __syncwarp();
+  return Sl;
+}
+
+template <int G, bool REFINE>
+__global__ void __launch_bounds__(32, 16) grad_lane_kernel(const GradArgs a) {
+  constexpr int PW = GL<G>::PW;
+  extern __shared__ __align__(16) unsigned char gl_smem[];
+  const int acap = a.max_atoms, ncap = a.max_rot;
+  FkLigand S;
+  float *T, *acc, *st;
+  gl_carve<G>(acap, ncap, gl_smem, &S, &T, &acc, &st);
+  const int lane = threadIdx.x & 31, grp = lane / G, sub = lane % G;
+  const int wpl = (a.P + PW - 1) / PW;   // warps per ligand
+  const size_t gw = blockIdx.x;
+  if (gw >= (size_t)a.n_list * wpl) return;
+  const int li = (int)(gw / wpl);
+  const int l = a.list ? a.list[li] : li;
+  const int p0 = (int)(gw % wpl) * PW + grp;
+  const bool own = p0 < a.P;
+  const int p = own ? p0 : a.P - 1;   // spare groups shadow the last pose and write nothing
+  const size_t gp = (size_t)l * a.P + p;
+  const int a0 = a.lig.atom_off[l];
+  const int N = a.lig.atom_off[l + 1] - a0;
+  const int r0 = a.lig.rot_off[l];
+  const int n = a.lig.rot_off[l + 1] - r0;
+  const int plen = 7 + n;
+  const size_t off = (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * plen;
+  bool ok = a.pk.status[l] == 0 && lg_check(a.grid.check, N <= acap && n <= ncap, kChkItemShape);
+  if (ok) ok = lg_check(a.grid.check, fk_stage(a.pk, a0, N, r0, n, S, lane), kChkAtomIndex);
+  if (!ok) {   // uniform over the warp (one ligand)
+    if (own && sub == 0) a.out_scores[gp] = -INFINITY;
+    if (!REFINE && own)
+      for (int e = sub; e < plen; e += G) a.out_grads[off + e] = 0.f;
+    return;
+  }
+  const int sl = 7 + ncap;
+  float* pose = st + (size_t)(0 * PW + grp) * sl;
+  float* cand = st + (size_t)(1 * PW + grp) * sl;
+  float* grad = st + (size_t)(2 * PW + grp) * sl;
+  float* grad_c = st + (size_t)(3 * PW + grp) * sl;
+  const float* src = REFINE ? a.inout_poses : a.poses;
+  for (int e = sub; e < plen; e += G) pose[e] = src[off + e];
+  __syncwarp();
+  float Sc = gl_eval<G>(a, S, N, n, pose, grad, T, acc, grp, sub, lane);
+  if constexpr (!REFINE) {
+    if (own) {
+      if (sub == 0) a.out_scores[gp] = Sc;
+      for (int e = sub; e < plen; e += G) a.out_grads[off + e] = grad[e];
+    }
+    return;
+  } else {
+    float s_t = a.step_t, s_q = a.step_q, s_th = a.step_theta;
+    for (int s = 0; s < a.steps; ++s) {
+      if (sub == 0) {
+        float nt = 0.f, nq = 0.f, nth = 0.f;
+        for (int e = 0; e < plen; ++e) {
+          const float v = grad[e] * grad[e];
+          if (e < 3) nt += v; else if (e < 7) nq += v; else nth += v;
+        }
+        nt = sqrtf(nt); nq = sqrtf(nq); nth = sqrtf(nth);
+        const float kt = nt > 0.f ? s_t / nt : 0.f;
+        const float kq = nq > 0.f ? s_q / nq : 0.f;
+        const float kth = nth > 0.f ? s_th / nth : 0.f;
+        const float rqn = 1.f / sqrtf(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
+        float qq[4], qm = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          qq[k] = fmaf(kq, grad[3 + k], pose[3 + k] * rqn);
+          qm += qq[k] * qq[k];
+        }
+        const float rqm = 1.f / sqrtf(qm);
+        for (int e = 0; e < plen; ++e) {
+          float v;
+          if (e < 3) {
+            v = fmaf(kt, grad[e], pose[e]);
+            v = fminf(fmaxf(v, a.box_lo[e]), a.box_hi[e]);
+          } else if (e < 7) {
+            v = qq[e - 3] * rqm;
+          } else {
+            // wrap to [-pi, pi): one turn suffices from a wrapped angle;
+            // other inputs take the general reduction
+            const float w0 = fmaf(kth, grad[e], pose[e]) + kPiF;
+            float w = w0;
+            if (w >= 2.f * kPiF) w -= 2.f * kPiF;
+            else if (w < 0.f) w += 2.f * kPiF;
+            if (!(w >= 0.f && w < 2.f * kPiF)) {
+              w = fmodf(w0, 2.f * kPiF);
+              if (w < 0.f) w += 2.f * kPiF;
+            }
+            v = w - kPiF;
+          }
+          cand[e] = v;
+        }
+      }
+      __syncwarp();
+      // the candidate with its gradient: a kept step needs no second evaluation
+      const float S2 = gl_eval<G>(a, S, N, n, cand, grad_c, T, acc, grp, sub, lane);
+      const bool take = S2 > Sc;   // identical in every lane of the group (group sums)
+      if (own && a.out_accept && sub == 0) a.out_accept[gp * a.steps + s] = take ? 1 : 0;
+      if (take) {
+        float* t = pose; pose = cand; cand = t;
+        t = grad; grad = grad_c; grad_c = t;
+        Sc = S2;
+      } else {
+        s_t *= 0.5f; s_q *= 0.5f; s_th *= 0.5f;
+      }
+      __syncwarp();
+    }
+    if (own) {
+      const float sgn = pose[3] < 0.f ? -1.f : 1.f;
+      for (int e = sub; e < plen; e += G) a.inout_poses[off + e] = (e >= 3 && e < 7) ? sgn * pose[e] : pose[e];
+      if (sub == 0) a.out_scores[gp] = Sc;
+    }
+  }
+}
+
+template <int G, bool REFINE>
+cudaError_t launch_gl(const GradArgs& a, cudaStream_t s) {
+  const size_t smem = gl_carve<G>(a.max_atoms, a.max_rot, nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(grad_lane_kernel<G, REFINE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const size_t blocks = (size_t)a.n_list * ((a.P + GL<G>::PW - 1) / GL<G>::PW);
+  grad_lane_kernel<G, REFINE><<<(unsigned)blocks, 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_grad_lanes(const GradArgs& a, bool refine, cudaStream_t s) {
+  if ((size_t)a.n_list * a.P == 0) return cudaSuccess;
+  // lanes per pose: the fewest that fill a warp with this many poses
+  const int G = a.P > 16 ? 1 : a.P > 8 ? 2 : 4;
+  if (G == 1) return refine ? launch_gl<1, true>(a, s) : launch_gl<1, false>(a, s);
+  if (G == 2) return refine ? launch_gl<2, true>(a, s) : launch_gl<2, false>(a, s);
+  return refine ? launch_gl<4, true>(a, s) : launch_gl<4, false>(a, s);
+}
 
 size_t grad_smem_bytes(int max_atoms) { return (size_t)kGroups * pose_region(max_atoms); }
 

@@ -16,6 +16,7 @@
 
 #include "../../include/ligen.h"
 #include "internal.h"
+#include "fk_pose.cuh"
 #include "pose_build.cuh"
 
 namespace ligen {
@@ -113,96 +114,25 @@ __global__ void __launch_bounds__(32 * kScoreWarps, 8) score_kernel(const ScoreA
 
 // Pose-per-lane scoring, for calls with many poses per ligand: one warp per
 // (ligand, 32 poses), lane p scoring pose p on its own, with the torsions
-// applied as forward kinematics instead of atom by atom.
-//
-// Moving sides are nested or disjoint, so the pose definition (bond by bond
-// in index order, each about its current axis) equals, in exact
-// arithmetic, a chain of rigid transforms: the transform of bond b is its
-// parent's transform (the smallest moving side that strictly contains b's)
-// composed with the rotation by theta_b about b's axis in the input
-// conformation. An atom's position is then the transform of its owner (the
-// smallest moving side holding it; the ligand's root frame when no torsion
-// moves it) applied to its input coordinates. Every transform here also
-// carries the pose's rotation R(q/|q|), its translation and the change to
-// grid units, so an atom costs one 3x4 transform (9 FMA) and one sample.
-//
-// Per ligand, the warp stages in shared memory with coalesced loads: the
-// centred input coordinates, the bond records and moving-atom lists; then
-// works out each atom's owner, each bond's parent (the owner of its moving
-// endpoint v, which no other bond's list holds), the order of the bonds
-// (larger moving side first, so a parent comes before its children) and the
-// bond axes. Per lane: the n + 1 transforms, 48 bytes each, in shared memory
+// applied as forward kinematics (fk_pose.cuh) instead of atom by atom: per
+// lane the n + 1 transforms of its pose, 48 bytes each, in shared memory
 // [slot][lane][12] (a 48-byte lane stride keeps 128-bit accesses free of
-// bank conflicts). Shared memory thus grows with the bonds, and the caller
-// launches ligands by rotatable-bond class. Lanes past the ligand's last
-// pose shadow it and write nothing.
-struct FkSmem {
-  float* T;       // [ncap + 1][32][12] per-lane transforms (rows of M, then o)
-  float4* sx;     // [acap] centred input coordinates (w = type)
-  float4* ax;     // [ncap] unit bond axes in the input conformation
-  uchar4* sb;     // [ncap] bond records (u, v, list length)
-  uint8_t* sf;    // [ncap][fstride] moving-atom lists (moving side without v)
-  uint8_t* own;   // [acap] owner of each atom (a bond, or ncap for the root)
-  uint8_t* par;   // [ncap] parent of each bond (a bond, or the root)
-  uint8_t* ord;   // [ncap] bonds, larger moving side first
-  int fstride;
-};
-
-// A moving side has at most N/2 atoms (the smaller side of the cut), so a
-// list of a ligand of at most `acap` atoms fits the first acap/2 bytes of its
-// kFragStride-byte slot, rounded to a whole 16-byte vector.
-__host__ __device__ inline int lane_fstride(int acap) {
-  const int s = ((acap / 2 + 15) / 16) * 16;
-  return s < 16 ? 16 : (s > kFragStride ? kFragStride : s);
-}
-
-__host__ __device__ inline size_t fk_carve(int acap, int ncap, unsigned char* base, FkSmem* S) {
-  const int fs = lane_fstride(acap);
-  const int n4 = (ncap + 15) / 16 * 16;
-  const int a16 = (acap + 15) / 16 * 16;
-  size_t o = 0;
-  const size_t oT = o;   o += (size_t)(ncap + 1) * 32 * 12 * sizeof(float);
-  const size_t osx = o;  o += (size_t)acap * sizeof(float4);
-  const size_t oax = o;  o += (size_t)ncap * sizeof(float4);
-  const size_t osb = o;  o += (size_t)n4 * sizeof(uchar4);
-  const size_t osf = o;  o += (size_t)ncap * fs;
-  const size_t oown = o; o += (size_t)a16;
-  const size_t opar = o; o += (size_t)n4;
-  const size_t oord = o; o += (size_t)n4;
-  if (S) {
-    S->T = (float*)(base + oT);
-    S->sx = (float4*)(base + osx);
-    S->ax = (float4*)(base + oax);
-    S->sb = (uchar4*)(base + osb);
-    S->sf = base + osf;
-    S->own = base + oown;
-    S->par = base + opar;
-    S->ord = base + oord;
-    S->fstride = fs;
-  }
-  return o;
-}
-
-__device__ __forceinline__ void fk_store(float* T, int slot, int lane, const float* m, const float* o) {
-  float4* d = reinterpret_cast<float4*>(T + ((size_t)slot * 32 + lane) * 12);
-  d[0] = make_float4(m[0], m[1], m[2], o[0]);
-  d[1] = make_float4(m[3], m[4], m[5], o[1]);
-  d[2] = make_float4(m[6], m[7], m[8], o[2]);
-}
-
-// rows (m0 m1 m2 | o0), (m3 m4 m5 | o1), (m6 m7 m8 | o2)
-__device__ __forceinline__ void fk_load(const float* T, int slot, int lane, float4& r0, float4& r1, float4& r2) {
-  const float4* d = reinterpret_cast<const float4*>(T + ((size_t)slot * 32 + lane) * 12);
-  r0 = d[0];
-  r1 = d[1];
-  r2 = d[2];
+// bank conflicts); per atom one 3x4 transform of its owner (9 FMA) and one
+// branch-free record load, 8 in flight per lane. Shared memory grows with
+// the bonds, so the caller launches ligands by rotatable-bond class. Lanes
+// past the ligand's last pose shadow it and write nothing.
+__host__ __device__ inline size_t lane_carve(int acap, int ncap, unsigned char* base, FkLigand* S, float** T) {
+  const size_t tbytes = (size_t)(ncap + 1) * 32 * 12 * sizeof(float);
+  if (T) *T = (float*)base;
+  return tbytes + fk_ligand_carve(acap, ncap, base ? base + tbytes : nullptr, S);
 }
 
 __global__ void __launch_bounds__(32, 16) score_lane_kernel(const ScoreArgs a) {
   extern __shared__ __align__(16) unsigned char lane_smem[];
   const int acap = a.max_atoms, ncap = a.max_rot;
-  FkSmem S;
-  fk_carve(acap, ncap, lane_smem, &S);
+  FkLigand S;
+  float* T;
+  lane_carve(acap, ncap, lane_smem, &S, &T);
   const int lane = threadIdx.x & 31;
   const int wpl = (a.P + 31) / 32;    // warps per ligand
   const size_t gw = blockIdx.x;
@@ -225,110 +155,20 @@ __global__ void __launch_bounds__(32, 16) score_lane_kernel(const ScoreArgs a) {
     if (own) a.out_scores[gp] = -INFINITY;
     return;
   }
-  // ---- stage the ligand (coalesced, all lanes)
-  for (int i = lane; i < N; i += 32) {
-    S.sx[i] = a.pk.xc[a0 + i];
-    S.own[i] = (uint8_t)ncap;   // the root frame until a list claims the atom
-  }
-  for (int b = lane; b < n; b += 32) S.sb[b] = a.pk.binfo[r0 + b];
-  {   // the first fstride bytes of every list (16-byte vectors)
-    const int per = S.fstride / 16;
-    const uint4* src = reinterpret_cast<const uint4*>(a.pk.frag + (size_t)r0 * kFragStride);
-    uint4* dst = reinterpret_cast<uint4*>(S.sf);
-    for (int v = lane; v < n * per; v += 32) dst[v] = src[(v / per) * (kFragStride / 16) + v % per];
-  }
   const float* pose = a.poses + (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
-  float t[3], q4[4];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) t[k] = pose[k];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) q4[k] = pose[3 + k];
-  __syncwarp();
-  // ---- owners: the bond with the shortest list holding the atom (lists of
-  // nested moving sides have different lengths; lanes of one bond touch
-  // distinct atoms, bonds go one after another)
-  bool bad = false;
-  for (int b = 0; b < n; ++b) {
-    const int m = S.sb[b].z;
-    bad |= m > S.fstride;
-    for (int k = lane; k < m && k < S.fstride; k += 32) {
-      const int i = S.sf[b * S.fstride + k];
-      if (i >= N) { bad = true; continue; }
-      const int o = S.own[i];
-      if (o == ncap || m < S.sb[o].z) S.own[i] = (uint8_t)b;
-    }
-    __syncwarp();
-  }
-  // ---- per bond: parent (owner of v), order (longer list first), axis
-  if (lane < n) {
-    const uchar4 bi = S.sb[lane];
-    bad |= bi.x >= N || bi.y >= N;
-    const int u = bi.x < N ? bi.x : 0, v = bi.y < N ? bi.y : 0;
-    const int po = S.own[v];
-    S.par[lane] = (uint8_t)(po == ncap ? n : po);   // root slot = n below
-    int rank = 0;
-    for (int b = 0; b < n; ++b) {
-      const int mb = S.sb[b].z;
-      rank += (mb > bi.z) || (mb == bi.z && b < lane);
-    }
-    S.ord[rank] = (uint8_t)lane;
-    const float4 xv = S.sx[v], xu = S.sx[u];
-    float kx = xv.x - xu.x, ky = xv.y - xu.y, kz = xv.z - xu.z;
-    const float kn = rsqrtf(kx * kx + ky * ky + kz * kz);
-    S.ax[lane] = make_float4(kx * kn, ky * kn, kz * kn, 0.f);
-  }
-  if (!lg_check(a.grid.check, !__any_sync(0xffffffffu, bad), kChkAtomIndex)) {
+  if (!lg_check(a.grid.check, fk_stage(a.pk, a0, N, r0, n, S, lane), kChkAtomIndex)) {
     if (own) a.out_scores[gp] = -INFINITY;
     return;
   }
-  __syncwarp();
-  // ---- per lane: the root transform (pose rotation and translation, in grid
-  // units), then every bond's, parents first; the root sits in slot n
-  {
-    const Quat q = qnormalize({q4[0], q4[1], q4[2], q4[3]});
-    float R[9], o[3];
-    qmat(q, R);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] *= a.inv_h;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) o[k] = (t[k] - a.origin[k]) * a.inv_h;
-    fk_store(S.T, n, lane, R, o);
-  }
-  for (int r = 0; r < n; ++r) {
-    const int b = S.ord[r];
-    const int pb = S.par[b];
-    float4 p0r, p1r, p2r;
-    fk_load(S.T, pb, lane, p0r, p1r, p2r);
-    const float Mp[9] = {p0r.x, p0r.y, p0r.z, p1r.x, p1r.y, p1r.z, p2r.x, p2r.y, p2r.z};
-    const float op[3] = {p0r.w, p1r.w, p2r.w};
-    float sn, cs;
-    sincosf(pose[7 + b], &sn, &cs);
-    const float4 k = S.ax[b];
-    const float tc = 1.f - cs;
-    // rotation by theta_b about k (right-handed): c I + s [k]x + (1 - c) k k^T
-    const float Rb[9] = {fmaf(tc * k.x, k.x, cs),     fmaf(tc * k.x, k.y, -sn * k.z), fmaf(tc * k.x, k.z, sn * k.y),
-                         fmaf(tc * k.x, k.y, sn * k.z), fmaf(tc * k.y, k.y, cs),     fmaf(tc * k.y, k.z, -sn * k.x),
-                         fmaf(tc * k.x, k.z, -sn * k.y), fmaf(tc * k.y, k.z, sn * k.x), fmaf(tc * k.z, k.z, cs)};
-    float Mb[9];
-    mat3mul(Mp, Rb, Mb);
-    // the axis point v keeps its place: o_b = T_p(x_v) - M_b x_v
-    const float4 xv = S.sx[S.sb[b].y];
-    float ob[3];
-#pragma unroll
-    for (int rr = 0; rr < 3; ++rr) {
-      const float tp = fmaf(Mp[3 * rr], xv.x, fmaf(Mp[3 * rr + 1], xv.y, fmaf(Mp[3 * rr + 2], xv.z, op[rr])));
-      ob[rr] = tp - fmaf(Mb[3 * rr], xv.x, fmaf(Mb[3 * rr + 1], xv.y, Mb[3 * rr + 2] * xv.z));
-    }
-    fk_store(S.T, b, lane, Mb, ob);
-  }
-  // ---- samples: unconditional loads, 8 gathers in flight per lane
+  const Quat q = qnormalize({pose[3], pose[4], pose[5], pose[6]});
+  fk_transforms(S, n, pose, q, pose + 7, a.origin, a.inv_h, T + 12 * lane, 32 * 12);
+  // samples: unconditional loads, 8 gathers in flight per lane
   float acc = 0.f;
 #pragma unroll 8
   for (int i = 0; i < N; ++i) {
     const float4 X = S.sx[i];
-    const int o = S.own[i];
     float4 m0, m1, m2;
-    fk_load(S.T, o == ncap ? n : o, lane, m0, m1, m2);
+    fk_get(T + ((size_t)S.own[i] * 32 + lane) * 12, m0, m1, m2);
     const float ux = fmaf(m0.x, X.x, fmaf(m0.y, X.y, fmaf(m0.z, X.z, m0.w)));
     const float uy = fmaf(m1.x, X.x, fmaf(m1.y, X.y, fmaf(m1.z, X.z, m1.w)));
     const float uz = fmaf(m2.x, X.x, fmaf(m2.y, X.y, fmaf(m2.z, X.z, m2.w)));
@@ -339,7 +179,7 @@ __global__ void __launch_bounds__(32, 16) score_lane_kernel(const ScoreArgs a) {
 
 }  // namespace
 
-size_t score_lane_smem_bytes(int acap, int ncap) { return fk_carve(acap, ncap, nullptr, nullptr); }
+size_t score_lane_smem_bytes(int acap, int ncap) { return lane_carve(acap, ncap, nullptr, nullptr, nullptr); }
 
 cudaError_t launch_score_lanes(const ScoreArgs& a, cudaStream_t s) {
   if ((size_t)a.n_list * a.P == 0) return cudaSuccess;

@@ -1254,6 +1254,10 @@ static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, i
   const size_t o_binfo = ar.take(4 * (size_t)sh.rot);
   const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
   const size_t o_status = ar.take(4 * (size_t)L);
+  ScorePlan plan;   // ligands by rotatable-bond class for the pose-group kernel
+  const bool lanes = poses_per_ligand >= kGradLanePosesMin;
+  if (lanes) plan_score(ligands->h_rot_off, L, &plan);
+  const size_t o_list = ar.take(4 * plan.list.size());
   size_t o_poses = 0, o_scores = 0, o_grads = 0, o_acc = 0;
   if (ohost) {
     o_poses = ar.take(4 * pose_floats);
@@ -1308,7 +1312,20 @@ static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, i
     ga.box_hi[k] = (float)((double)grid->origin[k] + (double)grid->spacing * (np[k] - 1));
   }
   ga.out_accept = out_accept ? (ohost ? ar.at<int8_t>(o_acc) : out_accept) : nullptr;
-  LG_CUDA(launch_grad(ga, refine != 0, s));
+  ga.h = grid->spacing;
+  if (!lanes) {
+    LG_CUDA(launch_grad(ga, refine != 0, s));
+  } else {   // pose groups on forward kinematics, class by class
+    LG_CUDA(cudaMemcpyAsync(ar.base + o_list, plan.list.data(), 4 * plan.list.size(), cudaMemcpyHostToDevice, s));
+    for (int c = 0; c < kScoreClasses; ++c) {
+      if (!plan.n[c]) continue;
+      GradArgs gc = ga;
+      gc.list = ar.at<int32_t>(o_list) + plan.start[c];
+      gc.n_list = plan.n[c];
+      gc.max_rot = kScoreRotCap[c];
+      LG_CUDA(launch_grad_lanes(gc, refine != 0, s));
+    }
+  }
   if (ohost) {
     LG_CUDA(cudaMemcpyAsync(out_scores, ga.out_scores, 4 * nposes, cudaMemcpyDeviceToHost, s));
     if (refine) LG_CUDA(cudaMemcpyAsync(poses_inout, d_poses, 4 * pose_floats, cudaMemcpyDeviceToHost, s));
