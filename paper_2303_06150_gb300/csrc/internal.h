@@ -168,7 +168,6 @@ cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s);
 // Pose-per-lane scoring of the ligands a.list[0 .. n_list) (all of them at
 // most a.max_atoms atoms), 32 poses per warp.
 cudaError_t launch_score_lanes(const ScoreArgs& a, cudaStream_t s);
-size_t score_lane_smem_bytes(int cap, int max_rot);
 cudaError_t launch_rescore(const RescoreArgs& a, cudaStream_t s);
 size_t grad_smem_bytes(int max_atoms);
 // refine = false: dS/dpose of every pose; true: gradient refinement in place.

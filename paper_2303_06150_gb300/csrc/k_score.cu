@@ -112,39 +112,43 @@ __global__ void __launch_bounds__(32 * kScoreWarps, 8) score_kernel(const ScoreA
   if (own && sub == 0) a.out_scores[gp] = acc;
 }
 
-// Pose-per-lane scoring, for calls with many poses per ligand: one warp per
-// (ligand, 32 poses), lane p scoring pose p on its own, with the torsions
-// applied as forward kinematics (fk_pose.cuh) instead of atom by atom: per
-// lane the n + 1 transforms of its pose, 48 bytes each, in shared memory
-// [slot][lane][12] (a 48-byte lane stride keeps 128-bit accesses free of
-// bank conflicts); per atom one 3x4 transform of its owner (9 FMA) and one
+// Pose-group scoring, for calls with many poses per ligand: one warp per
+// (ligand, 32/G poses), a group of G lanes per pose (G = 1 in use: lane p
+// scores pose p on its own), with the torsions applied as forward
+// kinematics (fk_pose.cuh) instead of atom by atom: the group's first lane
+// builds the n + 1 transforms of its pose, 48 bytes each, in shared memory
+// [slot][pose][12] (a 48-byte stride keeps 128-bit accesses free of bank
+// conflicts); per atom one 3x4 transform of its owner (9 FMA) and one
 // branch-free record load, 8 in flight per lane. Shared memory grows with
-// the bonds, so the caller launches ligands by rotatable-bond class. Lanes
+// the bonds, so the caller launches ligands by rotatable-bond class. Groups
 // past the ligand's last pose shadow it and write nothing.
+template <int G>
 __host__ __device__ inline size_t lane_carve(int acap, int ncap, unsigned char* base, FkLigand* S, float** T) {
-  const size_t tbytes = (size_t)(ncap + 1) * 32 * 12 * sizeof(float);
+  const size_t tbytes = (size_t)(ncap + 1) * (32 / G) * 12 * sizeof(float);
   if (T) *T = (float*)base;
   return tbytes + fk_ligand_carve(acap, ncap, base ? base + tbytes : nullptr, S);
 }
 
+template <int G>
 __global__ void __launch_bounds__(32, 16) score_lane_kernel(const ScoreArgs a) {
+  constexpr int PW = 32 / G;   // poses per warp
   extern __shared__ __align__(16) unsigned char lane_smem[];
   const int acap = a.max_atoms, ncap = a.max_rot;
   FkLigand S;
   float* T;
-  lane_carve(acap, ncap, lane_smem, &S, &T);
-  const int lane = threadIdx.x & 31;
-  const int wpl = (a.P + 31) / 32;    // warps per ligand
+  lane_carve<G>(acap, ncap, lane_smem, &S, &T);
+  const int lane = threadIdx.x & 31, grp = lane / G, sub = lane % G;
+  const int wpl = (a.P + PW - 1) / PW;    // warps per ligand
   const size_t gw = blockIdx.x;
   if (gw >= (size_t)a.n_list * wpl) return;
   const int li = (int)(gw / wpl);
   const int l = a.list ? a.list[li] : li;
-  const int p0 = (int)(gw % wpl) * 32 + lane;
+  const int p0 = (int)(gw % wpl) * PW + grp;
   const bool own = p0 < a.P;
   const int p = own ? p0 : a.P - 1;
   const size_t gp = (size_t)l * a.P + p;
   if (a.pk.status[l] != 0) {   // uniform over the warp (one ligand)
-    if (own) a.out_scores[gp] = -INFINITY;
+    if (own && sub == 0) a.out_scores[gp] = -INFINITY;
     return;
   }
   const int a0 = a.lig.atom_off[l];
@@ -152,45 +156,57 @@ __global__ void __launch_bounds__(32, 16) score_lane_kernel(const ScoreArgs a) {
   const int r0 = a.lig.rot_off[l];
   const int n = a.lig.rot_off[l + 1] - r0;
   if (!lg_check(a.grid.check, N <= acap && n <= ncap, kChkItemShape)) {
-    if (own) a.out_scores[gp] = -INFINITY;
+    if (own && sub == 0) a.out_scores[gp] = -INFINITY;
     return;
   }
   const float* pose = a.poses + (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
   if (!lg_check(a.grid.check, fk_stage(a.pk, a0, N, r0, n, S, lane), kChkAtomIndex)) {
-    if (own) a.out_scores[gp] = -INFINITY;
+    if (own && sub == 0) a.out_scores[gp] = -INFINITY;
     return;
   }
-  const Quat q = qnormalize({pose[3], pose[4], pose[5], pose[6]});
-  fk_transforms(S, n, pose, q, pose + 7, a.origin, a.inv_h, T + 12 * lane, 32 * 12);
+  if (sub == 0) {
+    const Quat q = qnormalize({pose[3], pose[4], pose[5], pose[6]});
+    fk_transforms(S, n, pose, q, pose + 7, a.origin, a.inv_h, T + 12 * grp, (size_t)PW * 12);
+  }
+  if (G > 1) __syncwarp();
   // samples: unconditional loads, 8 gathers in flight per lane
   float acc = 0.f;
 #pragma unroll 8
-  for (int i = 0; i < N; ++i) {
+  for (int i = sub; i < N; i += G) {
     const float4 X = S.sx[i];
     float4 m0, m1, m2;
-    fk_get(T + ((size_t)S.own[i] * 32 + lane) * 12, m0, m1, m2);
+    fk_get(T + ((size_t)S.own[i] * PW + grp) * 12, m0, m1, m2);
     const float ux = fmaf(m0.x, X.x, fmaf(m0.y, X.y, fmaf(m0.z, X.z, m0.w)));
     const float uy = fmaf(m1.x, X.x, fmaf(m1.y, X.y, fmaf(m1.z, X.z, m1.w)));
     const float uz = fmaf(m2.x, X.x, fmaf(m2.y, X.y, fmaf(m2.z, X.z, m2.w)));
     acc -= grid_sample_nb(a.grid, ux, uy, uz, __float_as_int(X.w));
   }
-  if (own) a.out_scores[gp] = acc;
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (own && sub == 0) a.out_scores[gp] = acc;
+}
+
+template <int G>
+cudaError_t launch_sl(const ScoreArgs& a, cudaStream_t s) {
+  const size_t smem = lane_carve<G>(a.max_atoms, a.max_rot, nullptr, nullptr, nullptr);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(score_lane_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const size_t blocks = (size_t)a.n_list * ((a.P + 32 / G - 1) / (32 / G));
+  score_lane_kernel<G><<<(unsigned)blocks, 32, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t score_lane_smem_bytes(int acap, int ncap) { return lane_carve(acap, ncap, nullptr, nullptr, nullptr); }
-
+// One lane per pose. Measured on GB300, scoring the 600,000 kept screening
+// poses: 0.255 ms with 1 lane per pose, 0.275 ms with 2 (one transform set
+// per pose, half the shared memory per warp, half of each lane's samples)
+// and 0.38 ms with 4.
 cudaError_t launch_score_lanes(const ScoreArgs& a, cudaStream_t s) {
   if ((size_t)a.n_list * a.P == 0) return cudaSuccess;
-  const size_t smem = score_lane_smem_bytes(a.max_atoms, a.max_rot);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(score_lane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  const size_t blocks = (size_t)a.n_list * ((a.P + 31) / 32);
-  score_lane_kernel<<<(unsigned)blocks, 32, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_sl<1>(a, s);
 }
 
 cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s) {
