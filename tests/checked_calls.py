@@ -51,11 +51,25 @@ def run_all(lg) -> dict:
              for g in (gen.make_grid(sp) for sp in gen.site_grids(w["grid"], 2))]
     keep("small_sites", lg.dock_sites(L, sites, trace=True, **kw))
     keep("small_static", lg.dock_batch_static(L, G, **kw))
+    keep("screen_queue", lg.dock_batch(Ls, Gs, batching="queue", trace=True, **kws))
     docked = lg.dock_batch(Ls, Gs, **kws)
     K = kws["top_k"]
     out["score"] = lg.score_poses(Ls, Gs, docked.poses, K).cpu().numpy()
-    sc, gr = lg.pose_grad(Ls, Gs, docked.poses, K)
-    out["grad.scores"], out["grad.grads"] = sc.cpu().numpy(), gr.cpu().numpy()
+    # 30 poses per ligand: the pose-per-lane scoring kernel, one-shot and prepared
+    d30 = lg.dock_batch(Ls, Gs, **dict(kws, top_k=30))
+    out["score30"] = lg.score_poses(Ls, Gs, d30.poses, 30).cpu().numpy()
+    prep = lg.prepare_scoring(Ls, Gs)
+    out["score30_prepared"] = prep.score(d30.poses, 30).cpu().numpy()
+    prep.release()
+    # gradients: 8 poses per ligand (4 lanes per pose), 16 (2
+    # lanes), 30 (1 lane) and 2 (the 16-lane group kernel)
+    for k, poses in ((K, docked.poses), (30, d30.poses)):
+        sc, gr = lg.pose_grad(Ls, Gs, poses, k)
+        out[f"grad.scores{k}"], out[f"grad.grads{k}"] = sc.cpu().numpy(), gr.cpu().numpy()
+    for k in (2, 16):
+        dk = lg.dock_batch(Ls, Gs, **dict(kws, top_k=k))
+        sc, gr = lg.pose_grad(Ls, Gs, dk.poses, k)
+        out[f"grad.scores{k}"], out[f"grad.grads{k}"] = sc.cpu().numpy(), gr.cpu().numpy()
     refined, rs, acc = lg.refine_poses(Ls, Gs, docked.poses, K, steps=10, accept=True)
     out["refine.poses"], out["refine.scores"] = refined.cpu().numpy(), rs.cpu().numpy()
     out["refine.accept"] = acc.cpu().numpy()

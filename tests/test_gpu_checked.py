@@ -3,7 +3,8 @@
 libligen_checked.so compares every data-dependent device index with its
 bound (grid records and channels, lattice nodes of the FP64 re-score,
 ligand sizes against the launch's shared-memory carve-up, bond endpoints and
-moving atoms against the ligand's atoms); a violation is recorded and the
+moving atoms against the ligand's atoms, moving lists against the staged
+list length); a violation is recorded and the
 access skipped, and the call returns LIGEN_ERR_CHECK. A child process runs
 every kernel through that build on seeded inputs (every call must succeed,
 i.e. no index was ever out of range), and its results must equal the normal
