@@ -1090,8 +1090,10 @@ int ligen_prepare_scoring(const ligen_ligands_t* ligands, const ligen_grid_t* gr
   CallCheck chk;
   chk.plan(tmp);
   if (tmp.used && (rc = get_workspace(s, tmp.used, &tmp.base)) != LIGEN_OK) return rc;
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
   auto* h = new ligen_prepared();
-  LG_CUDA(cudaGetDevice(&h->dev));
+  h->dev = dev;
   cudaError_t e = cudaMalloc(&h->mem, keep.used);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1111,9 +1113,9 @@ int ligen_prepare_scoring(const ligen_ligands_t* ligands, const ligen_grid_t* gr
   if ((rc = stage_ligands(tmp, ligands, sh, lp, s, &lig)) != LIGEN_OK) return bail(rc);
   const float* gvals = (const float*)grid->data;
   if (ghost) {
-    if (cudaMemcpyAsync(tmp.base + o_gval, grid->data, grid_values_bytes(grid), cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-      return bail(cuda_fail(cudaGetLastError(), "grid upload"));
+    const cudaError_t ge =
+        cudaMemcpyAsync(tmp.base + o_gval, grid->data, grid_values_bytes(grid), cudaMemcpyHostToDevice, s);
+    if (ge != cudaSuccess) return bail(cuda_fail(ge, "grid upload"));
     gvals = tmp.at<float>(o_gval);
   }
   const cudaMemcpyKind kind = lhost ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
