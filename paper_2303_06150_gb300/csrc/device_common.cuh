@@ -321,6 +321,48 @@ __device__ __forceinline__ float grid_sample_fmt(const GridView& g, float ux, fl
   }
 }
 
+// 16-bit record samplers with the channel's record base computed by the
+// caller (chan_base16, once per atom): a sample then forms its address from
+// a 32-bit in-channel cell index with one wide multiply-add instead of a
+// 64-bit record index. Same records, same arithmetic, same results as
+// grid_sample_fmt. Measured on GB300 (screen20k docking kernel): FP16
+// 45.65 -> 45.11 ms, BF16 47.13 -> 46.06 ms. The same change to the FP32
+// sampler made it 1.5% slower (more spills in the 8-CTA build), so FP32
+// records keep grid_sample.
+__device__ __forceinline__ const unsigned char* chan_base16(const GridView& g, int c) {
+  return reinterpret_cast<const unsigned char*>(g.coef) + (size_t)c * g.cz * g.cy * g.cx * 16;
+}
+
+template <int FMT>
+__device__ __forceinline__ float grid_sample16_cb(const GridView& g, const unsigned char* cb, float ux, float uy,
+                                                  float uz, int c) {
+  static_assert(FMT != kRecF32, "16-bit records only");
+  const bool inb = (ux >= 0.f) & (ux <= g.mx) & (uy >= 0.f) & (uy <= g.my) & (uz >= 0.f) & (uz <= g.mz);
+  float e = g.penalty;
+  if (inb) {
+    const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);   // the padding layer holds the upper faces
+    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+    const float dx = ux - fx, dy = uy - fy, dz = uz - fz;
+    const unsigned li = (unsigned)((iz * g.cy + iy) * g.cx + ix);
+    if constexpr (LIGEN_CHECKED) {
+      const size_t ri = rec_index(g.cx, g.cy, g.cz, c, ix, iy, iz);
+      if (!lg_check(g.check, c >= 0 && c < g.nc && ri < g.n_rec, kChkGridRecord)) return g.penalty;
+    }
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(cb) + li);
+    const float2 a = unpack2<FMT>(v.x), b = unpack2<FMT>(v.y);   // (c000, c100), (c010, c110)
+    const float2 d = unpack2<FMT>(v.z), f = unpack2<FMT>(v.w);   // (c001, c101), (c011, c111)
+    const float2 dxx = make_float2(dx, dx);
+    const float2 p0 = make_float2(a.x, b.x), q0 = make_float2(a.y, b.y);
+    const float2 p1 = make_float2(d.x, f.x), q1 = make_float2(d.y, f.y);
+    const float2 x0 = fma2(dxx, sub2(q0, p0), p0);
+    const float2 x1 = fma2(dxx, sub2(q1, p1), p1);
+    const float2 lo = make_float2(x0.x, x1.x), hi = make_float2(x0.y, x1.y);
+    const float2 y = fma2(make_float2(dy, dy), sub2(hi, lo), lo);
+    e = fmaf(dz, y.y - y.x, y.x);
+  }
+  return e;
+}
+
 // Value and gradient (per grid unit) of channel `c` at grid-unit position u:
 // the derivative of the cell's trilinear polynomial, zero outside the box.
 __device__ __forceinline__ float grid_sample_grad(const GridView& g, float ux, float uy, float uz, int c,

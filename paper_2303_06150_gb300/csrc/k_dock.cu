@@ -164,7 +164,9 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
       const float ux = fmaf(Mk[0], X.x, fmaf(Mk[1], X.y, fmaf(Mk[2], X.z, o[0])));
       const float uy = fmaf(Mk[3], X.x, fmaf(Mk[4], X.y, fmaf(Mk[5], X.z, o[1])));
       const float uz = fmaf(Mk[6], X.x, fmaf(Mk[7], X.y, fmaf(Mk[8], X.z, o[2])));
-      acc -= grid_sample_fmt<FMT>(grid, ux, uy, uz, __float_as_int(X.w));
+      const int c = __float_as_int(X.w);
+      if constexpr (FMT == kRecF32) acc -= grid_sample(grid, ux, uy, uz, c);
+      else acc -= grid_sample16_cb<FMT>(grid, chan_base16(grid, c), ux, uy, uz, c);
     }
     if (acc > best) { best = acc; kb = k; }
   }
@@ -249,6 +251,7 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
         for (int t = 0; t < m_live; ++t) {
           const int i = S.sfrag[off + t];
           const int c = __float_as_int(S.sx[i].w);
+          const unsigned char* cb = FMT == kRecF32 ? nullptr : chan_base16(grid, c);   // 16-bit records
           const float dx = S.cx[i * rpc + rr] - vx;
           const float dy = S.cy[i * rpc + rr] - vy;
           const float dz = S.cz[i * rpc + rr] - vz;
@@ -274,7 +277,7 @@ __device__ __forceinline__ void dock_item(const DockArgs& a, const SmemLayout& S
               uz[SLOTS - 1] = fmaf(ez, cs[SLOTS - 1], fmaf(qz, sn[SLOTS - 1], pz));
             }
 #pragma unroll
-            for (int s = 0; s < SLOTS; ++s) acc[s] -= grid_sample_fmt<FMT>(grid, ux[s], uy[s], uz[s], c);
+            for (int s = 0; s < SLOTS; ++s) acc[s] -= grid_sample16_cb<FMT>(grid, cb, ux[s], uy[s], uz[s], c);
           } else {
 #pragma unroll
             for (int s = 0; s < SLOTS; ++s) {
