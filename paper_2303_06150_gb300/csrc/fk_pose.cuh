@@ -16,8 +16,8 @@
 // the bond records and moving-atom lists (coalesced loads); each atom's
 // owner; each bond's parent (the owner of its moving endpoint v, which no
 // other bond's list holds); the bonds in decreasing moving-side size (a
-// parent before its children); the bond axes. Transforms are 12 floats:
-// three rows (m0 m1 m2 | o).
+// parent before its children) and grouped by depth in the bond tree; the
+// bond axes. Transforms are 12 floats: three rows (m0 m1 m2 | o).
 #pragma once
 
 #include "internal.h"
@@ -32,6 +32,9 @@ struct FkLigand {
   uint8_t* own;   // [acap] owner of each atom: a bond, or the root slot n after fk_stage
   uint8_t* par;   // [ncap] parent of each bond: a bond, or the root slot n
   uint8_t* ord;   // [ncap] bonds, larger moving side first
+  uint8_t* lord;  // [ncap] bonds by depth in the bond tree (root's children first)
+  uint8_t* loff;  // [LIGEN_MAX_ROT + 1] first entry of each depth in lord (loff[depths] = n);
+                  // loff[LIGEN_MAX_ROT] = the number of depths
   int fstride;
 };
 
@@ -56,7 +59,11 @@ __host__ __device__ inline size_t fk_ligand_carve(int acap, int ncap, unsigned c
   const size_t oown = o; o += (size_t)a16;
   const size_t opar = o; o += (size_t)n16;
   const size_t oord = o; o += (size_t)n16;
+  const size_t olord = o; o += (size_t)n16;
+  const size_t oloff = o; o += 48;   // LIGEN_MAX_ROT + 1 entries (the last: the number of depths)
   if (S) {
+    S->lord = base + olord;
+    S->loff = base + oloff;
     S->sx = (float4*)(base + osx);
     S->ax = (float4*)(base + oax);
     S->sb = (uchar4*)(base + osb);
@@ -69,9 +76,11 @@ __host__ __device__ inline size_t fk_ligand_carve(int acap, int ncap, unsigned c
   return o;
 }
 
-// Stage ligand (a0, N, r0, n) for the warp (all 32 lanes call it). Returns
-// false, on every lane, when a bond endpoint or a moving atom is out of
-// range (nothing out of range is written).
+// Stage ligand (a0, N, r0, n) for the warp (all 32 lanes call it); DEPTHS:
+// also the bonds grouped by depth (lord, loff) for fk_transforms_group.
+// Returns false, on every lane, when a bond endpoint or a moving atom is out
+// of range (nothing out of range is written).
+template <bool DEPTHS = false>
 __device__ inline bool fk_stage(const Packed& pk, int a0, int N, int r0, int n, const FkLigand& S, int lane) {
   for (int i = lane; i < N; i += 32) {
     S.sx[i] = pk.xc[a0 + i];
@@ -117,6 +126,27 @@ __device__ inline bool fk_stage(const Packed& pk, int a0, int N, int r0, int n, 
     S.ax[lane] = make_float4(kx * kn, ky * kn, kz * kn, 0.f);
   }
   bad = __any_sync(0xffffffffu, bad);
+  __syncwarp();
+  if (DEPTHS && lane == 0 && !bad) {   // depths (parents first in ord), then bonds by depth
+    uint8_t depth[LIGEN_MAX_ROT];
+    int cnt[LIGEN_MAX_ROT + 1] = {};
+    int dmax = -1;
+    for (int r = 0; r < n; ++r) {
+      const int b = S.ord[r], pb = S.par[b];
+      depth[b] = (uint8_t)(pb == n ? 0 : depth[pb] + 1);
+      ++cnt[depth[b]];
+      dmax = depth[b] > dmax ? depth[b] : dmax;
+    }
+    int o = 0;
+    for (int d = 0; d <= dmax; ++d) {
+      S.loff[d] = (uint8_t)o;
+      o += cnt[d];
+    }
+    S.loff[dmax + 1] = (uint8_t)n;
+    for (int d = 0; d <= dmax; ++d) cnt[d] = S.loff[d];
+    for (int r = 0; r < n; ++r) S.lord[cnt[depth[S.ord[r]]]++] = S.ord[r];
+    S.loff[LIGEN_MAX_ROT] = (uint8_t)(dmax + 1);   // number of depths
+  }
   __syncwarp();
   return !bad;
 }
@@ -175,6 +205,56 @@ __device__ inline void fk_transforms(const FkLigand& S, int n, const float* t, Q
       ob[rr] = tp - fmaf(Mb[3 * rr], xv.x, fmaf(Mb[3 * rr + 1], xv.y, Mb[3 * rr + 2] * xv.z));
     }
     fk_put(T + (size_t)b * slot_stride, Mb, ob);
+  }
+}
+
+// fk_transforms spread over a group of G lanes (sub = 0 .. G-1), all lanes
+// of the warp calling it: the root by the group's first lane, then the
+// bonds depth by depth (bonds of one depth are independent: a parent is one
+// depth up), round-robin over the group. Same transforms, bit for bit.
+template <int G>
+__device__ inline void fk_transforms_group(const FkLigand& S, int n, const float* t, Quat q, const float* theta,
+                                           const float* origin, float inv_h, float* T, size_t slot_stride,
+                                           int sub) {
+  if (sub == 0) {
+    float R[9], o[3];
+    qmat(q, R);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] *= inv_h;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[k] = (t[k] - origin[k]) * inv_h;
+    fk_put(T + (size_t)n * slot_stride, R, o);
+  }
+  __syncwarp();
+  const int depths = n ? S.loff[LIGEN_MAX_ROT] : 0;
+  for (int d = 0; d < depths; ++d) {
+    for (int k = S.loff[d] + sub; k < S.loff[d + 1]; k += G) {
+      const int b = S.lord[k];
+      float4 p0, p1, p2;
+      fk_get(T + (size_t)S.par[b] * slot_stride, p0, p1, p2);
+      const float Mp[9] = {p0.x, p0.y, p0.z, p1.x, p1.y, p1.z, p2.x, p2.y, p2.z};
+      const float op[3] = {p0.w, p1.w, p2.w};
+      float sn, cs;
+      sincosf(theta[b], &sn, &cs);
+      const float4 k4 = S.ax[b];
+      const float tc = 1.f - cs;
+      const float Rb[9] = {fmaf(tc * k4.x, k4.x, cs),     fmaf(tc * k4.x, k4.y, -sn * k4.z),
+                           fmaf(tc * k4.x, k4.z, sn * k4.y), fmaf(tc * k4.x, k4.y, sn * k4.z),
+                           fmaf(tc * k4.y, k4.y, cs),     fmaf(tc * k4.y, k4.z, -sn * k4.x),
+                           fmaf(tc * k4.x, k4.z, -sn * k4.y), fmaf(tc * k4.y, k4.z, sn * k4.x),
+                           fmaf(tc * k4.z, k4.z, cs)};
+      float Mb[9];
+      mat3mul(Mp, Rb, Mb);
+      const float4 xv = S.sx[S.sb[b].y];
+      float ob[3];
+#pragma unroll
+      for (int rr = 0; rr < 3; ++rr) {
+        const float tp = fmaf(Mp[3 * rr], xv.x, fmaf(Mp[3 * rr + 1], xv.y, fmaf(Mp[3 * rr + 2], xv.z, op[rr])));
+        ob[rr] = tp - fmaf(Mb[3 * rr], xv.x, fmaf(Mb[3 * rr + 1], xv.y, Mb[3 * rr + 2] * xv.z));
+      }
+      fk_put(T + (size_t)b * slot_stride, Mb, ob);
+    }
+    __syncwarp();
   }
 }
 

@@ -325,8 +325,9 @@ __global__ void __launch_bounds__(32 * kGradWarps, 6) refine_kernel(const GradAr
 // Pose-group gradients and refinement on forward kinematics (fk_pose.cuh).
 //
 // One warp per (ligand, PW poses), a group of G = 32 / PW lanes per pose. A
-// pose's n + 1 transforms are built once, by the group's first lane, into
-// shared memory [slot][pose][12]; each lane of the group then takes atoms
+// pose's n + 1 transforms are built once into shared memory
+// [slot][pose][12], the group's lanes sharing the bonds of each depth of
+// the bond tree (fk_transforms_group); each lane of the group then takes atoms
 // sub, sub + G, ... : position u = T_owner x (grid units), value and
 // gradient of the cell polynomial, du = dS/du. Per lane it accumulates
 //   dS/dt contribution  sum du,
@@ -337,8 +338,9 @@ __global__ void __launch_bounds__(32 * kGradWarps, 6) refine_kernel(const GradAr
 //   dS/dtheta_b = w_b . (tau_b - u_v x F_b)
 // with w_b the unit axis and u_v the axis point of bond b in the pose, from
 // the parent's transform (torsions commute, so theta_b may be taken as the
-// last rotation); dS/dq through q/|q| from Gy = Gp R (y = R^T (x - t) the
-// body coordinates), as in the group kernel above. Nothing is stored between
+// last rotation), the group's lanes sharing the bonds; dS/dq through q/|q|
+// from Gy = Gp R (y = R^T (x - t) the body coordinates), as in the group
+// kernel above. Nothing is stored between
 // evaluations but the pose, its gradient and the transforms.
 //
 // Refinement runs the group kernel's steps (normalised-step projected
@@ -382,7 +384,7 @@ __device__ float gl_eval(const GradArgs& a, const FkLigand& S, int N, int n, con
   constexpr int PW = GL<G>::PW;
   const float rqn = rsqrtf(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
   const Quat q = {pose[3] * rqn, pose[4] * rqn, pose[5] * rqn, pose[6] * rqn};
-  if (sub == 0) fk_transforms(S, n, pose, q, pose + 7, a.origin, a.inv_h, T + 12 * grp, (size_t)PW * 12);
+  fk_transforms_group<G>(S, n, pose, q, pose + 7, a.origin, a.inv_h, T + 12 * grp, (size_t)PW * 12, sub);
   for (int b = 0; b < n; ++b)
 #pragma unroll
     for (int e = 0; e < 6; ++e) acc[((size_t)b * 32 + lane) * 6 + e] = 0.f;
@@ -458,27 +460,27 @@ __device__ float gl_eval(const GradArgs& a, const FkLigand& S, int N, int n, con
     for (int r = 0; r < 3; ++r) grad[r] = gs[r] * a.inv_h;
 #pragma unroll
     for (int k = 0; k < 4; ++k) grad[3 + k] = (dq[k] - qh[k] * proj) * rqn;
-    for (int b = 0; b < n; ++b) {
-      float F[3] = {0.f, 0.f, 0.f}, tau[3] = {0.f, 0.f, 0.f};
-      for (int j = 0; j < G; ++j) {   // the group's lanes, in lane order
-        const float* ac = acc + ((size_t)b * 32 + grp * G + j) * 6;
-        F[0] += ac[0]; F[1] += ac[1]; F[2] += ac[2];
-        tau[0] += ac[3]; tau[1] += ac[4]; tau[2] += ac[5];
-      }
-      float4 p0, p1, p2;
-      fk_get(T + ((size_t)S.par[b] * PW + grp) * 12, p0, p1, p2);
-      const float4 xv = S.sx[S.sb[b].y], k = S.ax[b];
-      const float uv[3] = {fmaf(p0.x, xv.x, fmaf(p0.y, xv.y, fmaf(p0.z, xv.z, p0.w))),
-                           fmaf(p1.x, xv.x, fmaf(p1.y, xv.y, fmaf(p1.z, xv.z, p1.w))),
-                           fmaf(p2.x, xv.x, fmaf(p2.y, xv.y, fmaf(p2.z, xv.z, p2.w)))};
-      float w[3] = {p0.x * k.x + p0.y * k.y + p0.z * k.z, p1.x * k.x + p1.y * k.y + p1.z * k.z,
-                    p2.x * k.x + p2.y * k.y + p2.z * k.z};
-      const float wn = rsqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-      const float c0 = tau[0] - (uv[1] * F[2] - uv[2] * F[1]);
-      const float c1 = tau[1] - (uv[2] * F[0] - uv[0] * F[2]);
-      const float c2 = tau[2] - (uv[0] * F[1] - uv[1] * F[0]);
-      grad[7 + b] = (w[0] * c0 + w[1] * c1 + w[2] * c2) * wn;
+  }
+  for (int b = sub; b < n; b += G) {   // torsion gradients, bonds over the group's lanes
+    float F[3] = {0.f, 0.f, 0.f}, tau[3] = {0.f, 0.f, 0.f};
+    for (int j = 0; j < G; ++j) {   // the group's lanes, in lane order
+      const float* ac = acc + ((size_t)b * 32 + grp * G + j) * 6;
+      F[0] += ac[0]; F[1] += ac[1]; F[2] += ac[2];
+      tau[0] += ac[3]; tau[1] += ac[4]; tau[2] += ac[5];
     }
+    float4 p0, p1, p2;
+    fk_get(T + ((size_t)S.par[b] * PW + grp) * 12, p0, p1, p2);
+    const float4 xv = S.sx[S.sb[b].y], k = S.ax[b];
+    const float uv[3] = {fmaf(p0.x, xv.x, fmaf(p0.y, xv.y, fmaf(p0.z, xv.z, p0.w))),
+                         fmaf(p1.x, xv.x, fmaf(p1.y, xv.y, fmaf(p1.z, xv.z, p1.w))),
+                         fmaf(p2.x, xv.x, fmaf(p2.y, xv.y, fmaf(p2.z, xv.z, p2.w)))};
+    float w[3] = {p0.x * k.x + p0.y * k.y + p0.z * k.z, p1.x * k.x + p1.y * k.y + p1.z * k.z,
+                  p2.x * k.x + p2.y * k.y + p2.z * k.z};
+    const float wn = rsqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    const float c0 = tau[0] - (uv[1] * F[2] - uv[2] * F[1]);
+    const float c1 = tau[1] - (uv[2] * F[0] - uv[0] * F[2]);
+    const float c2 = tau[2] - (uv[0] * F[1] - uv[1] * F[0]);
+    grad[7 + b] = (w[0] * c0 + w[1] * c1 + w[2] * c2) * wn;
   }
   __syncwarp();
   return Sl;
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(32, 16) grad_lane_kernel(const GradArgs a) {
   const int plen = 7 + n;
   const size_t off = (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * plen;
   bool ok = a.pk.status[l] == 0 && lg_check(a.grid.check, N <= acap && n <= ncap, kChkItemShape);
-  if (ok) ok = lg_check(a.grid.check, fk_stage(a.pk, a0, N, r0, n, S, lane), kChkAtomIndex);
+  if (ok) ok = lg_check(a.grid.check, fk_stage<true>(a.pk, a0, N, r0, n, S, lane), kChkAtomIndex);
   if (!ok) {   // uniform over the warp (one ligand)
     if (own && sub == 0) a.out_scores[gp] = -INFINITY;
     if (!REFINE && own)
