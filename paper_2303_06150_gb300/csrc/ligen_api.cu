@@ -429,18 +429,20 @@ void plan_groups(const ligen_ligands_t* g, const ligen_params_t* p, int dev, std
   std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.cost > b.cost; });
 }
 
-// Side streams and events for the forked launches, per device.
+// Side streams and events for the forked launches, per (device, calling
+// stream): calls in flight on different streams fork onto different side
+// streams and record different events (calls on one stream are ordered).
 struct Fork {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> done;
   cudaEvent_t start = nullptr;
 };
 std::mutex g_fork_mu;
-std::map<int, Fork> g_fork;
+std::map<std::pair<int, cudaStream_t>, Fork> g_fork;
 
-int get_fork(int dev, int n, Fork** out) {
+int get_fork(int dev, cudaStream_t s, int n, Fork** out) {
   std::lock_guard<std::mutex> lk(g_fork_mu);
-  Fork& f = g_fork[dev];
+  Fork& f = g_fork[{dev, s}];
   if (!f.start) LG_CUDA(cudaEventCreateWithFlags(&f.start, cudaEventDisableTiming));
   while ((int)f.streams.size() < n) {
     cudaStream_t st;
@@ -490,7 +492,7 @@ std::string launch_key(const std::vector<DockArgs>& args, const std::vector<int>
 // Issue the groups' persistent launches forked from `s` and joined back.
 int issue_groups(const std::vector<DockArgs>& args, const std::vector<int>& ctas, int dev, cudaStream_t s) {
   Fork* f = nullptr;
-  int rc = get_fork(dev, (int)args.size(), &f);
+  int rc = get_fork(dev, s, (int)args.size(), &f);
   if (rc != LIGEN_OK) return rc;
   LG_CUDA(cudaEventRecord(f->start, s));
   for (size_t i = 0; i < args.size(); ++i) {
@@ -603,6 +605,9 @@ struct ScorePlan {
   std::vector<int32_t> list;        // ligand ids, class by class, ascending within a class
 };
 
+// (Within a class, ligands in decreasing atom count instead of index order
+// measured the same on GB300: 0.169 against 0.166 ms for the 600,000 kept
+// screening poses, 8.87 against 8.75 ms for their refinement.)
 void plan_score(const int32_t* h_rot_off, int L, ScorePlan* sp) {
   int cnt[kScoreClasses] = {};
   for (int l = 0; l < L; ++l) ++cnt[score_class_of(h_rot_off[l + 1] - h_rot_off[l])];
@@ -618,23 +623,62 @@ void plan_score(const int32_t* h_rot_off, int L, ScorePlan* sp) {
   for (int l = 0; l < L; ++l) sp->list[fill[score_class_of(h_rot_off[l + 1] - h_rot_off[l])]++] = l;
 }
 
-// Every ligand of base.lig scored: class by class (d_list = the plan's list
-// on the device; base.max_atoms the call's largest ligand) or in one
-// group-per-pose launch.
+// The launches launch(i, stream), i = 0 .. n-1, forked from `s` onto side
+// streams and joined back (on `s` itself when n == 1), so that the classes'
+// launches run side by side and one's ragged last wave overlaps another's
+// work. Measured on GB300 against the same launches one after another on
+// `s`: scoring the 600,000 kept screening poses (7 classes) 0.251 -> 0.166
+// ms, refining the top 16 poses of 20,000 ligands (50 steps) 13.4 -> 8.75
+// ms, their gradients 0.87 -> 0.70 ms.
+template <class F>
+int run_forked(int n, cudaStream_t s, F&& launch) {
+  if (n == 1) {
+    LG_CUDA(launch(0, s));
+    return LIGEN_OK;
+  }
+  if (n < 1) return LIGEN_OK;
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  Fork* f = nullptr;
+  int rc = get_fork(dev, s, n, &f);
+  if (rc != LIGEN_OK) return rc;
+  LG_CUDA(cudaEventRecord(f->start, s));
+  for (int i = 0; i < n; ++i) {
+    cudaStream_t st = f->streams[i];
+    LG_CUDA(cudaStreamWaitEvent(st, f->start, 0));
+    LG_CUDA(launch(i, st));
+    LG_CUDA(cudaEventRecord(f->done[i], st));
+    LG_CUDA(cudaStreamWaitEvent(s, f->done[i], 0));
+  }
+  return LIGEN_OK;
+}
+
+// The plan's non-empty classes, most bonds (longest warps) first.
+int used_classes(const ScorePlan& sp, int* used) {
+  int nu = 0;
+  for (int c = kScoreClasses - 1; c >= 0; --c)
+    if (sp.n[c]) used[nu++] = c;
+  return nu;
+}
+
+// Every ligand of base.lig scored: class by class, the classes' launches
+// concurrent (d_list = the plan's list on the device; base.max_atoms the
+// call's largest ligand), or in one group-per-pose launch.
 int run_score(const ScoreArgs& base, const ScorePlan& sp, const int32_t* d_list, cudaStream_t s) {
   if (base.P < kLanePosesMin) {
     LG_CUDA(launch_score(base, s));
     return LIGEN_OK;
   }
-  for (int c = 0; c < kScoreClasses; ++c) {
-    if (!sp.n[c]) continue;
+  int used[kScoreClasses];
+  const int nu = used_classes(sp, used);
+  return run_forked(nu, s, [&](int i, cudaStream_t st) {
+    const int c = used[i];
     ScoreArgs a = base;
     a.list = d_list + sp.start[c];
     a.n_list = sp.n[c];
     a.max_rot = kScoreRotCap[c];
-    LG_CUDA(launch_score_lanes(a, s));
-  }
-  return LIGEN_OK;
+    return launch_score_lanes(a, st);
+  });
 }
 
 }  // namespace
@@ -1319,14 +1363,17 @@ static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, i
     LG_CUDA(launch_grad(ga, refine != 0, s));
   } else {   // pose groups on forward kinematics, class by class
     LG_CUDA(cudaMemcpyAsync(ar.base + o_list, plan.list.data(), 4 * plan.list.size(), cudaMemcpyHostToDevice, s));
-    for (int c = 0; c < kScoreClasses; ++c) {
-      if (!plan.n[c]) continue;
+    int used[kScoreClasses];
+    const int nu = used_classes(plan, used);
+    rc = run_forked(nu, s, [&](int i, cudaStream_t st) {
+      const int c = used[i];
       GradArgs gc = ga;
       gc.list = ar.at<int32_t>(o_list) + plan.start[c];
       gc.n_list = plan.n[c];
       gc.max_rot = kScoreRotCap[c];
-      LG_CUDA(launch_grad_lanes(gc, refine != 0, s));
-    }
+      return launch_grad_lanes(gc, refine != 0, st);
+    });
+    if (rc != LIGEN_OK) return rc;
   }
   if (ohost) {
     LG_CUDA(cudaMemcpyAsync(out_scores, ga.out_scores, 4 * nposes, cudaMemcpyDeviceToHost, s));
