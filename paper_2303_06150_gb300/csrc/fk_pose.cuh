@@ -33,8 +33,8 @@ struct FkLigand {
   uint8_t* par;   // [ncap] parent of each bond: a bond, or the root slot n
   uint8_t* ord;   // [ncap] bonds, larger moving side first
   uint8_t* lord;  // [ncap] bonds by depth in the bond tree (root's children first)
-  uint8_t* loff;  // [LIGEN_MAX_ROT + 1] first entry of each depth in lord (loff[depths] = n);
-                  // loff[LIGEN_MAX_ROT] = the number of depths
+  uint8_t* loff;  // [48] first entry of each depth in lord (loff[depths] = n);
+                  // loff[LIGEN_MAX_ROT] = the number of depths; loff[kFkBad]: see fk_load
   int fstride;
 };
 
@@ -151,6 +151,33 @@ __device__ inline bool fk_stage(const Packed& pk, int a0, int N, int r0, int n, 
   return !bad;
 }
 
+// Stage ligand l = (a0, N, r0, n) for the warp (all 32 lanes call it) from
+// the forward-kinematics table (pk.fk_*, written by fk_table_kernel with
+// fk_stage<true>): the same shared-memory contents as fk_stage<true>, but
+// for the moving-atom lists, which nothing reads after staging. Vector
+// copies, no per-bond passes. Returns false, on every lane, when the table
+// marks the ligand's lists as malformed.
+__device__ inline bool fk_load(const Packed& pk, int l, int a0, int N, int r0, int n, const FkLigand& S, int lane) {
+  static_assert(kFkLoffBytes == 48 && kFkBad > LIGEN_MAX_ROT, "depth row of the table = the staged row");
+  for (int i = lane; i < N; i += 32) {
+    S.sx[i] = pk.xc[a0 + i];
+    S.own[i] = pk.fk_own[a0 + i];
+  }
+  for (int b = lane; b < n; b += 32) {
+    S.sb[b] = pk.binfo[r0 + b];
+    S.ax[b] = pk.fk_ax[r0 + b];
+    const uchar4 t = pk.fk_bond[r0 + b];
+    S.par[b] = t.x;
+    S.ord[b] = t.y;
+    S.lord[b] = t.z;
+  }
+  if (lane < kFkLoffBytes / 4)
+    reinterpret_cast<uint32_t*>(S.loff)[lane] =
+        reinterpret_cast<const uint32_t*>(pk.fk_loff + (size_t)l * kFkLoffBytes)[lane];
+  __syncwarp();
+  return S.loff[kFkBad] == 0;
+}
+
 __device__ __forceinline__ void fk_put(float* T, const float* m, const float* o) {
   float4* d = reinterpret_cast<float4*>(T);
   d[0] = make_float4(m[0], m[1], m[2], o[0]);
@@ -167,10 +194,12 @@ __device__ __forceinline__ void fk_get(const float* T, float4& r0, float4& r1, f
 
 // The n + 1 transforms of one pose: the root (slot n) from the translation
 // t and the unit quaternion q (w, x, y, z), in grid units; then every bond,
-// parents first, with the torsion angles theta[0 .. n). Transform of slot s
-// at T + s * slot_stride (16-byte aligned).
+// parents first, with the torsion angles theta[b * theta_stride], b = 0 ..
+// n-1 (which may lie in slot b itself: it is read before the slot is
+// written). Transform of slot s at T + s * slot_stride (16-byte aligned).
 __device__ inline void fk_transforms(const FkLigand& S, int n, const float* t, Quat q, const float* theta,
-                                     const float* origin, float inv_h, float* T, size_t slot_stride) {
+                                     size_t theta_stride, const float* origin, float inv_h, float* T,
+                                     size_t slot_stride) {
   {
     float R[9], o[3];
     qmat(q, R);
@@ -187,7 +216,7 @@ __device__ inline void fk_transforms(const FkLigand& S, int n, const float* t, Q
     const float Mp[9] = {p0.x, p0.y, p0.z, p1.x, p1.y, p1.z, p2.x, p2.y, p2.z};
     const float op[3] = {p0.w, p1.w, p2.w};
     float sn, cs;
-    sincosf(theta[b], &sn, &cs);
+    sincosf(theta[(size_t)b * theta_stride], &sn, &cs);
     const float4 k = S.ax[b];
     const float tc = 1.f - cs;
     // rotation by theta_b about k (right-handed): c I + s [k]x + (1 - c) k k^T

@@ -32,7 +32,16 @@ struct Packed {
   int32_t* axis;     // [sum n][2] optional: (u, v)
   uint32_t* touch;   // [sum n] optional: bit b of touch[b'] set when turning bond b'
                      // moves an atom bond b's sweep reads (bit b' always set)
+  // Forward-kinematics table (fk_table_kernel; read by the pose-per-lane
+  // scoring and pose-group gradient kernels), optional:
+  uint8_t* fk_own;   // [sum N] owner of each atom: a bond, or n (the root frame)
+  uchar4* fk_bond;   // [sum n] (parent of bond j, j-th bond parents first, j-th bond by depth, 0)
+  float4* fk_ax;     // [sum n] unit bond axes in the input conformation
+  uint8_t* fk_loff;  // [L][kFkLoffBytes] first entry of each depth, depth count, malformed flag
 };
+
+constexpr int kFkLoffBytes = 48;
+constexpr int kFkBad = 47;   // byte of a ligand's fk_loff row: 1 when its lists are malformed
 
 // Sample counters are spread over this many slots (summed on the host) so
 // that CTAs do not all add to one address.
@@ -150,6 +159,9 @@ cudaError_t launch_grid_prep(const float* values, int nx, int ny, int nz, int nc
 cudaError_t launch_grid_prep_fmt(const float* values, int nx, int ny, int nz, int nc, int fmt, void* rec,
                                  cudaStream_t s);
 cudaError_t launch_pack(const LigandsDev& lig, int nc, const Packed& out, cudaStream_t s);
+// The forward-kinematics table of every ligand (pk.fk_*), after launch_pack;
+// max_atoms / max_rot: the library's largest ligand.
+cudaError_t launch_fk_table(const LigandsDev& lig, const Packed& pk, int max_atoms, int max_rot, cudaStream_t s);
 size_t dock_smem_bytes(int max_atoms, int max_rot, int max_frag, int rpc);
 bool dock_lanes_supported(int lanes);
 bool dock_shape_supported(int lanes, int fmt);

@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(32, 16) grad_lane_kernel(const GradArgs a) {
   const int plen = 7 + n;
   const size_t off = (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * plen;
   bool ok = a.pk.status[l] == 0 && lg_check(a.grid.check, N <= acap && n <= ncap, kChkItemShape);
-  if (ok) ok = lg_check(a.grid.check, fk_stage<true>(a.pk, a0, N, r0, n, S, lane), kChkAtomIndex);
+  if (ok) ok = lg_check(a.grid.check, fk_load(a.pk, l, a0, N, r0, n, S, lane), kChkAtomIndex);
   if (!ok) {   // uniform over the warp (one ligand)
     if (own && sub == 0) a.out_scores[gp] = -INFINITY;
     if (!REFINE && own)

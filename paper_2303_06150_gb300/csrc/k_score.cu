@@ -147,26 +147,38 @@ __global__ void __launch_bounds__(32, 16) score_lane_kernel(const ScoreArgs a) {
   const bool own = p0 < a.P;
   const int p = own ? p0 : a.P - 1;
   const size_t gp = (size_t)l * a.P + p;
-  if (a.pk.status[l] != 0) {   // uniform over the warp (one ligand)
+  // the ligand's status and ranges read together (one round trip)
+  const int status = a.pk.status[l];
+  const int a0 = a.lig.atom_off[l], a1 = a.lig.atom_off[l + 1];
+  const int r0 = a.lig.rot_off[l], r1 = a.lig.rot_off[l + 1];
+  const int N = a1 - a0, n = r1 - r0;
+  if (status != 0 || !lg_check(a.grid.check, N <= acap && n <= ncap, kChkItemShape)) {   // uniform
     if (own && sub == 0) a.out_scores[gp] = -INFINITY;
     return;
   }
-  const int a0 = a.lig.atom_off[l];
-  const int N = a.lig.atom_off[l + 1] - a0;
-  const int r0 = a.lig.rot_off[l];
-  const int n = a.lig.rot_off[l + 1] - r0;
-  if (!lg_check(a.grid.check, N <= acap && n <= ncap, kChkItemShape)) {
-    if (own && sub == 0) a.out_scores[gp] = -INFINITY;
-    return;
-  }
+  // The pose read before the ligand is staged, so that its loads overlap the
+  // staging: t and q into registers, theta_b into element 0 of the pose's
+  // transform slot b (read there by fk_transforms before it writes the slot),
+  // instead of one dependent load per bond inside the forward kinematics.
   const float* pose = a.poses + (size_t)a.P * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
-  if (!lg_check(a.grid.check, fk_stage(a.pk, a0, N, r0, n, S, lane), kChkAtomIndex)) {
+  const size_t stride = (size_t)PW * 12;   // between a pose's transform slots
+  float* Tg = T + 12 * grp;
+  float pt[3], pq[4];
+  if (sub == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) pt[k] = pose[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pq[k] = pose[3 + k];
+#pragma unroll 4
+    for (int b = 0; b < n; ++b) Tg[(size_t)b * stride] = pose[7 + b];
+  }
+  if (!lg_check(a.grid.check, fk_load(a.pk, l, a0, N, r0, n, S, lane), kChkAtomIndex)) {
     if (own && sub == 0) a.out_scores[gp] = -INFINITY;
     return;
   }
   if (sub == 0) {
-    const Quat q = qnormalize({pose[3], pose[4], pose[5], pose[6]});
-    fk_transforms(S, n, pose, q, pose + 7, a.origin, a.inv_h, T + 12 * grp, (size_t)PW * 12);
+    const Quat q = qnormalize({pq[0], pq[1], pq[2], pq[3]});
+    fk_transforms(S, n, pt, q, Tg, stride, a.origin, a.inv_h, Tg, stride);
   }
   if (G > 1) __syncwarp();
   // samples: unconditional loads, 8 gathers in flight per lane
@@ -198,7 +210,53 @@ cudaError_t launch_sl(const ScoreArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// One warp per ligand: the ligand staged as fk_stage<true> stages it, then
+// the parts the scoring and gradient kernels read (owners, parents, orders,
+// depth offsets, axes) written to the table, with the malformed flag.
+constexpr int kTabWarps = 4;
+
+__global__ void __launch_bounds__(32 * kTabWarps) fk_table_kernel(const LigandsDev lig, const Packed pk, int acap,
+                                                                  int ncap) {
+  extern __shared__ __align__(16) unsigned char tab_smem[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = blockIdx.x * kTabWarps + w;
+  if (l >= lig.L) return;   // uniform over the warp
+  const size_t per = fk_ligand_carve(acap, ncap, nullptr, nullptr);
+  FkLigand S;
+  fk_ligand_carve(acap, ncap, tab_smem + (size_t)w * per, &S);
+  uint8_t* row = pk.fk_loff + (size_t)l * kFkLoffBytes;
+  const int a0 = lig.atom_off[l], N = lig.atom_off[l + 1] - a0;
+  const int r0 = lig.rot_off[l], n = lig.rot_off[l + 1] - r0;
+  bool ok = pk.status[l] == 0 && N >= 1 && N <= acap && n >= 0 && n <= ncap;
+  if (ok) ok = fk_stage<true>(pk, a0, N, r0, n, S, lane);
+  if (!ok) {   // nothing of the ligand is read: only the flag
+    if (lane < kFkLoffBytes) row[lane] = lane == kFkBad ? 1 : 0;
+    if (lane + 32 < kFkLoffBytes) row[lane + 32] = lane + 32 == kFkBad ? 1 : 0;
+    return;
+  }
+  for (int i = lane; i < N; i += 32) pk.fk_own[a0 + i] = S.own[i];
+  for (int b = lane; b < n; b += 32) {
+    pk.fk_ax[r0 + b] = S.ax[b];
+    pk.fk_bond[r0 + b] = make_uchar4(S.par[b], S.ord[b], S.lord[b], 0);
+  }
+  const int depths = S.loff[LIGEN_MAX_ROT];
+  for (int k = lane; k < kFkLoffBytes; k += 32)
+    row[k] = k <= depths || k == LIGEN_MAX_ROT ? S.loff[k] : 0;   // k == kFkBad: 0
+}
+
 }  // namespace
+
+cudaError_t launch_fk_table(const LigandsDev& lig, const Packed& pk, int max_atoms, int max_rot, cudaStream_t s) {
+  if (lig.L == 0) return cudaSuccess;
+  const size_t smem = (size_t)kTabWarps * fk_ligand_carve(max_atoms, max_rot, nullptr, nullptr);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fk_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned blocks = (unsigned)((lig.L + kTabWarps - 1) / kTabWarps);
+  fk_table_kernel<<<blocks, 32 * kTabWarps, smem, s>>>(lig, pk, max_atoms, max_rot);
+  return cudaGetLastError();
+}
 
 // One lane per pose. Measured on GB300, scoring the 600,000 kept screening
 // poses: 0.255 ms with 1 lane per pose, 0.275 ms with 2 (one transform set

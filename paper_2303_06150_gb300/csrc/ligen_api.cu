@@ -623,6 +623,27 @@ void plan_score(const int32_t* h_rot_off, int L, ScorePlan* sp) {
   for (int l = 0; l < L; ++l) sp->list[fill[score_class_of(h_rot_off[l + 1] - h_rot_off[l])]++] = l;
 }
 
+// Regions of the forward-kinematics table (Packed::fk_*) in an arena.
+struct FkRegions {
+  size_t own = 0, bond = 0, ax = 0, loff = 0;
+};
+
+FkRegions take_fk(Arena& ar, const LibShape& sh, int L) {
+  FkRegions r;
+  r.own = ar.take((size_t)sh.atoms);
+  r.bond = ar.take(4 * (size_t)sh.rot);
+  r.ax = ar.take(16 * (size_t)sh.rot);
+  r.loff = ar.take((size_t)kFkLoffBytes * L);
+  return r;
+}
+
+void set_fk(const Arena& ar, const FkRegions& r, Packed* pk) {
+  pk->fk_own = ar.at<uint8_t>(r.own);
+  pk->fk_bond = ar.at<uchar4>(r.bond);
+  pk->fk_ax = ar.at<float4>(r.ax);
+  pk->fk_loff = ar.at<uint8_t>(r.loff);
+}
+
 // The launches launch(i, stream), i = 0 .. n-1, forked from `s` onto side
 // streams and joined back (on `s` itself when n == 1), so that the classes'
 // launches run side by side and one's ragged last wave overlaps another's
@@ -665,10 +686,13 @@ int used_classes(const ScorePlan& sp, int* used) {
 // concurrent (d_list = the plan's list on the device; base.max_atoms the
 // call's largest ligand), or in one group-per-pose launch.
 int run_score(const ScoreArgs& base, const ScorePlan& sp, const int32_t* d_list, cudaStream_t s) {
-  if (base.P < kLanePosesMin) {
+  if (base.P < kLanePosesMin) {   // reads the moving-atom lists
+    if (!base.pk.frag) return fail(LIGEN_ERR_CUDA, "internal: scoring without the moving-atom lists");
     LG_CUDA(launch_score(base, s));
     return LIGEN_OK;
   }
+  if (!base.pk.fk_own || !base.pk.fk_bond || !base.pk.fk_ax || !base.pk.fk_loff)
+    return fail(LIGEN_ERR_CUDA, "internal: pose-per-lane scoring without the forward-kinematics table");
   int used[kScoreClasses];
   const int nu = used_classes(sp, used);
   return run_forked(nu, s, [&](int i, cudaStream_t st) {
@@ -1036,7 +1060,7 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
   const size_t pose_floats = (size_t)poses_per_ligand * (7 * (size_t)L + sh.rot);
   const size_t nscores = (size_t)poses_per_ligand * L;
   ScorePlan plan;
-  if (poses_per_ligand >= kLanePosesMin) plan_score(ligands->h_rot_off, L, &plan);
+  if (poses_per_ligand >= kLanePosesMin) plan_score(ligands->h_rot_off, L, &plan);   // pose-per-lane launches
   Arena ar;
   LigandPlan lp;
   plan_ligands(ar, ligands, sh, lhost == 1, &lp);
@@ -1047,6 +1071,8 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
   const size_t o_frag = ar.take((size_t)kFragStride * sh.rot);
   const size_t o_status = ar.take(4 * (size_t)L);
   const size_t o_list = ar.take(4 * plan.list.size());
+  const bool lanes = poses_per_ligand >= kLanePosesMin;
+  const FkRegions o_fk = lanes ? take_fk(ar, sh, L) : FkRegions{};
   size_t o_poses = 0, o_scores = 0;
   if (ohost) {
     o_poses = ar.take(4 * pose_floats);
@@ -1078,6 +1104,10 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid, 
   pk.frag = ar.at<uint8_t>(o_frag);
   pk.status = ar.at<int32_t>(o_status);
   LG_CUDA(launch_pack(lig, grid->nc, pk, s));
+  if (lanes) {
+    set_fk(ar, o_fk, &pk);
+    LG_CUDA(launch_fk_table(lig, pk, sh.max_atoms, sh.max_rot, s));
+  }
   ScoreArgs sa{};
   sa.lig = lig;
   sa.pk = pk;
@@ -1120,9 +1150,10 @@ int ligen_prepare_scoring(const ligen_ligands_t* ligands, const ligen_grid_t* gr
   const size_t k_coef = keep.take(grid_coef_bytes(grid));
   const size_t k_xc = keep.take(16 * (size_t)sh.atoms);
   const size_t k_binfo = keep.take(4 * (size_t)sh.rot);
-  const size_t k_frag = keep.take((size_t)kFragStride * sh.rot);
+  const size_t k_frag = keep.take((size_t)kFragStride * sh.rot);   // the group-per-pose kernel reads the lists
   const size_t k_status = keep.take(4 * (size_t)L);
   const size_t k_list = keep.take(4 * (size_t)L);
+  const FkRegions k_fk = take_fk(keep, sh, L);
   const size_t limit = g_ws_limit.load();
   if (limit && keep.used > limit)
     return fail(LIGEN_ERR_OOM, "prepared inputs of %zu bytes exceed the limit of %zu bytes", keep.used, limit);
@@ -1171,6 +1202,7 @@ int ligen_prepare_scoring(const ligen_ligands_t* ligands, const ligen_grid_t* gr
   h->pk.binfo = keep.at<uchar4>(k_binfo);
   h->pk.frag = keep.at<uint8_t>(k_frag);
   h->pk.status = keep.at<int32_t>(k_status);
+  set_fk(keep, k_fk, &h->pk);
   h->d_list = keep.at<int32_t>(k_list);
   cudaError_t ce = cudaSuccess;
   if (L) {
@@ -1182,6 +1214,7 @@ int ligen_prepare_scoring(const ligen_ligands_t* ligands, const ligen_grid_t* gr
   }
   if (ce == cudaSuccess) ce = launch_grid_prep(gvals, grid->nx, grid->ny, grid->nz, grid->nc, h->coef, s);
   if (ce == cudaSuccess && L) ce = launch_pack(lig, grid->nc, h->pk, s);
+  if (ce == cudaSuccess && L) ce = launch_fk_table(lig, h->pk, sh.max_atoms, sh.max_rot, s);
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "preparing the scoring inputs"));
   // Host inputs are copied through the workspace asynchronously: wait for
   // the copies, so the caller may reuse its host buffers on return.
@@ -1304,6 +1337,7 @@ static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, i
   const bool lanes = poses_per_ligand >= kGradLanePosesMin;
   if (lanes) plan_score(ligands->h_rot_off, L, &plan);
   const size_t o_list = ar.take(4 * plan.list.size());
+  const FkRegions o_fk = lanes ? take_fk(ar, sh, L) : FkRegions{};
   size_t o_poses = 0, o_scores = 0, o_grads = 0, o_acc = 0;
   if (ohost) {
     o_poses = ar.take(4 * pose_floats);
@@ -1335,6 +1369,10 @@ static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, i
   pk.frag = ar.at<uint8_t>(o_frag);
   pk.status = ar.at<int32_t>(o_status);
   LG_CUDA(launch_pack(lig, grid->nc, pk, s));
+  if (lanes) {
+    set_fk(ar, o_fk, &pk);
+    LG_CUDA(launch_fk_table(lig, pk, sh.max_atoms, sh.max_rot, s));
+  }
   GradArgs ga{};
   ga.lig = lig;
   ga.pk = pk;
@@ -1363,6 +1401,8 @@ static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, i
     LG_CUDA(launch_grad(ga, refine != 0, s));
   } else {   // pose groups on forward kinematics, class by class
     LG_CUDA(cudaMemcpyAsync(ar.base + o_list, plan.list.data(), 4 * plan.list.size(), cudaMemcpyHostToDevice, s));
+    if (!pk.fk_own || !pk.fk_bond || !pk.fk_ax || !pk.fk_loff)
+      return fail(LIGEN_ERR_CUDA, "internal: pose-group gradients without the forward-kinematics table");
     int used[kScoreClasses];
     const int nu = used_classes(plan, used);
     rc = run_forked(nu, s, [&](int i, cudaStream_t st) {
