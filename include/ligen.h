@@ -324,7 +324,15 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
  * the interaction strength of an already docked ligand.
  * Same pose packing as ligen_dock_batch with K = poses_per_ligand:
  * out_scores[l][p] = S of pose p of ligand l, or -INFINITY for an invalid
- * ligand. `poses` and `out_scores` share one memory space. */
+ * ligand. `poses` and `out_scores` share one memory space. With 16 or more
+ * poses per ligand the ligands are scored by rotatable-bond class (0, 2, 4,
+ * 6, 8, 12, 16, 24, 32 bonds at most), one pose per lane, the classes'
+ * launches on forked streams, the sequence captured once into a CUDA graph
+ * per (stream, call shape) and replayed; on the legacy or per-thread
+ * default stream the graph runs on a side stream ordered after `stream` and
+ * before its next work by events, and on a stream that is being captured
+ * the launches go into the caller's graph. ligen_release_workspaces() frees
+ * the cached graphs. */
 int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                       int32_t poses_per_ligand, const float* poses, float out_penalty,
                       float* out_scores, void* stream);
@@ -336,14 +344,16 @@ int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
  * counterpart; it is the scoring of ligen_score_poses split into its
  * per-input and per-pose parts.
  *   ligen_prepare_scoring  builds, on `stream`, the FP32 grid records, the
- *          packed library and the scoring plan in one device allocation
+ *          packed library, the forward-kinematics table (each atom's
+ *          owning bond, each bond's parent, the bonds parents first and by
+ *          depth, the bond axes) and the scoring plan in one device allocation
  *          owned by the returned handle (*out; NULL on error). Ligands and
  *          grid may be host or device memory; the handle keeps no pointer
  *          to them (host inputs: the call waits for their copies).
  *          LIGEN_ERR_OOM when the allocation fails or exceeds the
  *          ligen_set_workspace_limit cap.
  *   ligen_score_prepared   ligen_score_poses on the prepared inputs (same
- *          poses packing, outputs and results); `poses` and `out_scores`
+ *          poses packing, outputs, results, launches and graphs); `poses` and `out_scores`
  *          in one memory space. Stream-ordered after the preparation when
  *          on the same stream; otherwise the caller orders the streams.
  *          Must run on the device the handle was prepared on.

@@ -178,8 +178,15 @@ cudaError_t dock_occupancy(int lanes, int n_theta, int fmt, int rpc, size_t smem
 cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s);
 // Pose-per-lane scoring of the ligands a.list[0 .. n_list) (all of them at
-// most a.max_atoms atoms), 32 poses per warp.
-cudaError_t launch_score_lanes(const ScoreArgs& a, cudaStream_t s);
+// most a.max_atoms atoms and a.max_rot bonds), 32 poses per warp: the launch
+// shape (sets the kernel's shared-memory limit; no stream work, so it is
+// called before a graph capture), then the launch.
+struct LaunchCfg {
+  unsigned blocks = 0;
+  size_t smem = 0;
+};
+cudaError_t score_lanes_config(const ScoreArgs& a, LaunchCfg* c);
+cudaError_t launch_score_lanes(const ScoreArgs& a, const LaunchCfg& c, cudaStream_t s);
 cudaError_t launch_rescore(const RescoreArgs& a, cudaStream_t s);
 size_t grad_smem_bytes(int max_atoms);
 // refine = false: dS/dpose of every pose; true: gradient refinement in place.

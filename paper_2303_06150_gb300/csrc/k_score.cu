@@ -13,6 +13,8 @@
 // whose ligand has one pose left shadows it in the spare group, which
 // writes nothing.
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "../../include/ligen.h"
 #include "internal.h"
@@ -129,18 +131,13 @@ __host__ __device__ inline size_t lane_carve(int acap, int ncap, unsigned char* 
   return tbytes + fk_ligand_carve(acap, ncap, base ? base + tbytes : nullptr, S);
 }
 
+// Work item gw = (ligand entry, 32/G poses) of the warp.
 template <int G>
-__global__ void __launch_bounds__(32, 16) score_lane_kernel(const ScoreArgs a) {
+__device__ __forceinline__ void score_lane_item(const ScoreArgs& a, size_t gw, const FkLigand& S, float* T) {
   constexpr int PW = 32 / G;   // poses per warp
-  extern __shared__ __align__(16) unsigned char lane_smem[];
   const int acap = a.max_atoms, ncap = a.max_rot;
-  FkLigand S;
-  float* T;
-  lane_carve<G>(acap, ncap, lane_smem, &S, &T);
   const int lane = threadIdx.x & 31, grp = lane / G, sub = lane % G;
   const int wpl = (a.P + PW - 1) / PW;    // warps per ligand
-  const size_t gw = blockIdx.x;
-  if (gw >= (size_t)a.n_list * wpl) return;
   const int li = (int)(gw / wpl);
   const int l = a.list ? a.list[li] : li;
   const int p0 = (int)(gw % wpl) * PW + grp;
@@ -198,16 +195,58 @@ __global__ void __launch_bounds__(32, 16) score_lane_kernel(const ScoreArgs a) {
   if (own && sub == 0) a.out_scores[gp] = acc;
 }
 
+// Persistent: a one-warp CTA per resident slot, taking work items
+// blockIdx.x, blockIdx.x + gridDim.x, ... (one CTA per item left the
+// block scheduler starting 20,000 one-warp CTAs per call).
 template <int G>
-cudaError_t launch_sl(const ScoreArgs& a, cudaStream_t s) {
-  const size_t smem = lane_carve<G>(a.max_atoms, a.max_rot, nullptr, nullptr, nullptr);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(score_lane_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+__global__ void __launch_bounds__(32, 16) score_lane_kernel(const ScoreArgs a) {
+  extern __shared__ __align__(16) unsigned char lane_smem[];
+  FkLigand S;
+  float* T;
+  lane_carve<G>(a.max_atoms, a.max_rot, lane_smem, &S, &T);
+  const size_t items = (size_t)a.n_list * ((a.P + 32 / G - 1) / (32 / G));
+  for (size_t gw = blockIdx.x; gw < items; gw += gridDim.x) {
+    score_lane_item<G>(a, gw, S, T);
+    __syncwarp();   // every lane done with this item's staged ligand and transforms
   }
-  const size_t blocks = (size_t)a.n_list * ((a.P + 32 / G - 1) / (32 / G));
-  score_lane_kernel<G><<<(unsigned)blocks, 32, smem, s>>>(a);
-  return cudaGetLastError();
+}
+
+// Resident CTAs of score_lane_kernel<G> for `smem` bytes, per device and
+// carve-up size, queried once (the first query also sets the kernel's
+// shared-memory limit to the largest carve-up any call can ask for, the
+// same value every time).
+template <int G>
+cudaError_t slots_sl(size_t smem, size_t* slots) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, size_t> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find({dev, smem});
+  if (it != cache.end()) {
+    *slots = it->second;
+    return cudaSuccess;
+  }
+  const size_t cap = lane_carve<G>(LIGEN_MAX_ATOMS, LIGEN_MAX_ROT, nullptr, nullptr, nullptr);
+  int nsm = 0, per_sm = 0;
+  e = cudaFuncSetAttribute(score_lane_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, score_lane_kernel<G>, 32, smem);
+  if (e != cudaSuccess) return e;
+  *slots = cache[{dev, smem}] = (size_t)nsm * (per_sm > 0 ? per_sm : 1);
+  return cudaSuccess;
+}
+
+template <int G>
+cudaError_t config_sl(const ScoreArgs& a, LaunchCfg* c) {
+  c->smem = lane_carve<G>(a.max_atoms, a.max_rot, nullptr, nullptr, nullptr);
+  size_t slots = 0;
+  const cudaError_t e = slots_sl<G>(c->smem, &slots);
+  if (e != cudaSuccess) return e;
+  const size_t items = (size_t)a.n_list * ((a.P + 32 / G - 1) / (32 / G));
+  c->blocks = (unsigned)(items < slots ? items : slots);
+  return cudaSuccess;
 }
 
 // One warp per ligand: the ligand staged as fk_stage<true> stages it, then
@@ -261,10 +300,14 @@ cudaError_t launch_fk_table(const LigandsDev& lig, const Packed& pk, int max_ato
 // One lane per pose. Measured on GB300, scoring the 600,000 kept screening
 // poses: 0.255 ms with 1 lane per pose, 0.275 ms with 2 (one transform set
 // per pose, half the shared memory per warp, half of each lane's samples)
-// and 0.38 ms with 4.
-cudaError_t launch_score_lanes(const ScoreArgs& a, cudaStream_t s) {
-  if ((size_t)a.n_list * a.P == 0) return cudaSuccess;
-  return launch_sl<1>(a, s);
+// and 0.38 ms with 4 (class launches one after another); 0.169 against
+// 0.207 ms for 1 and 2 lanes with the class launches side by side.
+cudaError_t score_lanes_config(const ScoreArgs& a, LaunchCfg* c) { return config_sl<1>(a, c); }
+
+cudaError_t launch_score_lanes(const ScoreArgs& a, const LaunchCfg& c, cudaStream_t s) {
+  if ((size_t)a.n_list * a.P == 0 || c.blocks == 0) return cudaSuccess;
+  score_lane_kernel<1><<<c.blocks, 32, c.smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s) {

@@ -439,10 +439,11 @@ struct Fork {
 };
 std::mutex g_fork_mu;
 std::map<std::pair<int, cudaStream_t>, Fork> g_fork;
+std::map<std::pair<int, cudaStream_t>, Fork> g_fence;   // graph launches for uncapturable streams
 
-int get_fork(int dev, cudaStream_t s, int n, Fork** out) {
+int get_fork(int dev, cudaStream_t s, int n, Fork** out, bool fence = false) {
   std::lock_guard<std::mutex> lk(g_fork_mu);
-  Fork& f = g_fork[{dev, s}];
+  Fork& f = (fence ? g_fence : g_fork)[{dev, s}];
   if (!f.start) LG_CUDA(cudaEventCreateWithFlags(&f.start, cudaEventDisableTiming));
   while ((int)f.streams.size() < n) {
     cudaStream_t st;
@@ -506,10 +507,65 @@ int issue_groups(const std::vector<DockArgs>& args, const std::vector<int>& ctas
   return LIGEN_OK;
 }
 
+// issue(stream) replayed from a cached CUDA graph keyed by `key` (every
+// pointer, size and shape the launches capture by value), captured on its
+// first use: on `s`, or, where `s` cannot be captured (the legacy or
+// per-thread default stream), on a side stream fenced to `s` by events. When
+// `s` is already capturing, the launches are issued into the caller's graph.
+template <class F>
+int run_graphed(int dev, cudaStream_t s, const std::string& key, F&& issue) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  LG_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return issue(s);
+  const bool fence = s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread;
+  Fork* f = nullptr;
+  cudaStream_t gs = s;
+  if (fence) {
+    int rc = get_fork(dev, s, 1, &f, true);
+    if (rc != LIGEN_OK) return rc;
+    gs = f->streams[0];
+    LG_CUDA(cudaEventRecord(f->start, s));
+    LG_CUDA(cudaStreamWaitEvent(gs, f->start, 0));
+  }
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto& e : g_graphs[{dev, gs}])
+      if (e.key == key) exec = e.exec;
+  }
+  if (!exec) {
+    LG_CUDA(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    int rc = issue(gs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(gs, &graph);
+    if (rc != LIGEN_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto& v = g_graphs[{dev, gs}];
+    if (v.size() >= kGraphsPerStream) {
+      cudaGraphExecDestroy(v.front().exec);
+      v.erase(v.begin());
+    }
+    v.push_back({key, exec});
+  }
+  LG_CUDA(cudaGraphLaunch(exec, gs));
+  if (fence) {
+    LG_CUDA(cudaEventRecord(f->done[0], gs));
+    LG_CUDA(cudaStreamWaitEvent(s, f->done[0], 0));
+  }
+  return LIGEN_OK;
+}
+
 // The bucketed layout: one persistent launch per group, sized by Eq. 1
 // (b blocks per SM from the occupancy query, times the SM count), or with
 // `persistent` false one CTA per work item; run from a cached CUDA graph
-// when `s` can be captured.
+// (run_graphed).
 int run_bucketed(const DockArgs& base, const std::vector<Group>& groups, int32_t* d_order, int* d_queue,
                  bool persistent, cudaStream_t s) {
   int dev = 0, nsm = 0;
@@ -544,42 +600,8 @@ int run_bucketed(const DockArgs& base, const std::vector<Group>& groups, int32_t
     ctas.push_back(persistent ? (int)std::min<int64_t>((int64_t)b * nsm, a.n_items) : a.n_items);
     args.push_back(a);
   }
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  LG_CUDA(cudaStreamIsCapturing(s, &cs));
-  const bool can_graph = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread &&
-                         cs == cudaStreamCaptureStatusNone;
-  if (!can_graph) return issue_groups(args, ctas, dev, s);
-
-  const std::string key = launch_key(args, ctas);
-  cudaGraphExec_t exec = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_graph_mu);
-    for (auto& e : g_graphs[{dev, s}])
-      if (e.key == key) exec = e.exec;
-  }
-  if (!exec) {
-    LG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    int rc = issue_groups(args, ctas, dev, s);
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(s, &graph);
-    if (rc != LIGEN_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return rc;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    std::lock_guard<std::mutex> lk(g_graph_mu);
-    auto& v = g_graphs[{dev, s}];
-    if (v.size() >= kGraphsPerStream) {
-      cudaGraphExecDestroy(v.front().exec);
-      v.erase(v.begin());
-    }
-    v.push_back({key, exec});
-  }
-  LG_CUDA(cudaGraphLaunch(exec, s));
-  return LIGEN_OK;
+  return run_graphed(dev, s, launch_key(args, ctas),
+                     [&](cudaStream_t st) { return issue_groups(args, ctas, dev, st); });
 }
 
 // ------------------------------------------------------------- scoring --
@@ -682,9 +704,31 @@ int used_classes(const ScorePlan& sp, int* used) {
   return nu;
 }
 
+std::string score_key(const ScoreArgs& b, const int32_t* d_list, const int* used, int nu, const LaunchCfg* cfg,
+                      const ScorePlan& sp) {
+  std::string k;
+  const void* ptrs[] = {b.lig.atom_off, b.lig.rot_off, b.pk.xc, b.pk.binfo, b.pk.frag, b.pk.status, b.pk.fk_own,
+                        b.pk.fk_bond, b.pk.fk_ax, b.pk.fk_loff, b.grid.coef, b.grid.check, b.poses, b.out_scores,
+                        d_list};
+  append_key(k, ptrs, sizeof ptrs);
+  const int ints[] = {b.lig.L, b.grid.cx, b.grid.cy, b.grid.cz, b.grid.nc, b.P, b.max_atoms, nu};
+  append_key(k, ints, sizeof ints);
+  const float fl[] = {b.grid.mx, b.grid.my, b.grid.mz, b.grid.penalty, b.origin[0], b.origin[1], b.origin[2], b.inv_h};
+  append_key(k, fl, sizeof fl);
+  append_key(k, &b.grid.n_rec, sizeof b.grid.n_rec);
+  for (int i = 0; i < nu; ++i) {
+    const int c = used[i];
+    const int ci[] = {c, sp.start[c], sp.n[c], (int)cfg[i].blocks};
+    append_key(k, ci, sizeof ci);
+    append_key(k, &cfg[i].smem, sizeof cfg[i].smem);
+  }
+  return k;
+}
+
 // Every ligand of base.lig scored: class by class, the classes' launches
-// concurrent (d_list = the plan's list on the device; base.max_atoms the
-// call's largest ligand), or in one group-per-pose launch.
+// side by side (d_list = the plan's list on the device; base.max_atoms the
+// call's largest ligand) and replayed from a cached CUDA graph, or in one
+// group-per-pose launch.
 int run_score(const ScoreArgs& base, const ScorePlan& sp, const int32_t* d_list, cudaStream_t s) {
   if (base.P < kLanePosesMin) {   // reads the moving-atom lists
     if (!base.pk.frag) return fail(LIGEN_ERR_CUDA, "internal: scoring without the moving-atom lists");
@@ -695,13 +739,20 @@ int run_score(const ScoreArgs& base, const ScorePlan& sp, const int32_t* d_list,
     return fail(LIGEN_ERR_CUDA, "internal: pose-per-lane scoring without the forward-kinematics table");
   int used[kScoreClasses];
   const int nu = used_classes(sp, used);
-  return run_forked(nu, s, [&](int i, cudaStream_t st) {
+  ScoreArgs args[kScoreClasses];
+  LaunchCfg cfg[kScoreClasses];
+  for (int i = 0; i < nu; ++i) {
     const int c = used[i];
-    ScoreArgs a = base;
-    a.list = d_list + sp.start[c];
-    a.n_list = sp.n[c];
-    a.max_rot = kScoreRotCap[c];
-    return launch_score_lanes(a, st);
+    args[i] = base;
+    args[i].list = d_list + sp.start[c];
+    args[i].n_list = sp.n[c];
+    args[i].max_rot = kScoreRotCap[c];
+    LG_CUDA(score_lanes_config(args[i], &cfg[i]));
+  }
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  return run_graphed(dev, s, score_key(base, d_list, used, nu, cfg, sp), [&](cudaStream_t gs) {
+    return run_forked(nu, gs, [&](int i, cudaStream_t st) { return launch_score_lanes(args[i], cfg[i], st); });
   });
 }
 
