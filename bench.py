@@ -42,6 +42,16 @@ WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 BYTES_PER_SAMPLE = 32   # one trilinear sample = one 32-byte record of 8 FP32 coefficients
 
 
+SCORE_ROT_CAPS = (0, 2, 4, 6, 8, 12, 16, 24, 32)   # rotatable-bond classes of the pose-per-lane launches
+
+
+def score_classes(lib) -> int:
+    """Launches of one pose-per-lane scoring or gradient call: one per
+    rotatable-bond class present in the library."""
+    import bisect
+    return len({bisect.bisect_left(SCORE_ROT_CAPS, int(n)) for n in np.diff(lib.rot_off)})
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -590,10 +600,11 @@ def run_ours(args):
             "relative_gain_mean": float(np.mean(gain / np.maximum(np.abs(b), 1e-6))),
             "improved_fraction": float((gain > 0).mean()),
             "best_pose_gain_mean": float((after.max(1).values - before.max(1).values).mean().item()),
-            "launches_per_call": 3,
+            "launches_per_call": 3 + score_classes(lib),
             "how": "top-16 poses per ligand of the sweep, normalised-step projected ascent "
-                   "(0.1 A, 0.02, 0.05 rad; halve on rejection); per call grid preparation, packer "
-                   "and one refinement launch, timed with CUDA events (best of 3)"}
+                   "(0.1 A, 0.02, 0.05 rad; halve on rejection); per call grid preparation, packer, "
+                   "forward-kinematics table and one refinement launch per rotatable-bond class "
+                   "(side by side on forked streams), timed with CUDA events (best of 3)"}
 
     if args.workload == "screen20k":
         # ligen_score_poses on the kept poses of the timed form (all K per ligand):
@@ -629,11 +640,14 @@ def run_ours(args):
             "frac_gather": n_samples / (ms_k * 1e-3) / probe32["loads_per_s"],
             "frac_l2": n_samples * 32 / (ms_k * 1e-3) / 1e9 / l2_stream,
             "gather_peak_loads_per_s": probe32["loads_per_s"],
+            "launches_per_call": score_classes(lib),
             "how": "ligen_score_poses on the kept poses of the timed form (20,000 ligands x top 30), FP32 grid "
-                   "records: 'ms' is the whole call (grid records, packer, scoring launches), 'kernel_ms' the "
-                   "scoring launches alone on inputs prepared once (ligen_score_prepared); CUDA events, best of "
-                   "3 and 10; frac_gather = atom samples/s over the 32-byte random-gather probe's loads/s, "
-                   "frac_l2 = 32 bytes per sample over the streaming L2 bandwidth"}
+                   "records: 'ms' is the whole call (grid records, packer, forward-kinematics table, scoring "
+                   "launches), 'kernel_ms' the whole ligen_score_prepared call on inputs prepared once (one "
+                   "launch per rotatable-bond class, side by side, replayed from a CUDA graph; host issue "
+                   "included); CUDA events, best of 3 and 10; frac_gather = atom samples/s over the 32-byte "
+                   "random-gather probe's loads/s, frac_l2 = 32 bytes per sample over the streaming L2 "
+                   "bandwidth"}
 
     if args.sites > 0 and args.workload == "screen20k":
         # the same library docked into several sites of one target in one call
