@@ -383,50 +383,76 @@ struct Group {
 // (R * (n_rigid * N + passes * n * n_theta * N / 4)), and the groups by
 // decreasing total cost, so the longest work starts first. `single`: one
 // group of every ligand (the single-queue layout), default shape, in the
-// same cost order.
+// same cost order. Four times the per-restart cost is an integer, so the
+// order (group, cost descending, ligand index) comes from a stable
+// counting sort in O(L) (the call waits for it before its first launch).
 void plan_groups(const ligen_ligands_t* g, const ligen_params_t* p, int dev, std::vector<int32_t>& order,
                  std::vector<Group>& groups, bool single = false) {
   const int L = g->n_ligands;
   const int nt = 360 / p->torsion_step_deg;
-  struct Item {
-    int32_t l;
-    double cost;
-  };
-  std::map<std::tuple<int, int, int>, std::vector<Item>> by;
+  // the group key (atom class, lanes, restarts per CTA) of every bucket,
+  // groups numbered in key order
+  std::tuple<int, int, int> bkey[LIGEN_N_BUCKETS];
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    for (int l = 0; l < L; ++l) {
-      const int N = g->h_atom_off[l + 1] - g->h_atom_off[l];
-      const int n = g->h_rot_off[l + 1] - g->h_rot_off[l];
-      const int ac = single ? 0 : atom_class_of(N);
-      TuneEntry t = single ? TuneEntry() : g_tune[dev][ac * 11 + rot_class_of(n)];
+    for (int b = 0; b < LIGEN_N_BUCKETS; ++b) {
+      TuneEntry t = single ? TuneEntry() : g_tune[dev][b];
       if (!dock_shape_supported(t.lanes, p->grid_format)) t = TuneEntry();   // default shape
-      const double cost = (double)N * p->n_rigid + (double)p->passes * n * nt * (0.25 * N + 1.0);
-      by[std::make_tuple(ac, t.lanes, t.rpc)].push_back({l, cost});
+      bkey[b] = std::make_tuple(single ? 0 : b / 11, t.lanes, t.rpc);
     }
   }
-  order.clear();
+  std::vector<std::tuple<int, int, int>> keys(bkey, bkey + LIGEN_N_BUCKETS);
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  int bgid[LIGEN_N_BUCKETS];
+  for (int b = 0; b < LIGEN_N_BUCKETS; ++b)
+    bgid[b] = (int)(std::lower_bound(keys.begin(), keys.end(), bkey[b]) - keys.begin());
+  const int G = (int)keys.size();
+  std::vector<uint32_t> inv(L);   // 2^32 - 1 - 4 x cost: ascending = cost descending
+  std::vector<uint8_t> gid(L);
+  for (int l = 0; l < L; ++l) {
+    const int N = g->h_atom_off[l + 1] - g->h_atom_off[l];
+    const int n = g->h_rot_off[l + 1] - g->h_rot_off[l];
+    const uint64_t c4 = 4ull * N * p->n_rigid + (uint64_t)p->passes * n * nt * (N + 4);
+    inv[l] = 0xffffffffu - (uint32_t)std::min<uint64_t>(c4, 0xffffffffull);
+    gid[l] = (uint8_t)bgid[atom_class_of(N) * 11 + rot_class_of(n)];
+  }
+  // LSD: the cost key's low and high 16 bits, then the group (each pass stable)
+  std::vector<int32_t> a(L), b(L);
+  for (int l = 0; l < L; ++l) a[l] = l;
+  auto pass = [&](int buckets, auto digit) {
+    std::vector<int> cnt((size_t)buckets + 1, 0);
+    for (int i = 0; i < L; ++i) ++cnt[digit(a[i]) + 1];
+    for (int k = 0; k < buckets; ++k) cnt[k + 1] += cnt[k];
+    for (int i = 0; i < L; ++i) b[cnt[digit(a[i])]++] = a[i];
+    a.swap(b);
+  };
+  pass(1 << 16, [&](int l) { return (int)(inv[l] & 0xffffu); });
+  pass(1 << 16, [&](int l) { return (int)(inv[l] >> 16); });
+  pass(G, [&](int l) { return (int)gid[l]; });
+  order.assign(a.begin(), a.end());
   groups.clear();
-  for (auto& kv : by) {
-    auto& items = kv.second;
-    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
+  for (int i = 0; i < L;) {
+    const int k = gid[order[i]];
     Group gr;
-    gr.lanes = std::get<1>(kv.first);
-    gr.rpc = std::get<2>(kv.first);
-    gr.beg = (int)order.size();
-    for (const Item& it : items) {
-      order.push_back(it.l);
-      const int N = g->h_atom_off[it.l + 1] - g->h_atom_off[it.l];
-      const int n = g->h_rot_off[it.l + 1] - g->h_rot_off[it.l];
+    gr.lanes = std::get<1>(keys[k]);
+    gr.rpc = std::get<2>(keys[k]);
+    gr.beg = i;
+    uint64_t c4sum = 0;
+    for (; i < L && gid[order[i]] == k; ++i) {
+      const int l = order[i];
+      const int N = g->h_atom_off[l + 1] - g->h_atom_off[l];
+      const int n = g->h_rot_off[l + 1] - g->h_rot_off[l];
       gr.max_atoms = std::max(gr.max_atoms, N);
       gr.max_rot = std::max(gr.max_rot, n);
       gr.max_frag = std::max(gr.max_frag, n * (N / 2));
-      gr.cost += it.cost;
+      c4sum += 0xffffffffu - inv[l];
     }
-    gr.end = (int)order.size();
+    gr.end = i;
+    gr.cost = 0.25 * (double)c4sum;
     groups.push_back(gr);
   }
-  std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.cost > b.cost; });
+  std::stable_sort(groups.begin(), groups.end(), [](const Group& x, const Group& y) { return x.cost > y.cost; });
 }
 
 // Side streams and events for the forked launches, per (device, calling
@@ -892,13 +918,12 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
   std::vector<int32_t> order;
   std::vector<Group> groups;
   size_t o_order = 0, o_queue = 0;
-  if (buckets) {
-    int dev = 0;
-    LG_CUDA(cudaGetDevice(&dev));
-    if (dev >= kMaxDev) return fail(LIGEN_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDev);
-    plan_groups(ligands, params, dev, order, groups, params->batching == LIGEN_BATCH_QUEUE);
+  int plan_dev = 0;
+  if (buckets) {   // the plan itself is made after the first launches (below)
+    LG_CUDA(cudaGetDevice(&plan_dev));
+    if (plan_dev >= kMaxDev) return fail(LIGEN_ERR_UNSUPPORTED, "device ordinal %d >= %d", plan_dev, kMaxDev);
     o_order = ar.take(4 * (size_t)L);
-    o_queue = ar.take(sizeof(int) * groups.size());
+    o_queue = ar.take(sizeof(int) * LIGEN_N_BUCKETS);   // at most one group per bucket
   }
   const size_t o_samples = params->samples ? ar.take(8 * (size_t)kSampleSlots) : 0;
   CallCheck chk;
@@ -998,6 +1023,9 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
       // carved the workspace differently and overwritten this region (a
       // grid of another record format, for one). Pageable source: the copy
       // is staged before cudaMemcpyAsync returns.
+      // planned here, on the first site, while the grid records and the
+      // packer run on the device
+      if (groups.empty()) plan_groups(ligands, params, plan_dev, order, groups, params->batching == LIGEN_BATCH_QUEUE);
       int32_t* d_order = ar.at<int32_t>(o_order);
       LG_CUDA(cudaMemcpyAsync(d_order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, s));
       if ((rc = run_bucketed(da, groups, d_order, ar.at<int>(o_queue),
