@@ -301,7 +301,9 @@ cudaError_t launch_fk_table(const LigandsDev& lig, const Packed& pk, int max_ato
 // poses: 0.255 ms with 1 lane per pose, 0.275 ms with 2 (one transform set
 // per pose, half the shared memory per warp, half of each lane's samples)
 // and 0.38 ms with 4 (class launches one after another); 0.169 against
-// 0.207 ms for 1 and 2 lanes with the class launches side by side.
+// 0.207 ms for 1 and 2 lanes with the class launches side by side; 2 lanes
+// for the classes of 12 or more bonds only (half the transform slots per
+// warp, more warps per SM): 0.156 against 0.151 ms, from 16 bonds the same.
 cudaError_t score_lanes_config(const ScoreArgs& a, LaunchCfg* c) { return config_sl<1>(a, c); }
 
 cudaError_t launch_score_lanes(const ScoreArgs& a, const LaunchCfg& c, cudaStream_t s) {
