@@ -8,8 +8,9 @@
 // and the owning lane marks it taken. Ligands with more restarts than the
 // registers hold rank from memory instead: round k takes the best restart
 // ranked after the one taken in round k-1, so no marks are needed. The
-// winner's pose is rebuilt from its restart index (random stream), its cube
-// rotation and its torsion counts and written as t[3], q[4] (w >= 0),
+// winners are taken 32 at a time and the j-th lane rebuilds the j-th
+// winner's pose from its restart index (random stream), its cube rotation
+// and its torsion counts, all 32 at once, written as t[3], q[4] (w >= 0),
 // theta[n] in [-pi, pi). A NaN score (only possible from a NaN grid) ranks as
 // -infinity, so the order stays total and K <= R rounds always find a
 // restart.
@@ -64,29 +65,42 @@ __global__ void __launch_bounds__(32 * kTopkWarps) topk_kernel(const TopkArgs a)
   }
   float last_s = INFINITY;
   int last_r = -1;
-  for (int k = 0; k < a.K; ++k) {
-    float bs = -INFINITY;
-    int br = 0x7fffffff;
-    if (in_regs) {
+  // K winners in chunks of 32: select the chunk's winners (lane j keeps
+  // the j-th), then every lane rebuilds its winner's pose at once
+  for (int k0 = 0; k0 < a.K; k0 += 32) {
+    const int kn = a.K - k0 < 32 ? a.K - k0 : 32;
+    float my_s = -INFINITY;
+    int my_r = 0;
+    for (int j = 0; j < kn; ++j) {
+      float bs = -INFINITY;
+      int br = 0x7fffffff;
+      if (in_regs) {
 #pragma unroll
-      for (int i = 0; i < kRegSlots; ++i) {
-        const int r = lane + 32 * i;
-        if (!(taken >> i & 1u) && (v[i] > bs || (v[i] == bs && r < br))) { bs = v[i]; br = r; }
+        for (int i = 0; i < kRegSlots; ++i) {
+          const int r = lane + 32 * i;
+          if (!(taken >> i & 1u) && (v[i] > bs || (v[i] == bs && r < br))) { bs = v[i]; br = r; }
+        }
+        warp_best(bs, br);
+        if ((br & 31) == lane && br < a.R) taken |= 1u << (br >> 5);
+      } else {
+        for (int r = lane; r < a.R; r += 32) {
+          const float s = isnan(rs[r]) ? -INFINITY : rs[r];
+          const bool after = (s < last_s) || (s == last_s && r > last_r);
+          if (after && (s > bs || (s == bs && r < br))) { bs = s; br = r; }
+        }
+        warp_best(bs, br);
       }
-      warp_best(bs, br);
-      if ((br & 31) == lane && br < a.R) taken |= 1u << (br >> 5);
-    } else {
-      for (int r = lane; r < a.R; r += 32) {
-        const float s = isnan(rs[r]) ? -INFINITY : rs[r];
-        const bool after = (s < last_s) || (s == last_s && r > last_r);
-        if (after && (s > bs || (s == bs && r < br))) { bs = s; br = r; }
+      if (br >= a.R) br = a.R - 1;   // unreachable while K <= R; keeps every index in range
+      last_s = bs;
+      last_r = br;
+      if (lane == j) {
+        my_s = bs;
+        my_r = br;
       }
-      warp_best(bs, br);
     }
-    if (br >= a.R) br = a.R - 1;   // unreachable while K <= R; keeps every index in range
-    last_s = bs;
-    last_r = br;
+    if (lane >= kn) continue;
     // rebuild the winner's pose
+    const int k = k0 + lane, br = my_r;
     float u[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) u[q] = restart_uniform(a.seed, (uint32_t)l, (uint32_t)br, (uint32_t)q);
@@ -95,23 +109,19 @@ __global__ void __launch_bounds__(32 * kTopkWarps) topk_kernel(const TopkArgs a)
     if (q.w < 0.f) q = {-q.w, -q.x, -q.y, -q.z};
     float* out = poses + (size_t)k * plen;
     const uint8_t* cnt = a.res_cnt + (size_t)r0 * a.R + (size_t)br * n;
-    for (int e = lane; e < plen; e += 32) {
-      float v;
-      if (e < 3) {
-        v = a.center[e] + (2.0f * u[3 + e] - 1.0f) * a.jitter;
-      } else if (e < 7) {
-        v = (e == 3) ? q.w : (e == 4) ? q.x : (e == 5) ? q.y : q.z;
-      } else {
-        int deg = ((int)cnt[e - 7] * a.step_deg) % 360;
-        if (deg >= 180) deg -= 360;
-        v = (float)deg * 0.017453292519943295f;
-      }
-      out[e] = v;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) out[e] = a.center[e] + (2.0f * u[3 + e] - 1.0f) * a.jitter;
+    out[3] = q.w;
+    out[4] = q.x;
+    out[5] = q.y;
+    out[6] = q.z;
+    for (int b = 0; b < n; ++b) {
+      int deg = ((int)cnt[b] * a.step_deg) % 360;
+      if (deg >= 180) deg -= 360;
+      out[7 + b] = (float)deg * 0.017453292519943295f;
     }
-    if (lane == 0) {
-      scores[k] = bs;
-      if (a.top_restart) a.top_restart[(size_t)l * a.K + k] = br;
-    }
+    scores[k] = my_s;
+    if (a.top_restart) a.top_restart[(size_t)l * a.K + k] = br;
   }
 }
 
