@@ -163,7 +163,9 @@ __global__ void __launch_bounds__(32 * kPackWarps) pack_kernel(const LigandsDev 
       const int u = child_moves ? par : child;
       const int lo = S.tin[child], hi = lo + sz;
       int cnt = 0;
-      for (int base = 0; base < kMaxN; base += 32) {
+      const int words = (N + 31) >> 5;   // mask words holding atoms; the rest are zero
+      if (out.fbits && lane >= words && lane < kMaxN / 32) out.fbits[(size_t)gb * 8 + lane] = 0u;
+      for (int base = 0; base < 32 * words; base += 32) {
         const int i = base + lane;
         bool mv = false;
         if (i < N) {
