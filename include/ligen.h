@@ -144,12 +144,15 @@ typedef struct ligen_grid {
  *                        class, Eq. 1's b x SM CTAs (b from the occupancy query)
  *                        and the lanes-per-restart / restarts-per-CTA shape
  *                        of the tuning table (ligen_tune_set, ligen_autotune);
- *                        the classes run on forked streams and the whole
- *                        sequence is captured once into a CUDA graph and
- *                        replayed while the call's shape is unchanged;
- *   LIGEN_BATCH_BUCKETS_STATIC  the same groups, shapes, streams and graph,
- *                        but each group is a plain launch of one CTA per
- *                        work item (no device counter): the static
+ *                        the classes run one after another (a class's
+ *                        CTAs keep their SMs until its queue is empty) and
+ *                        the whole sequence is captured once into a CUDA
+ *                        graph and replayed while the call's shape is
+ *                        unchanged;
+ *   LIGEN_BATCH_BUCKETS_STATIC  the same groups, shapes and graph, but each
+ *                        group is a plain launch of one CTA per work item
+ *                        (no device counter), the groups side by side on
+ *                        forked streams: the static
  *                        per-bucket launches the persistent form is
  *                        compared against;
  *   LIGEN_BATCH_QUEUE    the whole library in ONE persistent launch: one
