@@ -140,6 +140,8 @@ FORMS = {
     "bf16": dict(batching="plain", grid_format="bf16"),
     # FP16 records, then the K kept poses re-scored in FP64 and re-ranked (C3's re-score)
     "f16_rescore": dict(batching="plain", grid_format="f16", rescore_fp64=True),
+    # static per-bucket launches on FP16 records (timed on the bimodal library)
+    "f16_buckets_static": dict(batching="buckets_static", grid_format="f16"),
 }
 
 # FP32-pipe operations per atom sample of the sweep, counted from the samplers'
@@ -406,6 +408,11 @@ def bimodal_leg(args, lg, G_screen, screen_grid_spec, flush, stream, dev, rank, 
     steps = max(2, min(args.steps, 3))
     forms = ["plain", "buckets", "buckets_static", "queue", "f16"]
     timed = {f: time_dock(lg, L, G, dict(kw, **FORMS[f]), flush, stream, steps, 2, local, world) for f in forms}
+    # the tuning table holds one shape per bucket, for the record format it
+    # was timed with: retuned on FP16 records for the FP16 bucketed form
+    tuned16 = lg.autotune(L, G, sample=256, grid_format="f16", **kw)
+    timed["f16_buckets_static"] = time_dock(lg, L, G, dict(kw, **FORMS["f16_buckets_static"]), flush, stream,
+                                            steps, 2, local, world)
     out = {"workload": WORKLOAD_DESCS["bimodal200k"].replace("200,000", f"{lib.n_ligands:,}"),
            "ligands": lib.n_ligands, "steps": steps, "warmup": 2,
            "nominal_poses_per_step": poses_step, "nominal_samples_per_step": samples_step,
@@ -416,9 +423,11 @@ def bimodal_leg(args, lg, G_screen, screen_grid_spec, flush, stream, dev, rank, 
            "buckets_vs_static": timed["buckets_static"]["ms_total"] / timed["buckets"]["ms_total"],
            "queue_vs_buckets": timed["buckets"]["ms_total"] / timed["queue"]["ms_total"],
            "tuning": {str(b): list(v[:2]) for b, v in sorted(tuned.items())},
+           "tuning_f16": {str(b): list(v[:2]) for b, v in sorted(tuned16.items())},
            "clocks": timed["plain"]["clocks"],
            "how": "each form: 2 untimed calls, then steps calls with the L2 flushed before each, CUDA events "
-                  "on the launching stream; accuracy of the FP16 form is measured on the headline workload"}
+                  "on the launching stream; accuracy of the FP16 form is measured on the headline workload "
+                  "(the FP16 static-bucket form makes the FP16 plain launch's decisions, tested)"}
     del L, timed
     return out
 

@@ -303,7 +303,11 @@ int ligen_dock_batch_static(const ligen_ligands_t* ligands, const ligen_grid_t* 
  * lanes per restart (2, 4, 8, 16 or 32) and restarts per CTA (a multiple of
  * 32/lanes, lanes * restarts <= 128). Defaults: 8 lanes, 16 restarts. The
  * 16-bit grid formats run with 4 to 32 lanes; other shapes fall back to the
- * default. */
+ * default. The table keeps one shape per bucket whatever the record format;
+ * shapes tuned on one format can be far from the best on another (measured
+ * on GB300, the bimodal library's static per-bucket launches on FP16
+ * records with the FP32-tuned shapes: 1224 ms, against 836 ms for the plain
+ * FP16 launch), so tune with the format the bucketed calls will use. */
 int ligen_tune_set(int32_t bucket, int32_t lanes, int32_t restarts_per_cta);
 int ligen_tune_get(int32_t bucket, int32_t* lanes, int32_t* restarts_per_cta);
 

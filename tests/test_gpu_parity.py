@@ -162,6 +162,43 @@ def test_prepared_scoring_equals_score_poses(lg, screen_sample, K):
         prep.score(poses, K)
 
 
+def test_scoring_graph_paths_agree(lg, screen_sample):
+    """The class launches of pose-per-lane scoring replay from a cached CUDA
+    graph: on the legacy default stream through an event-fenced side stream,
+    on a user stream captured directly, and inside a caller's own capture
+    issued into that graph. Every path, first call and replay, gives the
+    same scores, and work queued before and after on the calling stream is
+    ordered around it."""
+    w, lib, grid = screen_sample
+    K = 30
+    rng = np.random.default_rng(21)
+    poses = torch.tensor(_random_poses(rng, lib, grid, K), dtype=torch.float32, device="cuda")
+    Ld, Gd = _dev(lg, lib, grid)
+    prep = lg.prepare_scoring(Ld, Gd)
+    ref = prep.score(poses, K)                      # default stream, first call: captured
+    assert torch.equal(prep.score(poses, K), ref)   # replayed
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        outs = [torch.full_like(ref, 7.0) for _ in range(3)]
+        for o in outs:
+            prep.score(poses, K, out=o)               # user stream: captured on it, then replayed
+        shifted = outs[-1] + 1.0                      # ordered after the scoring on `side`
+    torch.cuda.current_stream().wait_stream(side)
+    for o in outs:
+        assert torch.equal(o, ref)
+    assert torch.equal(shifted, ref + 1.0)
+    cap = torch.full_like(ref, 7.0)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):                          # the caller's own capture
+        prep.score(poses, K, out=cap)
+    cap.fill_(7.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(cap, ref)
+    prep.release()
+
+
 # ------------------------------------------------------------ docking ---
 def _dock_and_compare(lg, oracle_lib, w, lib, grid, restarts=None, ligands=None, device="cuda", fmt="f32"):
     s = dict(w["search"])
