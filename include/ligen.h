@@ -454,7 +454,10 @@ int ligen_probe_gather(const float* records, int64_t n_records, int32_t bytes_pe
 int ligen_probe_stream(const void* buffer, int64_t n_bytes, int32_t passes, float* sink, double* bytes_done,
                        float* ms_out, void* stream);
 
-/* Release every cached workspace of the calling thread's current device. */
+/* Release every cached workspace of the calling thread's current device,
+ * with the cached CUDA graphs and the side streams and events of the forked
+ * launches (created per calling stream on first use). Waits for the work on
+ * those streams. */
 int ligen_release_workspaces(void);
 
 /* Caps every internal workspace at `bytes` (<= 0: no cap, the default), for

@@ -840,6 +840,24 @@ int ligen_release_workspaces(void) {
       }
     }
   }
+  {   // side streams and events of the forked launches (a captured graph keeps no reference to them)
+    std::lock_guard<std::mutex> fl(g_fork_mu);
+    for (auto* m : {&g_fork, &g_fence}) {
+      for (auto it = m->begin(); it != m->end();) {
+        if (it->first.first == dev) {
+          for (cudaStream_t st : it->second.streams) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+          }
+          for (cudaEvent_t ev : it->second.done) cudaEventDestroy(ev);
+          if (it->second.start) cudaEventDestroy(it->second.start);
+          it = m->erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+  }
   std::lock_guard<std::mutex> lk(g_ws_mu);
   for (auto it = g_ws.begin(); it != g_ws.end();) {
     if (it->first.first == dev) {

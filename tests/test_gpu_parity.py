@@ -196,6 +196,15 @@ def test_scoring_graph_paths_agree(lg, screen_sample):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(cap, ref)
+    # releasing the workspaces frees the cached graphs and side streams; the
+    # next calls recreate them, and the caller's own graph still replays
+    lg.release_workspaces()
+    assert torch.equal(prep.score(poses, K), ref)
+    cap.fill_(7.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(cap, ref)
+    del g
     prep.release()
 
 
