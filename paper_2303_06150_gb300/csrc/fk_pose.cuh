@@ -153,20 +153,23 @@ __device__ inline bool fk_stage(const Packed& pk, int a0, int N, int r0, int n, 
 
 // Stage ligand l = (a0, N, r0, n) for the warp (all 32 lanes call it) from
 // the forward-kinematics table (pk.fk_*, written by fk_table_kernel with
-// fk_stage<true>): the same shared-memory contents as fk_stage<true>, but
-// for the moving-atom lists, which nothing reads after staging. Vector
-// copies, no per-bond passes. Returns false, on every lane, when the table
-// marks the ligand's lists as malformed.
+// fk_stage<true>): the contents fk_stage<true> builds, but for the
+// moving-atom lists (nothing reads them after staging), with the atoms
+// listed by owner (S.sx, S.own in the table's order) and S.sb[b].y the list
+// position of bond b's v (S.sb[b].x unused). Vector copies, no per-bond
+// passes. Returns false, on every lane, when the table marks the ligand's
+// lists as malformed.
 __device__ inline bool fk_load(const Packed& pk, int l, int a0, int N, int r0, int n, const FkLigand& S, int lane) {
   static_assert(kFkLoffBytes == 48 && kFkBad > LIGEN_MAX_ROT, "depth row of the table = the staged row");
   for (int i = lane; i < N; i += 32) {
-    S.sx[i] = pk.xc[a0 + i];
+    S.sx[i] = pk.fk_xs[a0 + i];
     S.own[i] = pk.fk_own[a0 + i];
   }
   for (int b = lane; b < n; b += 32) {
-    S.sb[b] = pk.binfo[r0 + b];
-    S.ax[b] = pk.fk_ax[r0 + b];
+    const uchar4 bi = pk.binfo[r0 + b];
     const uchar4 t = pk.fk_bond[r0 + b];
+    S.sb[b] = make_uchar4(0, t.w, bi.z, 0);
+    S.ax[b] = pk.fk_ax[r0 + b];
     S.par[b] = t.x;
     S.ord[b] = t.y;
     S.lord[b] = t.z;

@@ -33,9 +33,13 @@ struct Packed {
   uint32_t* touch;   // [sum n] optional: bit b of touch[b'] set when turning bond b'
                      // moves an atom bond b's sweep reads (bit b' always set)
   // Forward-kinematics table (fk_table_kernel; read by the pose-per-lane
-  // scoring and pose-group gradient kernels), optional:
-  uint8_t* fk_own;   // [sum N] owner of each atom: a bond, or n (the root frame)
-  uchar4* fk_bond;   // [sum n] (parent of bond j, j-th bond parents first, j-th bond by depth, 0)
+  // scoring and pose-group gradient kernels), optional. A ligand's atoms
+  // are listed by owner (bond 0's, bond 1's, ..., then the root frame's;
+  // input order within an owner):
+  float4* fk_xs;     // [sum N] centred input coordinates (w = type) in that order
+  uint8_t* fk_own;   // [sum N] owner of each listed atom: a bond, or n (the root frame)
+  uchar4* fk_bond;   // [sum n] (parent of bond j, j-th bond parents first, j-th bond by depth,
+                     //          list position of bond j's moving endpoint v)
   float4* fk_ax;     // [sum n] unit bond axes in the input conformation
   uint8_t* fk_loff;  // [L][kFkLoffBytes] first entry of each depth, depth count, malformed flag
 };

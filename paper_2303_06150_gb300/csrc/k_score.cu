@@ -178,13 +178,21 @@ __device__ __forceinline__ void score_lane_item(const ScoreArgs& a, size_t gw, c
     fk_transforms(S, n, pt, q, Tg, stride, a.origin, a.inv_h, Tg, stride);
   }
   if (G > 1) __syncwarp();
-  // samples: unconditional loads, 8 gathers in flight per lane
+  // samples: unconditional loads, 8 gathers in flight per lane. The atoms
+  // are listed by owner, so the owner's transform stays in registers across
+  // its atoms and is read again only where the owner changes (a uniform
+  // branch: every lane is at the same atom).
   float acc = 0.f;
+  int cur = -1;
+  float4 m0, m1, m2;
 #pragma unroll 8
   for (int i = sub; i < N; i += G) {
     const float4 X = S.sx[i];
-    float4 m0, m1, m2;
-    fk_get(T + ((size_t)S.own[i] * PW + grp) * 12, m0, m1, m2);
+    const int o = S.own[i];
+    if (o != cur) {
+      fk_get(T + ((size_t)o * PW + grp) * 12, m0, m1, m2);
+      cur = o;
+    }
     const float ux = fmaf(m0.x, X.x, fmaf(m0.y, X.y, fmaf(m0.z, X.z, m0.w)));
     const float uy = fmaf(m1.x, X.x, fmaf(m1.y, X.y, fmaf(m1.z, X.z, m1.w)));
     const float uz = fmaf(m2.x, X.x, fmaf(m2.y, X.y, fmaf(m2.z, X.z, m2.w)));
@@ -260,9 +268,11 @@ __global__ void __launch_bounds__(32 * kTabWarps) fk_table_kernel(const LigandsD
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int l = blockIdx.x * kTabWarps + w;
   if (l >= lig.L) return;   // uniform over the warp
-  const size_t per = fk_ligand_carve(acap, ncap, nullptr, nullptr);
+  const size_t lig_bytes = fk_ligand_carve(acap, ncap, nullptr, nullptr);
+  const size_t per = lig_bytes + LIGEN_MAX_ATOMS;   // + each atom's position in the owner-ordered list
   FkLigand S;
   fk_ligand_carve(acap, ncap, tab_smem + (size_t)w * per, &S);
+  uint8_t* pos = tab_smem + (size_t)w * per + lig_bytes;
   uint8_t* row = pk.fk_loff + (size_t)l * kFkLoffBytes;
   const int a0 = lig.atom_off[l], N = lig.atom_off[l + 1] - a0;
   const int r0 = lig.rot_off[l], n = lig.rot_off[l + 1] - r0;
@@ -273,10 +283,24 @@ __global__ void __launch_bounds__(32 * kTabWarps) fk_table_kernel(const LigandsD
     if (lane + 32 < kFkLoffBytes) row[lane + 32] = lane + 32 == kFkBad ? 1 : 0;
     return;
   }
-  for (int i = lane; i < N; i += 32) pk.fk_own[a0 + i] = S.own[i];
+  // the atoms listed by owner (bond 0's, ..., bond n-1's, the root's; a
+  // stable counting sort), so that a pose's consecutive atoms mostly share
+  // one transform
+  if (lane == 0) {
+    int start[LIGEN_MAX_ROT + 2];
+    for (int o = 0; o <= n + 1; ++o) start[o] = 0;
+    for (int i = 0; i < N; ++i) ++start[S.own[i] + 1];
+    for (int o = 0; o < n + 1; ++o) start[o + 1] += start[o];
+    for (int i = 0; i < N; ++i) pos[i] = (uint8_t)start[S.own[i]]++;
+  }
+  __syncwarp();
+  for (int i = lane; i < N; i += 32) {
+    pk.fk_xs[a0 + pos[i]] = S.sx[i];
+    pk.fk_own[a0 + pos[i]] = S.own[i];
+  }
   for (int b = lane; b < n; b += 32) {
     pk.fk_ax[r0 + b] = S.ax[b];
-    pk.fk_bond[r0 + b] = make_uchar4(S.par[b], S.ord[b], S.lord[b], 0);
+    pk.fk_bond[r0 + b] = make_uchar4(S.par[b], S.ord[b], S.lord[b], pos[S.sb[b].y]);
   }
   const int depths = S.loff[LIGEN_MAX_ROT];
   for (int k = lane; k < kFkLoffBytes; k += 32)
@@ -287,7 +311,7 @@ __global__ void __launch_bounds__(32 * kTabWarps) fk_table_kernel(const LigandsD
 
 cudaError_t launch_fk_table(const LigandsDev& lig, const Packed& pk, int max_atoms, int max_rot, cudaStream_t s) {
   if (lig.L == 0) return cudaSuccess;
-  const size_t smem = (size_t)kTabWarps * fk_ligand_carve(max_atoms, max_rot, nullptr, nullptr);
+  const size_t smem = (size_t)kTabWarps * (fk_ligand_carve(max_atoms, max_rot, nullptr, nullptr) + LIGEN_MAX_ATOMS);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fk_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -688,11 +688,12 @@ void plan_score(const int32_t* h_rot_off, int L, ScorePlan* sp) {
 
 // Regions of the forward-kinematics table (Packed::fk_*) in an arena.
 struct FkRegions {
-  size_t own = 0, bond = 0, ax = 0, loff = 0;
+  size_t xs = 0, own = 0, bond = 0, ax = 0, loff = 0;
 };
 
 FkRegions take_fk(Arena& ar, const LibShape& sh, int L) {
   FkRegions r;
+  r.xs = ar.take(16 * (size_t)sh.atoms);
   r.own = ar.take((size_t)sh.atoms);
   r.bond = ar.take(4 * (size_t)sh.rot);
   r.ax = ar.take(16 * (size_t)sh.rot);
@@ -701,6 +702,7 @@ FkRegions take_fk(Arena& ar, const LibShape& sh, int L) {
 }
 
 void set_fk(const Arena& ar, const FkRegions& r, Packed* pk) {
+  pk->fk_xs = ar.at<float4>(r.xs);
   pk->fk_own = ar.at<uint8_t>(r.own);
   pk->fk_bond = ar.at<uchar4>(r.bond);
   pk->fk_ax = ar.at<float4>(r.ax);
@@ -748,9 +750,9 @@ int used_classes(const ScorePlan& sp, int* used) {
 std::string score_key(const ScoreArgs& b, const int32_t* d_list, const int* used, int nu, const LaunchCfg* cfg,
                       const ScorePlan& sp) {
   std::string k;
-  const void* ptrs[] = {b.lig.atom_off, b.lig.rot_off, b.pk.xc, b.pk.binfo, b.pk.frag, b.pk.status, b.pk.fk_own,
-                        b.pk.fk_bond, b.pk.fk_ax, b.pk.fk_loff, b.grid.coef, b.grid.check, b.poses, b.out_scores,
-                        d_list};
+  const void* ptrs[] = {b.lig.atom_off, b.lig.rot_off, b.pk.xc,     b.pk.binfo,  b.pk.frag,    b.pk.status,
+                        b.pk.fk_xs,     b.pk.fk_own,   b.pk.fk_bond, b.pk.fk_ax, b.pk.fk_loff, b.grid.coef,
+                        b.grid.check,   b.poses,       b.out_scores, d_list};
   append_key(k, ptrs, sizeof ptrs);
   const int ints[] = {b.lig.L, b.grid.cx, b.grid.cy, b.grid.cz, b.grid.nc, b.P, b.max_atoms, nu};
   append_key(k, ints, sizeof ints);
@@ -776,7 +778,7 @@ int run_score(const ScoreArgs& base, const ScorePlan& sp, const int32_t* d_list,
     LG_CUDA(launch_score(base, s));
     return LIGEN_OK;
   }
-  if (!base.pk.fk_own || !base.pk.fk_bond || !base.pk.fk_ax || !base.pk.fk_loff)
+  if (!base.pk.fk_xs || !base.pk.fk_own || !base.pk.fk_bond || !base.pk.fk_ax || !base.pk.fk_loff)
     return fail(LIGEN_ERR_CUDA, "internal: pose-per-lane scoring without the forward-kinematics table");
   int used[kScoreClasses];
   const int nu = used_classes(sp, used);
@@ -1513,7 +1515,7 @@ static int grad_call(const ligen_ligands_t* ligands, const ligen_grid_t* grid, i
     LG_CUDA(launch_grad(ga, refine != 0, s));
   } else {   // pose groups on forward kinematics, class by class
     LG_CUDA(cudaMemcpyAsync(ar.base + o_list, plan.list.data(), 4 * plan.list.size(), cudaMemcpyHostToDevice, s));
-    if (!pk.fk_own || !pk.fk_bond || !pk.fk_ax || !pk.fk_loff)
+    if (!pk.fk_xs || !pk.fk_own || !pk.fk_bond || !pk.fk_ax || !pk.fk_loff)
       return fail(LIGEN_ERR_CUDA, "internal: pose-group gradients without the forward-kinematics table");
     int used[kScoreClasses];
     const int nu = used_classes(plan, used);
