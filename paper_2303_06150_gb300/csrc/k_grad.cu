@@ -393,11 +393,30 @@ __device__ float gl_eval(const GradArgs& a, const FkLigand& S, int N, int n, con
   float Sl = 0.f, gs[3] = {0.f, 0.f, 0.f}, Gp[9];
 #pragma unroll
   for (int e = 0; e < 9; ++e) Gp[e] = 0.f;
+  // The atoms are listed by owner: the owner's transform stays in registers
+  // across its atoms, and so do this lane's (F, tau) sums of the owner, added
+  // to the shared per-owner row once per run (the same additions in the
+  // same order as adding atom by atom to the row, which starts at zero).
+  int cur = -1;
+  float4 m0, m1, m2;
+  float fa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  auto flush = [&]() {
+    if (cur >= 0 && cur < n) {
+      float* ac = acc + ((size_t)cur * 32 + lane) * 6;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) ac[e] += fa[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 6; ++e) fa[e] = 0.f;
+  };
   for (int i = sub; i < N; i += G) {
     const float4 X = S.sx[i];
     const int o = S.own[i];
-    float4 m0, m1, m2;
-    fk_get(T + ((size_t)o * PW + grp) * 12, m0, m1, m2);
+    if (o != cur) {
+      flush();
+      fk_get(T + ((size_t)o * PW + grp) * 12, m0, m1, m2);
+      cur = o;
+    }
     const float u[3] = {fmaf(m0.x, X.x, fmaf(m0.y, X.y, fmaf(m0.z, X.z, m0.w))),
                         fmaf(m1.x, X.x, fmaf(m1.y, X.y, fmaf(m1.z, X.z, m1.w))),
                         fmaf(m2.x, X.x, fmaf(m2.y, X.y, fmaf(m2.z, X.z, m2.w)))};
@@ -411,16 +430,16 @@ __device__ float gl_eval(const GradArgs& a, const FkLigand& S, int N, int n, con
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int c = 0; c < 3; ++c) Gp[3 * r + c] = fmaf(du[r], dv[c], Gp[3 * r + c]);
-    if (o < n) {   // uniform over the warp: every group samples atom i of the same ligand
-      float* ac = acc + ((size_t)o * 32 + lane) * 6;
-      ac[0] += du[0];
-      ac[1] += du[1];
-      ac[2] += du[2];
-      ac[3] += u[1] * du[2] - u[2] * du[1];
-      ac[4] += u[2] * du[0] - u[0] * du[2];
-      ac[5] += u[0] * du[1] - u[1] * du[0];
+    if (o < n) {
+      fa[0] += du[0];
+      fa[1] += du[1];
+      fa[2] += du[2];
+      fa[3] += u[1] * du[2] - u[2] * du[1];
+      fa[4] += u[2] * du[0] - u[0] * du[2];
+      fa[5] += u[0] * du[1] - u[1] * du[0];
     }
   }
+  flush();
   // subtree sums, children first (this lane's own sums)
   for (int r = n - 1; r >= 0; --r) {
     const int b = S.ord[r], pb = S.par[b];
