@@ -335,11 +335,11 @@ int ligen_autotune(const ligen_ligands_t* ligands, const ligen_grid_t* grid, con
  * poses per ligand the ligands are scored by rotatable-bond class (0, 2, 4,
  * 6, 8, 12, 16, 24, 32 bonds at most), one pose per lane, the classes'
  * launches on forked streams, the sequence captured once into a CUDA graph
- * per (stream, call shape) and replayed; on the legacy or per-thread
- * default stream the graph runs on a side stream ordered after `stream` and
- * before its next work by events, and on a stream that is being captured
- * the launches go into the caller's graph. ligen_release_workspaces() frees
- * the cached graphs. */
+ * per (stream, call shape) and replayed on `stream` (for the legacy or
+ * per-thread default stream, which cannot be captured, the capture is made
+ * on a side stream); on a stream that is being captured the launches go
+ * into the caller's graph. ligen_release_workspaces() frees the cached
+ * graphs. */
 int ligen_score_poses(const ligen_ligands_t* ligands, const ligen_grid_t* grid,
                       int32_t poses_per_ligand, const float* poses, float out_penalty,
                       float* out_scores, void* stream);

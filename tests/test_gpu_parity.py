@@ -164,9 +164,9 @@ def test_prepared_scoring_equals_score_poses(lg, screen_sample, K):
 
 def test_scoring_graph_paths_agree(lg, screen_sample):
     """The class launches of pose-per-lane scoring replay from a cached CUDA
-    graph: on the legacy default stream through an event-fenced side stream,
-    on a user stream captured directly, and inside a caller's own capture
-    issued into that graph. Every path, first call and replay, gives the
+    graph: captured on a side stream for the legacy default stream and
+    launched on it, captured directly on a user stream, and inside a
+    caller's own capture issued into that graph. Every path, first call and replay, gives the
     same scores, and work queued before and after on the calling stream is
     ordered around it."""
     w, lib, grid = screen_sample
@@ -177,9 +177,14 @@ def test_scoring_graph_paths_agree(lg, screen_sample):
     prep = lg.prepare_scoring(Ld, Gd)
     ref = prep.score(poses, K)                      # default stream, first call: captured
     assert torch.equal(prep.score(poses, K), ref)   # replayed
+    from paper_2303_06150_gb300 import api
+    dev = torch.device("cuda", torch.cuda.current_device())
+    assert (api._stream_handle(dev).value or 0) == torch.cuda.current_stream().cuda_stream
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
+        assert api._stream_handle(dev).value == side.cuda_stream          # the binding passes the current stream
+        assert api._stream_handle(torch.device("cuda")).value == side.cuda_stream
         outs = [torch.full_like(ref, 7.0) for _ in range(3)]
         for o in outs:
             prep.score(poses, K, out=o)               # user stream: captured on it, then replayed
