@@ -1,17 +1,24 @@
-// Pose scoring: a group of kScoreLanes lanes per pose, two poses of one
-// ligand per warp (the warp's per-bond work, the torsion rebuild, serves
-// both; measured on GB300, scoring the 600,000 kept poses of the screening
-// library took 1.17 ms per call against 1.24 ms with a warp per pose, grid
-// preparation and packing included; 0.86 ms since the FP32 grid records are
-// prepared in FP32, 0.68 ms with the occupancy below).
-//
-// The pose (t, q, theta) is turned into atom positions exactly as the docking
-// output defines them: torsions bond by bond in index order on the centred
-// input coordinates (each about the current axis from its fixed endpoint to
-// its moving endpoint), then the rotation R(q / |q|) and the translation t.
-// Each lane then samples its atoms and the group sums S = -sum_i E_i. A warp
-// whose ligand has one pose left shadows it in the spare group, which
-// writes nothing.
+// Pose scoring: S = -sum_i E_i of given poses (t, q, theta), the atom
+// positions as the docking output defines them (torsions bond by bond in
+// index order on the centred input coordinates, each about the current axis
+// from its fixed endpoint to its moving endpoint; then R(q / |q|) and t).
+// Three kernels:
+//   score_lane_kernel  16 or more poses per ligand: one pose per lane, the
+//                      torsions as forward kinematics (fk_pose.cuh), launched
+//                      by rotatable-bond class (see its comment);
+//   fk_table_kernel    the ligand-only part of the forward kinematics, once
+//                      per library or call (owners, parents, orders, axes,
+//                      the atoms listed by owner);
+//   score_kernel       fewer poses: a group of kScoreLanes lanes per pose,
+//                      two poses of one ligand per warp, the torsions
+//                      applied atom by atom (pose_build.cuh). Measured on
+//                      GB300 on the 600,000 kept screening poses, before
+//                      the pose-per-lane kernel: 1.17 ms per call against
+//                      1.24 ms with a warp per pose, grid preparation and
+//                      packing included; 0.86 ms with the FP32 grid records
+//                      prepared in FP32, 0.68 ms with the occupancy below.
+//                      A warp whose ligand has one pose left shadows it in
+//                      the spare group, which writes nothing.
 #include <cmath>
 #include <map>
 #include <mutex>
