@@ -1,5 +1,11 @@
-// Pose gradients and gradient refinement: a group of kGradLanes lanes per
-// pose, 32 / kGradLanes poses (of one ligand) per warp.
+// Pose gradients and gradient refinement. Two kernels: grad_lane_kernel
+// (4 or more poses per ligand; the main path) puts a group of G = 1, 2 or 4
+// lanes on each pose and builds the torsions as forward kinematics
+// (fk_pose.cuh, the table of fk_table_kernel), the torsion gradients from
+// subtree sums, launched by rotatable-bond class; grad_kernel / refine_kernel
+// (fewer poses) put a group of kGradLanes lanes on each pose, 32 / kGradLanes
+// poses (of one ligand) per warp, and apply the torsions atom by atom. What
+// follows holds for both.
 //
 // S(t, q, theta) = -sum_i E(x_i), x_i = R(q/|q|) y_i + t, y_i the centred
 // input coordinates after the torsions. Per atom g_i = dS/dx_i = -grad E(x_i)
@@ -22,7 +28,7 @@
 //
 // Mapping. The poses of a warp belong to one ligand, so every group runs the
 // same atom and bond loops in lockstep and the per-bond work (the torsion
-// rebuild, the group sums) is shared by 32 / kGradLanes poses instead of
+// rebuild, the group sums) is shared by the warp's poses instead of
 // occupying a whole warp for one pose, whose 32 lanes mostly idle on ligands
 // of a few dozen atoms. A warp whose ligand has fewer
 // poses left than groups shadows the last pose in the spare groups and
