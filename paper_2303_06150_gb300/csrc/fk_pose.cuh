@@ -12,12 +12,15 @@
 // The root frame carries the pose's rotation, translation and the change to
 // grid units, so every transform maps input coordinates to grid units.
 //
-// Per ligand a warp stages, in shared memory: the centred input coordinates,
-// the bond records and moving-atom lists (coalesced loads); each atom's
-// owner; each bond's parent (the owner of its moving endpoint v, which no
-// other bond's list holds); the bonds in decreasing moving-side size (a
-// parent before its children) and grouped by depth in the bond tree; the
-// bond axes. Transforms are 12 floats: three rows (m0 m1 m2 | o).
+// fk_stage derives, per ligand, in shared memory: the centred input
+// coordinates, the bond records and moving-atom lists (coalesced loads);
+// each atom's owner; each bond's parent (the owner of its moving endpoint v,
+// which no other bond's list holds); the bonds in decreasing moving-side
+// size (a parent before its children) and grouped by depth in the bond
+// tree; the bond axes. fk_table_kernel runs it once per ligand and writes
+// the result out, with the atoms listed by owner; the scoring and gradient
+// kernels stage it with fk_load (vector copies). Transforms are 12 floats:
+// three rows (m0 m1 m2 | o).
 #pragma once
 
 #include "internal.h"
