@@ -147,6 +147,7 @@ struct RescoreArgs {
   double penalty;
   int K;                    // kept poses per ligand
   int max_atoms;            // largest ligand (shared-memory carve-up)
+  int max_rot;              // most rotatable bonds of a ligand (shared-memory carve-up)
   float* poses;             // outputs, re-ranked in place
   float* scores;            // [L][K], FP64 scores rounded to FP32
   int32_t* top_restart;     // [L][K] or NULL

@@ -3,21 +3,28 @@
 // FP32 scores decide the ranking.
 //
 // Everything is recomputed in FP64 from the caller's FP32 inputs: the input
-// centroid, the torsions (bond by bond, about the current axes), the
-// rotation q/|q|, the translation, and the trilinear value from the eight
-// FP32 node values of the caller's [z][y][x][c] grid.
+// centroid, the pose's atom positions, and the trilinear value from the
+// eight FP32 node values of the caller's [z][y][x][c] grid. The positions
+// follow the pose definition (torsions bond by bond in index order, each
+// about its current axis; then R(q/|q|) and t) as forward kinematics in
+// FP64, equal in exact arithmetic: bond b's transform is its parent's
+// composed with the rotation by theta_b about b's input-frame axis through
+// its moving endpoint v, and an atom's position is its owner's transform of
+// its centred input coordinates (owners, parents and the bond order from
+// fk_stage, as in the scoring kernels).
 //
 // Mapping. GB300 issues FP64 at a small fraction of its FP32 rate, so the
-// FP64 instruction count decides the time. A group of kRsLanes lanes scores
-// one pose and a warp holds kRsPoses poses of the same ligand: the per-bond
-// work (axis length, its reciprocal) is one FP64 instruction stream for all
-// of the warp's poses, each group's lanes split the moving atoms and the
-// atoms, and the torsions' sines and cosines are computed once per bond by
-// one lane of the group and passed by shuffle (measured on GB300, re-scoring
-// the 600,000 kept poses of the screening library: 28 ms with a warp per
-// pose and every lane repeating the per-bond work). Positions are scaled by
-// 1/h (one FP64 product) instead of divided by h; the two differ by FP64
-// rounding only.
+// FP64 instruction count decides the time. A warp holds kRsPoses poses of
+// one ligand, a group of kRsLanes lanes per pose. The bond axes and pivots
+// are computed once per warp, one lane per bond. Each pose's transforms are
+// composed depth by depth, the group's lanes splitting a depth's bonds. Then
+// the group's lanes split the atoms: one 3x4 transform each, then the
+// trilinear value. Measured on GB300, re-scoring the 600,000 kept poses of
+// the screening library:
+//   warp per pose, every lane repeating the per-bond work     28 ms
+//   torsions atom by atom, bond axes by every lane of a group  8.5 ms
+// Positions are scaled by 1/h (one FP64 product) instead of divided by h;
+// the two differ by FP64 rounding only.
 // Re-ranking: one warp per ligand orders its K poses by FP64 score
 // (descending; ties by the restart that produced them) and rewrites poses,
 // scores and restart ids in that order.
@@ -25,6 +32,7 @@
 
 #include "../../include/ligen.h"
 #include "internal.h"
+#include "fk_pose.cuh"
 
 namespace ligen {
 namespace {
@@ -32,7 +40,6 @@ namespace {
 constexpr int kResWarps = 4;
 constexpr int kRsLanes = 8;
 constexpr int kRsPoses = 32 / kRsLanes;            // poses per warp (one ligand)
-constexpr int kRsK = LIGEN_MAX_ROT / kRsLanes;     // bonds per lane of a group
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -70,10 +77,30 @@ __device__ double trilinear64(const RescoreArgs& a, double inv_h, double x, doub
   return e;
 }
 
+// Shared memory of one warp: the staged ligand (fk_stage), then per bond
+// its unit axis and pivot v in the input frame (FP64, 6 each), then the
+// transforms of the warp's poses (FP64, 12 each) [slot][pose][12].
+__host__ __device__ inline size_t rs_warp_bytes(int acap, int ncap, unsigned char* base, FkLigand* S, double** B,
+                                                double** T) {
+  const size_t lb = fk_ligand_carve(acap, ncap, base, S);   // a multiple of 16
+  const size_t bb = (size_t)ncap * 6 * sizeof(double);
+  const size_t tb = (size_t)(ncap + 1) * kRsPoses * 12 * sizeof(double);
+  if (base) {
+    *B = reinterpret_cast<double*>(base + lb);
+    *T = reinterpret_cast<double*>(base + lb + bb);
+  }
+  return lb + bb + tb;
+}
+
 __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreArgs a) {
-  extern __shared__ double ys[];   // [kResWarps * kRsPoses][max_atoms * 3]
+  extern __shared__ __align__(16) unsigned char rs_smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int grp = lane / kRsLanes, sub = lane % kRsLanes;
+  const int acap = a.max_atoms, ncap = a.max_rot;
+  FkLigand S;
+  double *B, *T;
+  const size_t per = rs_warp_bytes(acap, ncap, nullptr, nullptr, nullptr, nullptr);
+  rs_warp_bytes(acap, ncap, rs_smem + (size_t)w * per, &S, &B, &T);
   const int wpl = (a.K + kRsPoses - 1) / kRsPoses;   // warps per ligand
   const size_t gw = (size_t)blockIdx.x * kResWarps + w;
   if (gw >= (size_t)a.lig.L * wpl) return;   // uniform over the warp
@@ -82,74 +109,103 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
   const bool own = p0 < a.K;
   const int p = own ? p0 : a.K - 1;          // spare groups shadow the last pose
   const size_t gp = (size_t)l * a.K + p;
-  if (a.status[l] != 0 ||
-      !lg_check(a.check, a.lig.atom_off[l + 1] - a.lig.atom_off[l] <= a.max_atoms, kChkItemShape)) {
-    if (own && sub == 0) a.s64[gp] = -INFINITY;
-    return;
-  }
   const int a0 = a.lig.atom_off[l];
   const int N = a.lig.atom_off[l + 1] - a0;
   const int r0 = a.lig.rot_off[l];
   const int n = a.lig.rot_off[l + 1] - r0;
-  const float* pose = a.poses + (size_t)a.K * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
-  double* y = ys + (size_t)(w * kRsPoses + grp) * a.max_atoms * 3;
+  bool ok = a.status[l] == 0 && lg_check(a.check, N <= acap && n <= ncap, kChkItemShape);   // uniform
+  if (ok) ok = lg_check(a.check, fk_stage<true>(a.pk, a0, N, r0, n, S, lane), kChkAtomIndex);
+  if (!ok) {
+    if (own && sub == 0) a.s64[gp] = -INFINITY;
+    return;
+  }
+  // FP64 centroid of the input coordinates
   double c0[3] = {0.0, 0.0, 0.0};
   for (int i = lane; i < N; i += 32)
     for (int k = 0; k < 3; ++k) c0[k] += (double)a.lig.xyz[3 * (a0 + i) + k];
   for (int k = 0; k < 3; ++k) c0[k] = warp_sum_d(c0[k]) / N;
-  for (int i = sub; i < N; i += kRsLanes)
-    for (int k = 0; k < 3; ++k) y[3 * i + k] = (double)a.lig.xyz[3 * (a0 + i) + k] - c0[k];
-  // sine and cosine of bond b held by lane b % kRsLanes of the group
-  double bs[kRsK], bc[kRsK];
-#pragma unroll
-  for (int k = 0; k < kRsK; ++k) {
-    bs[k] = 0.0;
-    bc[k] = 1.0;
-    if (sub + k * kRsLanes < n) sincos((double)pose[7 + sub + k * kRsLanes], &bs[k], &bc[k]);
+  // per bond, once for the warp's poses: unit axis u -> v and pivot v in the
+  // input frame (fk_stage checked both ends against N)
+  for (int b = lane; b < n; b += 32) {
+    const uchar4 bi = S.sb[b];
+    double pu[3], pv[3];
+    for (int k = 0; k < 3; ++k) {
+      pu[k] = (double)a.lig.xyz[3 * (a0 + bi.x) + k] - c0[k];
+      pv[k] = (double)a.lig.xyz[3 * (a0 + bi.y) + k] - c0[k];
+    }
+    const double kx = pv[0] - pu[0], ky = pv[1] - pu[1], kz = pv[2] - pu[2];
+    const double inv = 1.0 / sqrt(kx * kx + ky * ky + kz * kz);
+    double* bb = B + 6 * b;
+    bb[0] = kx * inv; bb[1] = ky * inv; bb[2] = kz * inv;
+    bb[3] = pv[0]; bb[4] = pv[1]; bb[5] = pv[2];
+  }
+  // the pose's transforms (input frame -> world, Angstrom): the root R(q/|q|)
+  // and t, then bond by bond, parents first (depth by depth, the group's
+  // lanes splitting the bonds of a depth): bond b's is its parent's composed
+  // with the rotation by theta_b about b's axis through v
+  const float* pose = a.poses + (size_t)a.K * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
+  const size_t stride = (size_t)kRsPoses * 12;
+  double* Tg = T + 12 * grp;
+  if (sub == 0) {
+    const double qn = sqrt((double)pose[3] * pose[3] + (double)pose[4] * pose[4] + (double)pose[5] * pose[5] +
+                           (double)pose[6] * pose[6]);
+    const double qi = 1.0 / qn;
+    const double qw = pose[3] * qi, qx = pose[4] * qi, qy = pose[5] * qi, qz = pose[6] * qi;
+    const double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
+                         2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
+                         2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)};
+    double* Tr = Tg + (size_t)n * stride;
+    for (int r = 0; r < 3; ++r) {
+      Tr[4 * r] = R[3 * r];
+      Tr[4 * r + 1] = R[3 * r + 1];
+      Tr[4 * r + 2] = R[3 * r + 2];
+      Tr[4 * r + 3] = (double)pose[r];
+    }
   }
   __syncwarp();
-  for (int b = 0; b < n; ++b) {   // uniform over the warp (one ligand)
-    const uchar4 bi = a.pk.binfo[r0 + b];
-    if (!lg_check(a.check, bi.x < N && bi.y < N && bi.z < N, kChkAtomIndex)) continue;
-    double sb = bs[0], cb = bc[0];
-#pragma unroll
-    for (int k = 1; k < kRsK; ++k)
-      if (b / kRsLanes == k) { sb = bs[k]; cb = bc[k]; }
-    const double s = __shfl_sync(kFull, sb, b % kRsLanes, kRsLanes);
-    const double c = __shfl_sync(kFull, cb, b % kRsLanes, kRsLanes);
-    const double pv[3] = {y[3 * bi.y], y[3 * bi.y + 1], y[3 * bi.y + 2]};
-    double kx = pv[0] - y[3 * bi.x], ky = pv[1] - y[3 * bi.x + 1], kz = pv[2] - y[3 * bi.x + 2];
-    const double inv = 1.0 / sqrt(kx * kx + ky * ky + kz * kz);
-    kx *= inv; ky *= inv; kz *= inv;
-    const uint8_t* fr = a.pk.frag + (size_t)(r0 + b) * kFragStride;
-    for (int t = sub; t < bi.z; t += kRsLanes) {
-      const int i = fr[t];
-      if (!lg_check(a.check, i < N, kChkAtomIndex)) continue;
-      const double dx = y[3 * i] - pv[0], dy = y[3 * i + 1] - pv[1], dz = y[3 * i + 2] - pv[2];
-      const double kd = kx * dx + ky * dy + kz * dz;
-      y[3 * i] = pv[0] + kx * kd + (dx - kx * kd) * c + (ky * dz - kz * dy) * s;
-      y[3 * i + 1] = pv[1] + ky * kd + (dy - ky * kd) * c + (kz * dx - kx * dz) * s;
-      y[3 * i + 2] = pv[2] + kz * kd + (dz - kz * kd) * c + (kx * dy - ky * dx) * s;
+  const int depths = n ? S.loff[LIGEN_MAX_ROT] : 0;
+  for (int d = 0; d < depths; ++d) {
+    for (int k = S.loff[d] + sub; k < S.loff[d + 1]; k += kRsLanes) {
+      const int b = S.lord[k];
+      const double* P = Tg + (size_t)S.par[b] * stride;
+      const double* bb = B + 6 * b;
+      const double kx = bb[0], ky = bb[1], kz = bb[2];
+      double sn, cs;
+      sincos((double)pose[7 + b], &sn, &cs);
+      const double tc = 1.0 - cs;
+      // c I + s [k]x + (1 - c) k k^T: the right-handed rotation about k
+      const double Rb[9] = {tc * kx * kx + cs,      tc * kx * ky - sn * kz, tc * kx * kz + sn * ky,
+                            tc * kx * ky + sn * kz, tc * ky * ky + cs,      tc * ky * kz - sn * kx,
+                            tc * kx * kz - sn * ky, tc * ky * kz + sn * kx, tc * kz * kz + cs};
+      double* Tb = Tg + (size_t)b * stride;
+      for (int r = 0; r < 3; ++r) {
+        const double p0r = P[4 * r], p1r = P[4 * r + 1], p2r = P[4 * r + 2];
+        const double m0 = p0r * Rb[0] + p1r * Rb[3] + p2r * Rb[6];
+        const double m1 = p0r * Rb[1] + p1r * Rb[4] + p2r * Rb[7];
+        const double m2 = p0r * Rb[2] + p1r * Rb[5] + p2r * Rb[8];
+        // v keeps its place: o_b = T_p(v) - M_b v
+        const double tp = p0r * bb[3] + p1r * bb[4] + p2r * bb[5] + P[4 * r + 3];
+        Tb[4 * r] = m0;
+        Tb[4 * r + 1] = m1;
+        Tb[4 * r + 2] = m2;
+        Tb[4 * r + 3] = tp - (m0 * bb[3] + m1 * bb[4] + m2 * bb[5]);
+      }
     }
     __syncwarp();
   }
-  const double qn = sqrt((double)pose[3] * pose[3] + (double)pose[4] * pose[4] + (double)pose[5] * pose[5] +
-                         (double)pose[6] * pose[6]);
-  const double qi = 1.0 / qn;
-  const double qw = pose[3] * qi, qx = pose[4] * qi, qy = pose[5] * qi, qz = pose[6] * qi;
-  const double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
-                       2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
-                       2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)};
+  // the group's lanes split the atoms: owner's transform, FP64 trilinear value
   const double inv_h = 1.0 / a.h;
-  double S = 0.0;
+  double Sg = 0.0;
   for (int i = sub; i < N; i += kRsLanes) {
+    const double* M = Tg + (size_t)S.own[i] * stride;
+    double y[3];
+    for (int k = 0; k < 3; ++k) y[k] = (double)a.lig.xyz[3 * (a0 + i) + k] - c0[k];
     double x[3];
-    for (int r = 0; r < 3; ++r)
-      x[r] = R[3 * r] * y[3 * i] + R[3 * r + 1] * y[3 * i + 1] + R[3 * r + 2] * y[3 * i + 2] + (double)pose[r];
-    S -= trilinear64(a, inv_h, x[0], x[1], x[2], a.lig.type[a0 + i]);
+    for (int r = 0; r < 3; ++r) x[r] = M[4 * r] * y[0] + M[4 * r + 1] * y[1] + M[4 * r + 2] * y[2] + M[4 * r + 3];
+    Sg -= trilinear64(a, inv_h, x[0], x[1], x[2], a.lig.type[a0 + i]);
   }
-  S = group_sum_d(S);
-  if (own && sub == 0) a.s64[gp] = S;
+  Sg = group_sum_d(Sg);
+  if (own && sub == 0) a.s64[gp] = Sg;
 }
 
 // Re-rank the K poses of each ligand by FP64 score; ties go to the lower
@@ -198,7 +254,7 @@ __global__ void __launch_bounds__(32 * kResWarps) rerank_kernel(const RescoreArg
 cudaError_t launch_rescore(const RescoreArgs& a, cudaStream_t s) {
   const size_t total = (size_t)a.lig.L * a.K;
   if (total == 0) return cudaSuccess;
-  const size_t smem = (size_t)kResWarps * kRsPoses * a.max_atoms * 3 * sizeof(double);
+  const size_t smem = (size_t)kResWarps * rs_warp_bytes(a.max_atoms, a.max_rot, nullptr, nullptr, nullptr, nullptr);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -1094,6 +1094,7 @@ static int dock_impl(const ligen_ligands_t* ligands, const ligen_grid_t* grids, 
       rsa.penalty = params->out_penalty;
       rsa.K = K;
       rsa.max_atoms = sh.max_atoms;
+      rsa.max_rot = sh.max_rot;
       rsa.poses = d_poses;
       rsa.scores = d_scores;
       rsa.top_restart = site_top ? d_top : nullptr;
