@@ -54,42 +54,56 @@ __device__ __forceinline__ double group_sum_d(double v) {
   return v;
 }
 
-__device__ double trilinear64(const RescoreArgs& a, double inv_h, double x, double y, double z, int c) {
-  const double u[3] = {(x - a.origin[0]) * inv_h, (y - a.origin[1]) * inv_h, (z - a.origin[2]) * inv_h};
-  const int n[3] = {a.nx, a.ny, a.nz};
-  int i[3];
-  double f[3];
-  for (int k = 0; k < 3; ++k) {
-    if (!(u[k] >= 0.0 && u[k] <= n[k] - 1)) return a.penalty;
-    i[k] = min((int)floor(u[k]), n[k] - 2);
-    f[k] = u[k] - i[k];
-  }
-  double e = 0.0;
-  for (int dz = 0; dz < 2; ++dz)
-    for (int dy = 0; dy < 2; ++dy)
-      for (int dx = 0; dx < 2; ++dx) {
-        const double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
-        const size_t node = (((size_t)(i[2] + dz) * a.ny + (i[1] + dy)) * a.nx + (i[0] + dx));
-        if (!lg_check(a.check, c >= 0 && c < a.nc && node < (size_t)a.nx * a.ny * a.nz, kChkRescoreNode))
-          continue;
-        e += w * (double)a.values[node * a.nc + c];
-      }
-  return e;
+// The box and scaling of the FP64 trilinear value, once per thread.
+struct Tri64 {
+  double ox, oy, oz, inv_h;   // origin, 1 / h
+  double mx, my, mz;          // points - 1 per axis: the box in grid units
+};
+
+// FP64 trilinear value of channel c at world point (x, y, z): the cell by a
+// round-down conversion, then 7 interpolations (x, then y, then z) of the 8
+// FP32 node values widened to FP64. Outside the box: the penalty.
+__device__ __forceinline__ double trilinear64(const RescoreArgs& a, const Tri64& t, double x, double y, double z,
+                                              int c) {
+  const double u0 = (x - t.ox) * t.inv_h, u1 = (y - t.oy) * t.inv_h, u2 = (z - t.oz) * t.inv_h;
+  if (!(u0 >= 0.0 && u0 <= t.mx && u1 >= 0.0 && u1 <= t.my && u2 >= 0.0 && u2 <= t.mz)) return a.penalty;
+  const int i0 = min(__double2int_rd(u0), a.nx - 2);
+  const int i1 = min(__double2int_rd(u1), a.ny - 2);
+  const int i2 = min(__double2int_rd(u2), a.nz - 2);
+  const double f0 = u0 - i0, f1 = u1 - i1, f2 = u2 - i2;
+  const size_t sx = (size_t)a.nc, sy = sx * a.nx, sz = sy * a.ny;
+  const size_t base = ((size_t)i2 * a.ny + i1) * a.nx + i0;
+  if (!lg_check(a.check, c >= 0 && c < a.nc && base + (size_t)a.nx * a.ny + a.nx + 1 < (size_t)a.nx * a.ny * a.nz,
+                kChkRescoreNode))
+    return a.penalty;
+  const float* v = a.values + base * sx + c;
+  const double c000 = v[0], c100 = v[sx], c010 = v[sy], c110 = v[sy + sx];
+  const double c001 = v[sz], c101 = v[sz + sx], c011 = v[sz + sy], c111 = v[sz + sy + sx];
+  const double e00 = fma(f0, c100 - c000, c000), e10 = fma(f0, c110 - c010, c010);
+  const double e01 = fma(f0, c101 - c001, c001), e11 = fma(f0, c111 - c011, c011);
+  const double e0 = fma(f1, e10 - e00, e00), e1 = fma(f1, e11 - e01, e01);
+  return fma(f2, e1 - e0, e0);
 }
 
 // Shared memory of one warp: the staged ligand (fk_stage), then per bond
 // its unit axis and pivot v in the input frame (FP64, 6 each), then the
-// transforms of the warp's poses (FP64, 12 each) [slot][pose][12].
+// transforms of the warp's poses (FP64, 12 each) [slot][pose][12], the
+// centred input coordinates (FP64, 3 per atom), and the sine and cosine of
+// every (pose, bond) [pose][bond][2].
 __host__ __device__ inline size_t rs_warp_bytes(int acap, int ncap, unsigned char* base, FkLigand* S, double** B,
-                                                double** T) {
+                                                double** T, double** Y, double** SC) {
   const size_t lb = fk_ligand_carve(acap, ncap, base, S);   // a multiple of 16
   const size_t bb = (size_t)ncap * 6 * sizeof(double);
   const size_t tb = (size_t)(ncap + 1) * kRsPoses * 12 * sizeof(double);
+  const size_t yb = ((size_t)acap * 3 * sizeof(double) + 15) & ~(size_t)15;
+  const size_t sb = (size_t)kRsPoses * ncap * 2 * sizeof(double);
   if (base) {
     *B = reinterpret_cast<double*>(base + lb);
     *T = reinterpret_cast<double*>(base + lb + bb);
+    *Y = reinterpret_cast<double*>(base + lb + bb + tb);
+    *SC = reinterpret_cast<double*>(base + lb + bb + tb + yb);
   }
-  return lb + bb + tb;
+  return lb + bb + tb + yb + sb;
 }
 
 __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreArgs a) {
@@ -98,9 +112,9 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
   const int grp = lane / kRsLanes, sub = lane % kRsLanes;
   const int acap = a.max_atoms, ncap = a.max_rot;
   FkLigand S;
-  double *B, *T;
-  const size_t per = rs_warp_bytes(acap, ncap, nullptr, nullptr, nullptr, nullptr);
-  rs_warp_bytes(acap, ncap, rs_smem + (size_t)w * per, &S, &B, &T);
+  double *B, *T, *Y, *SC;
+  const size_t per = rs_warp_bytes(acap, ncap, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  rs_warp_bytes(acap, ncap, rs_smem + (size_t)w * per, &S, &B, &T, &Y, &SC);
   const int wpl = (a.K + kRsPoses - 1) / kRsPoses;   // warps per ligand
   const size_t gw = (size_t)blockIdx.x * kResWarps + w;
   if (gw >= (size_t)a.lig.L * wpl) return;   // uniform over the warp
@@ -124,6 +138,8 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
   for (int i = lane; i < N; i += 32)
     for (int k = 0; k < 3; ++k) c0[k] += (double)a.lig.xyz[3 * (a0 + i) + k];
   for (int k = 0; k < 3; ++k) c0[k] = warp_sum_d(c0[k]) / N;
+  for (int i = lane; i < N; i += 32)   // centred coordinates, once for the warp's poses
+    for (int k = 0; k < 3; ++k) Y[3 * i + k] = (double)a.lig.xyz[3 * (a0 + i) + k] - c0[k];
   // per bond, once for the warp's poses: unit axis u -> v and pivot v in the
   // input frame (fk_stage checked both ends against N)
   for (int b = lane; b < n; b += 32) {
@@ -134,7 +150,7 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
       pv[k] = (double)a.lig.xyz[3 * (a0 + bi.y) + k] - c0[k];
     }
     const double kx = pv[0] - pu[0], ky = pv[1] - pu[1], kz = pv[2] - pu[2];
-    const double inv = 1.0 / sqrt(kx * kx + ky * ky + kz * kz);
+    const double inv = rsqrt(kx * kx + ky * ky + kz * kz);
     double* bb = B + 6 * b;
     bb[0] = kx * inv; bb[1] = ky * inv; bb[2] = kz * inv;
     bb[3] = pv[0]; bb[4] = pv[1]; bb[5] = pv[2];
@@ -146,10 +162,15 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
   const float* pose = a.poses + (size_t)a.K * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
   const size_t stride = (size_t)kRsPoses * 12;
   double* Tg = T + 12 * grp;
+  // Every lane runs a warp's FP64 instruction at the full cost whether or
+  // not it is active (GB300's FP64 pipe is narrow), so the sines and cosines
+  // of all (pose, bond) pairs are taken in one pass over the warp's lanes,
+  // not inside the depth loop where a few lanes would be busy per depth.
+  double* scg = SC + (size_t)grp * ncap * 2;
+  for (int b = sub; b < n; b += kRsLanes) sincos((double)pose[7 + b], &scg[2 * b], &scg[2 * b + 1]);
   if (sub == 0) {
-    const double qn = sqrt((double)pose[3] * pose[3] + (double)pose[4] * pose[4] + (double)pose[5] * pose[5] +
-                           (double)pose[6] * pose[6]);
-    const double qi = 1.0 / qn;
+    const double qi = rsqrt((double)pose[3] * pose[3] + (double)pose[4] * pose[4] + (double)pose[5] * pose[5] +
+                            (double)pose[6] * pose[6]);
     const double qw = pose[3] * qi, qx = pose[4] * qi, qy = pose[5] * qi, qz = pose[6] * qi;
     const double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
                          2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
@@ -170,8 +191,7 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
       const double* P = Tg + (size_t)S.par[b] * stride;
       const double* bb = B + 6 * b;
       const double kx = bb[0], ky = bb[1], kz = bb[2];
-      double sn, cs;
-      sincos((double)pose[7 + b], &sn, &cs);
+      const double sn = scg[2 * b], cs = scg[2 * b + 1];
       const double tc = 1.0 - cs;
       // c I + s [k]x + (1 - c) k k^T: the right-handed rotation about k
       const double Rb[9] = {tc * kx * kx + cs,      tc * kx * ky - sn * kz, tc * kx * kz + sn * ky,
@@ -194,15 +214,17 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
     __syncwarp();
   }
   // the group's lanes split the atoms: owner's transform, FP64 trilinear value
-  const double inv_h = 1.0 / a.h;
+  Tri64 tb;
+  tb.ox = a.origin[0]; tb.oy = a.origin[1]; tb.oz = a.origin[2];
+  tb.inv_h = 1.0 / a.h;
+  tb.mx = a.nx - 1; tb.my = a.ny - 1; tb.mz = a.nz - 1;
   double Sg = 0.0;
   for (int i = sub; i < N; i += kRsLanes) {
     const double* M = Tg + (size_t)S.own[i] * stride;
-    double y[3];
-    for (int k = 0; k < 3; ++k) y[k] = (double)a.lig.xyz[3 * (a0 + i) + k] - c0[k];
+    const double* y = Y + 3 * i;
     double x[3];
     for (int r = 0; r < 3; ++r) x[r] = M[4 * r] * y[0] + M[4 * r + 1] * y[1] + M[4 * r + 2] * y[2] + M[4 * r + 3];
-    Sg -= trilinear64(a, inv_h, x[0], x[1], x[2], a.lig.type[a0 + i]);
+    Sg -= trilinear64(a, tb, x[0], x[1], x[2], a.lig.type[a0 + i]);
   }
   Sg = group_sum_d(Sg);
   if (own && sub == 0) a.s64[gp] = Sg;
@@ -254,7 +276,8 @@ __global__ void __launch_bounds__(32 * kResWarps) rerank_kernel(const RescoreArg
 cudaError_t launch_rescore(const RescoreArgs& a, cudaStream_t s) {
   const size_t total = (size_t)a.lig.L * a.K;
   if (total == 0) return cudaSuccess;
-  const size_t smem = (size_t)kResWarps * rs_warp_bytes(a.max_atoms, a.max_rot, nullptr, nullptr, nullptr, nullptr);
+  const size_t smem =
+      (size_t)kResWarps * rs_warp_bytes(a.max_atoms, a.max_rot, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
