@@ -162,10 +162,10 @@ __global__ void __launch_bounds__(32 * kResWarps) rescore_kernel(const RescoreAr
   const float* pose = a.poses + (size_t)a.K * (7 * (size_t)l + r0) + (size_t)p * (7 + n);
   const size_t stride = (size_t)kRsPoses * 12;
   double* Tg = T + 12 * grp;
-  // Every lane runs a warp's FP64 instruction at the full cost whether or
-  // not it is active (GB300's FP64 pipe is narrow), so the sines and cosines
-  // of all (pose, bond) pairs are taken in one pass over the warp's lanes,
-  // not inside the depth loop where a few lanes would be busy per depth.
+  // The sines and cosines of all (pose, bond) pairs in one pass over the
+  // warp's lanes, not inside the depth loop, where only a depth's bonds
+  // keep lanes busy (measured on GB300: re-score 6.9 -> 6.5 ms; FP64 warp
+  // instructions seem to cost about the same however few lanes are active).
   double* scg = SC + (size_t)grp * ncap * 2;
   for (int b = sub; b < n; b += kRsLanes) sincos((double)pose[7 + b], &scg[2 * b], &scg[2 * b + 1]);
   if (sub == 0) {
