@@ -23,6 +23,8 @@
 // the screening library:
 //   warp per pose, every lane repeating the per-bond work     28 ms
 //   torsions atom by atom, bond axes by every lane of a group  8.5 ms
+//   forward kinematics, 4 poses per warp                       6.5 ms
+//   the same, 8 poses per warp (4 lanes each)                  5.1 ms
 // Positions are scaled by 1/h (one FP64 product) instead of divided by h;
 // the two differ by FP64 rounding only.
 // Re-ranking: one warp per ligand orders its K poses by FP64 score
@@ -38,7 +40,11 @@ namespace ligen {
 namespace {
 
 constexpr int kResWarps = 4;
-constexpr int kRsLanes = 8;
+// lanes per pose: the warp's per-pose FP64 passes (root, sines and cosines,
+// transforms by depth) serve 32 / kRsLanes poses. Measured on GB300, the
+// re-score stage of a screening step: 8 lanes 6.6 ms, 4 lanes 5.2 ms,
+// 2 lanes 5.6 ms.
+constexpr int kRsLanes = 4;
 constexpr int kRsPoses = 32 / kRsLanes;            // poses per warp (one ligand)
 constexpr unsigned kFull = 0xffffffffu;
 
