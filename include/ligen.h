@@ -457,7 +457,8 @@ int ligen_probe_stream(const void* buffer, int64_t n_bytes, int32_t passes, floa
 /* Release every cached workspace of the calling thread's current device,
  * with the cached CUDA graphs and the side streams and events of the forked
  * launches (created per calling stream on first use). Waits for the work on
- * those streams. */
+ * those streams. No other library call may run on that device meanwhile
+ * (from any thread): they share these caches. */
 int ligen_release_workspaces(void);
 
 /* Caps every internal workspace at `bytes` (<= 0: no cap, the default), for
